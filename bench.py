@@ -1,0 +1,350 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 asymmetric-plmDCA library.
+
+One step = the whole hot path on one synthetic protein family (N = 120
+positions, B = 5000 sequences, q = 21, 180 planted chain contacts, 15 %
+gaps): reweighting at 0.8 identity, the batched per-site L-BFGS solve of
+every g_r^(reg) to ||grad|| <= 1e-4, then Ising gauge + average + FN + APC
+and the top-N contact list.  The MSA is resident in HBM before the timed
+region; L2 is flushed (a 256 MiB write) between timed steps.
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle instead (on host cores, a bounded sample of the same workload).
+Multi-GPU runs (torchrun) are independent replicas (one family per rank).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "plmDCA full-solve seconds & objective+grad evals/s vs plain FP32 path at fixed error"
+WORKLOAD = "synthetic protein family N=120 B=5000 q=21 (180 planted chain contacts, 15% gaps)"
+MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="auto", choices=["auto", "fp32", "split_bf16"])
+    ap.add_argument("--gtol", type=float, default=1e-4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sites", type=int, default=0,
+                    help="sites per CPU-oracle sample (0 = one per host core, at most 16)")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(MEASURED) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_sample(fam, n_sites, gtol):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload:
+    the full reweighting, the L-BFGS solve of `n_sites` site problems (the
+    site problems are independent), and FN+APC on the full J; the solve time
+    is scaled by N / n_sites to one full solve."""
+    import numpy as np
+    import oracle
+    S = fam.msa
+    N = S.shape[1]
+    t0 = time.perf_counter()
+    m, w, w32, beff = oracle.reweight(S, 0.8)
+    t1 = time.perf_counter()
+    sites = list(np.linspace(0, N - 1, n_sites).round().astype(int))
+    h, J, info = oracle.solve(S, w, beff, 0.01, 0.01, gtol=gtol, sites=sites)
+    t2 = time.perf_counter()
+    fn, cfn = oracle.scores(J)
+    oracle.topL(cfn, N, 5)
+    t3 = time.perf_counter()
+    full = (t1 - t0) + (t2 - t1) * N / len(sites) + (t3 - t2)
+    evals = float(np.mean(info["nevals"]))
+    return full, (t3 - t0), evals, len(sites)
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    import oracle
+    from paper_1401_4832_gb300 import synth
+    fam = synth.protein_family(seed=0)
+    cores = oracle.num_threads()
+    n_sites = args.cpu_sites or min(16, cores)
+    for _ in range(args.warmup):
+        cpu_sample(fam, max(1, n_sites // 4), args.gtol)
+    vals, walls = [], []
+    for _ in range(args.steps):
+        full, wall, evals, ns = cpu_sample(fam, n_sites, args.gtol)
+        vals.append(full)
+        walls.append(wall)
+    v = statistics.mean(vals)
+    sample = (f"full reweighting + L-BFGS of {ns} of {fam.N} sites (gtol {args.gtol}) scaled "
+              f"x{fam.N}/{ns} + full FN/APC/top-L, FP64 oracle, {cores} OpenMP threads")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * statistics.mean(walls), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": fam.N, "B": fam.B, "q": 21, "gtol": args.gtol,
+                   "parallelism": "host cores (OpenMP over sites)"},
+        "cpu_baseline": {"value": v, "unit": "s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import numpy as np
+    import torch
+    from paper_1401_4832_gb300 import _native, api, synth
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    device = local
+    torch.cuda.set_device(device)
+    pk, pk_kind = peaks()
+
+    # one replica per rank (weak scaling): family seed = rank
+    fam = synth.protein_family(seed=rank)
+    B, N = fam.B, fam.N
+    msa = torch.from_numpy(fam.msa).to(f"cuda:{device}")
+    stream = torch.cuda.Stream(device)
+    ctx = api.Context(device, stream)
+    prec = args.prec
+    if prec == "auto":
+        prec = "split_bf16"
+        try:
+            api.plm_solve(ctx, msa[:64, :8].contiguous(), prec="split_bf16", max_iter=1)
+        except _native.PlmError:
+            prec = "fp32"
+    opts = dict(gtol=args.gtol, prec=prec)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{device}")
+
+    def step():
+        h, J, rep = api.plm_solve(ctx, msa, **opts)
+        fn, cfn, top = api.fn_apc_scores(ctx, J)
+        return rep, top
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize(device)
+        if dist:
+            dist.barrier()
+        lib = _native.load()
+        launches0 = lib.plm_kernel_launches()
+        sampler = ClockSampler(device)
+        sampler.start()
+        times, reps = [], []
+        t_wall0 = time.perf_counter()
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize(device)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rep, top = step()
+            e1.record(stream)
+            torch.cuda.synchronize(device)
+            times.append(e0.elapsed_time(e1) / 1000.0)
+            reps.append(rep)
+        t_wall = time.perf_counter() - t_wall0
+        clocks = sampler.stop()
+        launches = lib.plm_kernel_launches() - launches0
+    if dist:
+        dist.barrier()
+    mean_t = statistics.mean(times)
+    if dist:
+        tt = torch.tensor([sum(times)], device=f"cuda:{device}", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_max = tt.item()
+    else:
+        total_max = sum(times)
+    value = total_max / (args.steps * world)  # seconds per solve for the whole job
+    evals = statistics.mean(r["evals"] for r in reps)
+
+    # end to end through the C ABI with host buffers (pinned MSA in, J/h/scores out)
+    msa_host = torch.from_numpy(fam.msa).pin_memory()
+    msa_np = msa_host.numpy()
+    e2e_times = []
+    for _ in range(max(1, args.steps)):
+        torch.cuda.synchronize(device)
+        t0 = time.perf_counter()
+        h_h, J_h, _ = api.plm_solve(ctx, msa_np, **opts)
+        fn_h, cfn_h, top_h = api.fn_apc_scores(ctx, J_h)
+        e2e_times.append(time.perf_counter() - t0)
+    h2d = B * N + N * 21 * N * 21 * 4  # msa in; J back in for the scoring call
+    d2h = (N * 21 + (N * 21) ** 2) * 4 + 2 * N * N * 8 + N * 2 * 4
+
+    # per-kernel device times of one profiled solve (events on the library stream)
+    lib.plm_profile(ctx.handle, 1)
+    with torch.cuda.stream(stream):
+        flush.zero_()
+        rep_p, _ = step()
+    import ctypes
+    buf = ctypes.create_string_buffer(1 << 16)
+    lib.plm_profile_report.argtypes = [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_int]
+    lib.plm_profile_report(ctx.handle, buf, len(buf))
+    lib.plm_profile(ctx.handle, 0)
+    kern = {}
+    for ln in buf.value.decode().splitlines():
+        name, cnt, ms = ln.split()
+        kern[name] = (int(cnt), float(ms))
+    dom = max(kern, key=lambda k: kern[k][1]) if kern else None
+    roof = None
+    if dom:
+        cnt, ms = kern[dom]
+        avg_s = ms / 1000.0 / cnt
+        roof = roofline_entry(dom, avg_s, B, N, pk, pk_kind)
+        roof["kernel"] = dom
+        roof["launches_profiled"] = cnt
+        roof["share_of_profiled"] = ms / sum(v[1] for v in kern.values())
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        cores = oracle.num_threads()
+        n_sites = args.cpu_sites or min(16, cores)
+        full, wall, oevals, ns = cpu_sample(fam, n_sites, args.gtol)
+        cpu = {"value": full, "unit": "s", "cores": cores, "kind": "oracle",
+               "sample": (f"full reweighting + L-BFGS of {ns} of {N} sites (gtol {args.gtol}) "
+                          f"scaled x{N}/{ns} + full FN/APC/top-L; {wall:.1f} s of CPU wall time")}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": "s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * mean_t,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16" if prec == "split_bf16" else "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": N, "B": B, "q": 21, "gtol": args.gtol,
+                       "precision": prec, "lbfgs_m": 5, "lambda_h": 0.01, "lambda_J": 0.01,
+                       "x": 0.8, "l2": "flushed between timed steps (256 MiB write)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "evals_per_s": evals / mean_t,
+            "evals_per_solve": evals,
+            "iters": statistics.mean(r["iters"] for r in reps),
+            "sites_converged": reps[-1]["n_converged"], "sites_noise": reps[-1]["n_noise"],
+            "sites_failed": reps[-1]["n_failed"], "gnorm_max": reps[-1]["gnorm_max"],
+            "clocks": clocks,
+            "e2e": {"value": statistics.mean(e2e_times), "unit": "s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "roofline": roof,
+            "kernels_profiled_ms": {k: v[1] for k, v in kern.items()},
+            "cpu_baseline": cpu,
+            "wall_s_timed_region": t_wall,
+        }
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def roofline_entry(kernel, avg_s, B, N, pk, pk_kind):
+    """Algorithmic work of one launch of the dominant kernel / its duration."""
+    q = 21
+    if kernel in ("logits_gather", "grad_gather"):
+        # one FP32 add per gathered coupling: B * N * (N-1) * q couplings + B*N*q fields
+        adds = B * N * N * q
+        sm_mhz = pk.get("sm_max_mhz", 2070.0)
+        peak = 152 * 128 * sm_mhz * 1e6 / 1e12  # FP32 lanes x clock, T adds/s
+        ach = adds / avg_s / 1e12
+        return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Tadd/s",
+                "frac": ach / peak, "traffic": None,
+                "peak_note": f"152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (derived)"}
+    if kernel in ("tc_logits", "tc_grad"):
+        KP = (N * q + 1 + 63) // 64 * 64
+        R = N * 24
+        BP = (B + 127) // 128 * 128
+        flops = 2 * 2 * BP * R * KP  # split: two bf16 products into one accumulator
+        peak = pk.get("bf16_tflops_sustained", 1700.0)
+        ach = flops / avg_s / 1e12
+        return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None,
+                "peak_note": f"bf16 dense sustained, {pk_kind}"}
+    # L-BFGS / other streaming kernels: HBM bound
+    return {"bound": "hbm", "achieved": None, "peak": pk.get("hbm_gbs"), "unit": "GB/s",
+            "frac": None, "traffic": None}
+
+
+if __name__ == "__main__":
+    main()

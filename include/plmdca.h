@@ -1,0 +1,188 @@
+/*
+ * plmdca.h -- C ABI of the GB300 (sm_103a) asymmetric plmDCA library.
+ *
+ * Method: Ekeberg, Hartonen & Aurell, "Fast pseudolikelihood maximization
+ * for direct-coupling analysis of protein structure from many homologous
+ * amino-acid sequences" (J. Comput. Phys. 2014).  The calls follow the
+ * paper's statement of the problem (Sec. 3.5): an MSA, a reweighting
+ * threshold x and regularisation strengths lambda_h, lambda_J go in;
+ * couplings and contact scores come out.
+ *
+ * Conventions for every call
+ *   - q must be 21 (20 amino acids + gap, Sec. 2); other values give
+ *     PLM_EINVAL.  State 0 is the gap.
+ *   - msa is int8 [B][N], row-major (sequence b, position i), values 0..q-1.
+ *   - Couplings use the public, unpadded "asymmetric" layout
+ *         J[r][s][i][k] = J^r_{ri}(s,k)     (float [N][q][N][q])
+ *     i.e. the estimate of coupling (r,i) produced by site r's problem, with
+ *     the first state index belonging to r (Sec. 3, remark after Eq.
+ *     condpfinal).  Diagonal blocks J[r][.][r][.] are not parameters: they
+ *     must be zero on input and are returned zero.  Fields: h[r][s], float
+ *     [N][q].
+ *   - Array arguments may be device pointers or host pointers (pageable or
+ *     pinned); the library checks each with cudaPointerGetAttributes and
+ *     stages host arrays through its own device workspace.  The caller keeps
+ *     ownership of every array it passes.
+ *   - Work is ordered on the context's stream.  Calls that return host
+ *     scalars (msa_reweight's B_eff, plm_solve's report) or that were given
+ *     host arrays synchronise that stream before returning.
+ *   - A status != PLM_OK leaves the outputs unspecified and the context
+ *     usable, except PLM_ECUDA after a sticky CUDA error.  plm_last_error()
+ *     returns a message for the last failing call on that context.
+ *   - Nothing here may be called from two host threads on one context at
+ *     the same time.
+ */
+#ifndef PLMDCA_H
+#define PLMDCA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct plm_ctx plm_ctx; /* opaque; owns the device workspace */
+
+typedef enum {
+    PLM_OK = 0,
+    PLM_EINVAL = -1,    /* bad argument (shape, range, null pointer) */
+    PLM_ENOMEM = -2,    /* device or host allocation failed */
+    PLM_ECUDA = -3,     /* a CUDA call failed */
+    PLM_ENOTCONV = -4,  /* plm_solve: some site did not reach gtol */
+    PLM_ETIMEOUT = -5,  /* a device-side wait ran out of its budget */
+    PLM_ENOTIMPL = -6   /* option not built */
+} plm_status;
+
+/* Arithmetic of the two contractions (logits and gradient). */
+typedef enum {
+    PLM_FP32_EXACT = 0, /* FP32 gather/scatter sums on the CUDA cores */
+    PLM_TF32 = 1,       /* reserved; returns PLM_ENOTIMPL */
+    PLM_SPLIT_BF16 = 2  /* tcgen05 tensor cores: couplings and residuals split
+                           into bf16 hi + lo parts, one-hot operand exact,
+                           FP32 accumulation in tensor memory */
+} plm_precision;
+
+typedef struct {
+    double x;          /* reweighting identity threshold, 0..1 (paper: 0.8) */
+    double lambda_h;   /* field strength (paper: 0.01) */
+    double lambda_J;   /* coupling strength as the user gives it (paper: 0.01);
+                          halved inside, lambda'_J = 0.5 lambda_J (step 1) */
+    double gtol;       /* stop a site when ||grad g_r^(reg)||_2 <= gtol */
+    int lbfgs_m;       /* L-BFGS memory, 1..16 */
+    int max_iter;      /* iteration cap per site */
+    int max_ls;        /* trial steps per line search before a site fails */
+    plm_precision prec;
+    int use_graph;     /* 1: capture the per-iteration launches in a CUDA graph */
+    int reserved[7];
+} plm_opts;
+
+typedef struct {
+    int iters;         /* iterations of the slowest site */
+    int evals;         /* objective+gradient evaluations (all sites each) */
+    int n_converged;   /* sites with ||grad|| <= gtol */
+    int n_noise;       /* sites stopped because the line search could not
+                          resolve a decrease within the FP32 evaluation noise;
+                          their gradient norm is reported in gnorm_max */
+    int n_failed;      /* sites stopped by max_iter or a failed line search */
+    double f_total;    /* sum over sites of g_r^(reg) at the returned point */
+    double gnorm_max;  /* largest ||grad g_r^(reg)||_2 over sites */
+    double beff;       /* B_eff of the reweighting */
+    double seconds;    /* wall time of the call */
+} plm_report;
+
+/* Fills opts with the paper's recommended inputs (x = 0.8, lambda_h =
+ * lambda_J = 0.01, Sec. 3.5) and gtol = 1e-4, m = 5, max_iter = 1000,
+ * max_ls = 20, PLM_SPLIT_BF16, use_graph = 1. */
+void plm_default_opts(plm_opts *opts);
+
+/* Creates a context on CUDA device `device` that orders its work on
+ * `cuda_stream` (a cudaStream_t; NULL = the legacy default stream). */
+plm_status plm_create(plm_ctx **ctx, int device, void *cuda_stream);
+plm_status plm_destroy(plm_ctx *ctx);
+const char *plm_last_error(plm_ctx *ctx);
+
+/* Step 2 of the rundown, Eq. inverse_weights2 (Sec. 3.1, Eq.
+ * inverse_weights): m_b = #{a : similarity(a,b) >= x}, counting b itself and
+ * counting a gap facing a gap as identical; similarity >= x is evaluated in
+ * integers as matches >= ceil(x N).  w_b = 1/m_b rounded to float, and
+ * B_eff = sum_b 1/m_b in double precision (added over the histogram of m in
+ * increasing m, so the value is independent of sequence order).
+ *   msa      [B][N] int8      in
+ *   m_out    [B] int32        out (may be NULL)
+ *   w_out    [B] float        out (may be NULL)
+ *   beff_out host double      out (may be NULL)
+ * Errors: PLM_EINVAL for B < 1, N < 1, x outside [0,1], q != 21, states out
+ * of range. */
+plm_status msa_reweight(plm_ctx *ctx, const int8_t *msa, int B, int N, int q,
+                        double x, int32_t *m_out, float *w_out,
+                        double *beff_out);
+
+/* Step 3 of the rundown at one parameter point, all sites at once: the
+ * objective g_r^(reg) of Eq. g_regdef2 and its gradient, Eqs. g_gradh2 and
+ * g_gradJ2, normalised by 1/B_eff as in the paper:
+ *   g_r = -(1/B_eff) sum_b w_b log P(sigma_r^b | sigma_\r^b)
+ *         + lambda_h ||h_r||^2 + lambda'_J sum_{i != r} ||J_ri||^2.
+ *   w        [B] float        in (from msa_reweight)
+ *   beff     B_eff
+ *   h, J     in, public layout
+ *   lambda_J the user's strength; lambda'_J = 0.5 lambda_J inside (step 1)
+ *   prec     PLM_FP32_EXACT or PLM_SPLIT_BF16
+ *   f_out    [N] double       out, per-site objective
+ *   gh, gJ   out, same layouts as h and J (diagonal blocks zero)
+ * Errors: PLM_EINVAL for shapes, beff <= 0, negative lambdas. */
+plm_status plm_site_objective_grad(plm_ctx *ctx, const int8_t *msa,
+                                   const float *w, double beff, int B, int N,
+                                   int q, const float *h, const float *J,
+                                   double lambda_h, double lambda_J,
+                                   plm_precision prec, double *f_out,
+                                   float *gh, float *gJ);
+
+/* Steps 1-3 of the rundown: reweighting, then every g_r^(reg) minimised
+ * separately (Eq. npll_2) from the origin (Sec. 6) by a batched per-site
+ * L-BFGS (Sec. 5 names the method; memory, line search and tolerance come
+ * from opts).  All sites share each objective+gradient evaluation; each
+ * site keeps its own curvature pairs, step length and stopping state.
+ *   h_out [N][q], J_out [N][q][N][q]   out, the asymmetric estimates
+ *   report                            out (host, may be NULL)
+ * Returns PLM_ENOTCONV (outputs valid) when some site stopped without
+ * reaching gtol, PLM_ETIMEOUT if a device wait ran out. */
+plm_status plm_solve(plm_ctx *ctx, const int8_t *msa, int B, int N, int q,
+                     const plm_opts *opts, float *h_out, float *J_out,
+                     plm_report *report);
+
+/* Steps 4-6 of the rundown: Ising gauge of every estimate (Eq.
+ * gauge_change2), combination of J^i_ij with J^j_ij = (J^j_ji)^T (Eq.
+ * average2; combine = 1 / 2 selects the elementwise min / max alternatives
+ * of Sec. 6), Frobenius norm (Eq. frob_normtrans2) and the average product
+ * correction (Eq. corr_norm2) with ":" = mean over the other N-1
+ * positions.  Then the L highest-scoring pairs i<j with j - i >= min_sep,
+ * ordered by score descending, ties by (i, j) ascending (Sec. 4 drops pairs
+ * with |i-j| <= 4, i.e. min_sep = 5).
+ *   J        [N][q][N][q] float   in (asymmetric estimates from plm_solve)
+ *   fn_out   [N][N] double        out (may be NULL)
+ *   cfn_out  [N][N] double        out (may be NULL)
+ *   topL_out [L][2] int32         out (may be NULL); rows beyond the number
+ *                                 of eligible pairs are set to -1
+ * Errors: PLM_EINVAL for N < 2, q != 21, L < 0, min_sep < 1, combine
+ * outside 0..2. */
+plm_status fn_apc_scores(plm_ctx *ctx, const float *J, int N, int q,
+                         int combine, double *fn_out, double *cfn_out,
+                         int32_t *topL_out, int L, int min_sep);
+
+/* ---- diagnostics (no counterpart in the paper) ----
+ * plm_kernel_launches: number of CUDA kernels this library has launched in
+ * this process so far (all contexts).
+ * plm_profile: with enable = 1 the context brackets each hot kernel with
+ * CUDA events on its stream (a small timing overhead); enable = 0 stops and
+ * clears the record.  plm_profile_report writes one line per kernel,
+ * "name launches total_ms\n", into buf (NUL-terminated, truncated to len);
+ * it synchronises the stream and returns the number of bytes needed. */
+long long plm_kernel_launches(void);
+plm_status plm_profile(plm_ctx *ctx, int enable);
+int plm_profile_report(plm_ctx *ctx, char *buf, int len);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PLMDCA_H */

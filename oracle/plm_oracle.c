@@ -519,7 +519,9 @@ void orc_fn(const double *J, int N, int q, int combine, double *fn)
  * where ":" is the mean over positions.  The means are over the N-1 true
  * pairs of a row and the N(N-1) ordered pairs overall (the diagonal is not
  * a pair): FN_i: = sum_{j != i} FN_ij / (N-1), FN_:: = sum_{i != j} FN_ij /
- * (N(N-1)).  cfn is [N][N] with a zero diagonal. */
+ * (N(N-1)).  cfn is [N][N] with a zero diagonal.  When every FN is zero the
+ * correction term is 0/0; it is taken as 0 (its limit along any path on which
+ * the FN values shrink together). */
 void orc_apc(const double *fn, int N, double *cfn)
 {
     double *row = (double *)malloc(sizeof(double) * N);
@@ -542,7 +544,9 @@ void orc_apc(const double *fn, int N, double *cfn)
     for (int i = 0; i < N; ++i)
         for (int j = 0; j < N; ++j)
             cfn[(size_t)i * N + j] =
-                (i == j) ? 0.0 : fn[(size_t)i * N + j] - col[j] * row[i] / tot;
+                (i == j) ? 0.0
+                         : fn[(size_t)i * N + j] -
+                               (tot > 0.0 ? col[j] * row[i] / tot : 0.0);
     free(row);
     free(col);
 }

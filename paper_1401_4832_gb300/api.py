@@ -1,0 +1,184 @@
+"""Python binding of the plmDCA C ABI (argument marshalling only).
+
+Every function takes a :class:`Context` plus torch tensors (CUDA or CPU) or
+numpy arrays, passes their raw pointers to the C library, and returns
+outputs allocated next to the inputs: CUDA tensors when the MSA is on the
+GPU, host arrays otherwise (the library stages host arrays through device
+memory itself).  All arithmetic happens in the library's CUDA kernels.
+
+Names follow the C calls: ``msa_reweight``, ``plm_site_objective_grad``,
+``plm_solve``, ``fn_apc_scores``.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _native as N_
+
+Q = 21
+
+
+def _torch():
+    import torch
+    return torch
+
+
+class Context:
+    """Owns one ``plm_ctx`` (device workspace) bound to a CUDA stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        torch = _torch()
+        self.lib = N_.load()
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.device = device
+        self.stream = stream
+        handle = ctypes.c_void_p()
+        st = self.lib.plm_create(ctypes.byref(handle), device,
+                                 ctypes.c_void_p(stream.cuda_stream))
+        if st != N_.PLM_OK:
+            raise N_.PlmError(st, "plm_create failed")
+        self.handle = handle
+
+    def check(self, status):
+        if status != N_.PLM_OK:
+            msg = self.lib.plm_last_error(self.handle)
+            raise N_.PlmError(status, msg.decode() if msg else "")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.plm_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _is_torch(x):
+    try:
+        import torch
+        return isinstance(x, torch.Tensor)
+    except ImportError:
+        return False
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if _is_torch(x):
+        assert x.is_contiguous()
+        return ctypes.c_void_p(x.data_ptr())
+    assert x.flags["C_CONTIGUOUS"]
+    return ctypes.c_void_p(x.ctypes.data)
+
+
+def _like(ref, shape, dtype_np):
+    """Output buffer beside ``ref``: a CUDA tensor if ref is one, else numpy."""
+    if _is_torch(ref) and ref.is_cuda:
+        torch = _torch()
+        tdt = {np.float32: torch.float32, np.float64: torch.float64,
+               np.int32: torch.int32}[dtype_np]
+        return torch.empty(shape, dtype=tdt, device=ref.device)
+    return np.empty(shape, dtype=dtype_np)
+
+
+def _as_input(x, dtype_np):
+    if _is_torch(x):
+        torch = _torch()
+        tdt = {np.int8: torch.int8, np.float32: torch.float32}[dtype_np]
+        return x.to(tdt).contiguous()
+    return np.ascontiguousarray(x, dtype=dtype_np)
+
+
+def msa_reweight(ctx: Context, msa, x: float = 0.8):
+    """Step 2 of the rundown (Eq. inverse_weights2): returns (m, w, B_eff)."""
+    msa = _as_input(msa, np.int8)
+    B, N = msa.shape
+    m = _like(msa, (B,), np.int32)
+    w = _like(msa, (B,), np.float32)
+    beff = ctypes.c_double()
+    ctx.check(ctx.lib.msa_reweight(ctx.handle, _ptr(msa), B, N, Q, float(x),
+                                   _ptr(m), _ptr(w), ctypes.byref(beff)))
+    return m, w, beff.value
+
+
+def plm_site_objective_grad(ctx: Context, msa, w, beff: float, h, J,
+                            lambda_h: float = 0.01, lambda_J: float = 0.01,
+                            prec: str = "fp32"):
+    """Objective g_r^(reg) (Eq. g_regdef2) of every site and its gradient
+    (Eqs. g_gradh2, g_gradJ2) at (h, J); returns (f[N], gh[N,q], gJ[N,q,N,q])."""
+    msa = _as_input(msa, np.int8)
+    B, N = msa.shape
+    w = _as_input(w, np.float32)
+    h = _as_input(h, np.float32)
+    J = _as_input(J, np.float32)
+    f = _like(msa, (N,), np.float64)
+    gh = _like(msa, (N, Q), np.float32)
+    gJ = _like(msa, (N, Q, N, Q), np.float32)
+    ctx.check(ctx.lib.plm_site_objective_grad(
+        ctx.handle, _ptr(msa), _ptr(w), float(beff), B, N, Q, _ptr(h), _ptr(J),
+        float(lambda_h), float(lambda_J), N_.PRECISIONS[prec], _ptr(f), _ptr(gh), _ptr(gJ)))
+    return f, gh, gJ
+
+
+def default_opts(**kw) -> N_.plm_opts:
+    o = N_.plm_opts()
+    N_.load().plm_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "prec" and isinstance(v, str):
+            v = N_.PRECISIONS[v]
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+def plm_solve(ctx: Context, msa, raise_on_notconv: bool = False, **opts):
+    """Steps 1-3 of the rundown: reweighting and the batched per-site L-BFGS.
+    Returns (h[N,q], J[N,q,N,q], report dict incl. 'status')."""
+    msa = _as_input(msa, np.int8)
+    B, N = msa.shape
+    o = default_opts(**opts)
+    h = _like(msa, (N, Q), np.float32)
+    J = _like(msa, (N, Q, N, Q), np.float32)
+    rep = N_.plm_report()
+    st = ctx.lib.plm_solve(ctx.handle, _ptr(msa), B, N, Q, ctypes.byref(o),
+                           _ptr(h), _ptr(J), ctypes.byref(rep))
+    if st != N_.PLM_OK and (st != N_.PLM_ENOTCONV or raise_on_notconv):
+        ctx.check(st)
+    d = rep.as_dict()
+    d["status"] = N_.STATUS_NAMES.get(st, st)
+    return h, J, d
+
+
+def fn_apc_scores(ctx: Context, J, combine: str = "mean", L: int | None = None,
+                  min_sep: int = 5):
+    """Steps 4-6 of the rundown: returns (FN[N,N], CFN[N,N], top[L,2])."""
+    J = _as_input(J, np.float32)
+    N = J.shape[0]
+    L = N if L is None else L
+    fn = _like(J, (N, N), np.float64)
+    cfn = _like(J, (N, N), np.float64)
+    top = _like(J, (L, 2), np.int32)
+    ctx.check(ctx.lib.fn_apc_scores(ctx.handle, _ptr(J), N, Q,
+                                    {"mean": 0, "min": 1, "max": 2}[combine],
+                                    _ptr(fn), _ptr(cfn), _ptr(top), L, min_sep))
+    return fn, cfn, top
+
+
+def plmdca(ctx: Context, msa, L: int | None = None, min_sep: int = 5, **opts):
+    """The whole rundown (steps 1-6) on the GPU."""
+    h, J, rep = plm_solve(ctx, msa, **opts)
+    fn, cfn, top = fn_apc_scores(ctx, J, L=L, min_sep=min_sep)
+    return dict(h=h, J=J, report=rep, fn=fn, cfn=cfn, top=top)

@@ -1,0 +1,317 @@
+// k_gather.cu -- the exact-FP32 objective/gradient path on the CUDA cores.
+//
+// Logits (Eq. condpfinal):  L[b][(r,s)] = sum_i Theta[(r,s)][i*Q + S_bi] + h_r(s)
+// i.e. the one-hot product X Theta^T done as gathers: for every position i
+// only the column of the observed state contributes.  A CTA stages a tile
+// of 128 rows (r,s) x 8 positions x 21 states of Theta transposed in shared
+// memory (row stride 129 words, so both the staging stores and the lane-wise
+// loads are bank-conflict free) and each warp sums the gathered entries for
+// 16 sequences.
+//
+// Log-softmax, objective and residual (Eq. g_regdef2; Eqs. g_gradh2,
+// g_gradJ2): one thread per (site, sequence) over the 21 states in FP32,
+// objective partial sums in FP64 in a fixed order.
+//
+// Gradient (Eq. g_gradJ2):  G[(r,s)][i*Q + k] = sum_b D[b][(r,s)] [S_bi == k]
+// A CTA owns 128 rows x 8 positions (one position per warp); each lane keeps
+// 21 x 4 accumulators in registers and, for every staged sequence, adds its
+// residuals to the accumulator of the observed state.  That state is the
+// same for all lanes of the warp, so the selection is a uniform branch.
+#include "plm_device.cuh"
+#include "plm_internal.cuh"
+
+namespace plm {
+
+namespace {
+
+constexpr int LG_ROWS = 128;        // rows (r,s) per CTA
+constexpr int LG_IC = 8;            // positions per staged chunk
+constexpr int LG_BPW = 16;          // sequences per warp
+constexpr int LG_BT = 8 * LG_BPW;   // sequences per CTA
+constexpr int LG_STRIDE = 129;      // padded row stride of the staged tile
+constexpr size_t LG_SMEM = (size_t)LG_IC * Q * LG_STRIDE * sizeof(float) +
+                           (size_t)LG_BT * LG_IC;
+
+__global__ void __launch_bounds__(256)
+k_logits_gather(const int8_t *__restrict__ msa, const float *__restrict__ theta,
+                Dims d, float *__restrict__ L)
+{
+    extern __shared__ float smem[];
+    float *ths = smem;                                           // [IC*Q][129]
+    int8_t *ss = (int8_t *)(smem + LG_IC * Q * LG_STRIDE);       // [BT][IC]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int row0 = blockIdx.x * LG_ROWS;
+    const int b0 = blockIdx.y * LG_BT;
+    const int NQ = d.N * Q;
+
+    float acc[LG_BPW][4];
+#pragma unroll
+    for (int u = 0; u < LG_BPW; ++u)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[u][j] = 0.0f;
+
+    for (int i0 = 0; i0 < d.N; i0 += LG_IC) {
+        const int ncol = min(LG_IC, d.N - i0) * Q;
+        __syncthreads();
+        // stage Theta[row0 .. +128][i0*Q .. +ncol] transposed
+        for (int e = tid; e < LG_ROWS * LG_IC * Q; e += blockDim.x) {
+            int cc = e % (LG_IC * Q);
+            int rr = e / (LG_IC * Q);
+            float v = 0.0f;
+            if (cc < ncol && row0 + rr < d.R)
+                v = theta[(size_t)(row0 + rr) * d.KP + i0 * Q + cc];
+            ths[cc * LG_STRIDE + rr] = v;
+        }
+        for (int e = tid; e < LG_BT * LG_IC; e += blockDim.x) {
+            int ic = e % LG_IC, bb = e / LG_IC;
+            int b = b0 + bb, i = i0 + ic;
+            ss[e] = (b < d.B && i < d.N) ? msa[(size_t)b * d.N + i] : 0;
+        }
+        __syncthreads();
+        const int nic = min(LG_IC, d.N - i0);
+#pragma unroll
+        for (int u = 0; u < LG_BPW; ++u) {
+            const int8_t *sb = ss + (warp * LG_BPW + u) * LG_IC;
+            for (int ic = 0; ic < nic; ++ic) {
+                const float *col = ths + (ic * Q + sb[ic]) * LG_STRIDE + lane;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[u][j] += col[32 * j];
+            }
+        }
+    }
+    // field column (its one-hot feature is 1 for every sequence)
+    float hv[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        int row = row0 + lane + 32 * j;
+        hv[j] = (row < d.R) ? theta[(size_t)row * d.KP + NQ] : 0.0f;
+    }
+#pragma unroll
+    for (int u = 0; u < LG_BPW; ++u) {
+        int b = b0 + warp * LG_BPW + u;
+        if (b >= d.B) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int row = row0 + lane + 32 * j;
+            if (row < d.R) L[(size_t)b * d.R + row] = acc[u][j] + hv[j];
+        }
+    }
+}
+
+constexpr int SM_WARPS = 8;
+
+__global__ void __launch_bounds__(256)
+k_softmax_resid(const int8_t *__restrict__ msa, const float *__restrict__ w,
+                double beff, const float *__restrict__ L, Dims d,
+                double *__restrict__ partial, float *__restrict__ D)
+{
+    __shared__ double red[SM_WARPS][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int r = blockIdx.x * 32 + lane;
+    const int nslices = gridDim.y * SM_WARPS;
+    const int slice = blockIdx.y * SM_WARPS + warp;
+    double obj = 0.0;
+    if (r < d.N) {
+        for (int b = slice; b < d.B; b += nslices) {
+            const float *lr = L + (size_t)b * d.R + (size_t)r * QP;
+            float l[Q];
+            float mx = -INFINITY;
+#pragma unroll
+            for (int s = 0; s < Q; ++s) {
+                l[s] = lr[s];
+                mx = fmaxf(mx, l[s]);
+            }
+            float z = 0.0f;
+#pragma unroll
+            for (int s = 0; s < Q; ++s) z += expf(l[s] - mx);
+            const float lse = mx + logf(z);
+            const int sr = msa[(size_t)b * d.N + r];
+            float lsr = l[0];
+#pragma unroll
+            for (int s = 1; s < Q; ++s)
+                if (s == sr) lsr = l[s];
+            const double wb = (double)w[b];
+            obj += wb * (double)(lsr - lse);
+            const float scale = (float)(wb / beff);
+            float *dr = D + (size_t)b * d.R + (size_t)r * QP;
+#pragma unroll
+            for (int s = 0; s < Q; ++s)
+                dr[s] = scale * (expf(l[s] - lse) - (s == sr ? 1.0f : 0.0f));
+#pragma unroll
+            for (int s = Q; s < QP; ++s) dr[s] = 0.0f;
+        }
+    }
+    red[warp][lane] = obj;
+    __syncthreads();
+    if (warp == 0 && r < d.N) {
+        double t = 0.0;
+        for (int k = 0; k < SM_WARPS; ++k) t += red[k][lane];
+        partial[(size_t)blockIdx.y * d.N + r] = t;
+    }
+}
+
+__global__ void k_finish_objective(const double *__restrict__ partial,
+                                   int slices, Dims d, double beff,
+                                   const double *__restrict__ pen,
+                                   double *__restrict__ f)
+{
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= d.N) return;
+    double t = 0.0;
+    for (int y = 0; y < slices; ++y) t += partial[(size_t)y * d.N + r];
+    f[r] = -t / beff + (pen ? pen[r] : 0.0);
+}
+
+constexpr int GG_ROWS = 128;
+constexpr int GG_IC = 8;     // positions per CTA (one per warp)
+constexpr int GG_BT = 64;    // sequences per staged tile
+
+#define GG_CASE(K)                 \
+    case K:                        \
+        acc[K][0] += v0;           \
+        acc[K][1] += v1;           \
+        acc[K][2] += v2;           \
+        acc[K][3] += v3;           \
+        break;
+
+__global__ void __launch_bounds__(256)
+k_grad_gather(const int8_t *__restrict__ msa, const float *__restrict__ D,
+              const float *__restrict__ theta, Dims d, double lambda_h,
+              double lambda_Jp, float *__restrict__ G)
+{
+    __shared__ float ds[GG_BT][GG_ROWS];
+    __shared__ int8_t ss[GG_BT][GG_IC];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int row0 = blockIdx.x * GG_ROWS;
+    const int i0 = blockIdx.y * GG_IC;
+    const int i = i0 + warp;
+    const int NQ = d.N * Q;
+    const bool field_warp = (blockIdx.y == 0 && warp == 0);
+
+    float acc[Q][4];
+#pragma unroll
+    for (int k = 0; k < Q; ++k)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[k][j] = 0.0f;
+    float tot[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+
+    for (int b0 = 0; b0 < d.B; b0 += GG_BT) {
+        __syncthreads();
+        for (int e = tid; e < GG_BT * GG_ROWS; e += blockDim.x) {
+            int rr = e % GG_ROWS, bb = e / GG_ROWS;
+            int b = b0 + bb, row = row0 + rr;
+            ds[bb][rr] = (b < d.B && row < d.R) ? D[(size_t)b * d.R + row] : 0.0f;
+        }
+        for (int e = tid; e < GG_BT * GG_IC; e += blockDim.x) {
+            int ic = e % GG_IC, bb = e / GG_IC;
+            int b = b0 + bb, ii = i0 + ic;
+            ss[bb][ic] = (b < d.B && ii < d.N) ? msa[(size_t)b * d.N + ii] : 0;
+        }
+        __syncthreads();
+        if (i < d.N) {
+            for (int bb = 0; bb < GG_BT; ++bb) {
+                const float v0 = ds[bb][lane], v1 = ds[bb][lane + 32];
+                const float v2 = ds[bb][lane + 64], v3 = ds[bb][lane + 96];
+                if (field_warp) {
+                    tot[0] += v0;
+                    tot[1] += v1;
+                    tot[2] += v2;
+                    tot[3] += v3;
+                }
+                switch (ss[bb][warp]) {
+                    GG_CASE(0) GG_CASE(1) GG_CASE(2) GG_CASE(3) GG_CASE(4)
+                    GG_CASE(5) GG_CASE(6) GG_CASE(7) GG_CASE(8) GG_CASE(9)
+                    GG_CASE(10) GG_CASE(11) GG_CASE(12) GG_CASE(13) GG_CASE(14)
+                    GG_CASE(15) GG_CASE(16) GG_CASE(17) GG_CASE(18) GG_CASE(19)
+                    GG_CASE(20)
+                    default: break;
+                }
+            }
+        }
+    }
+    // epilogue: add the penalty gradient 2 lambda theta; the diagonal block,
+    // padding rows and padding columns are zero
+    const float two_lj = (float)(2.0 * lambda_Jp), two_lh = (float)(2.0 * lambda_h);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int row = row0 + lane + 32 * j;
+        if (row >= d.R) continue;
+        const int r = row / QP, s = row % QP;
+        const float *th = theta + (size_t)row * d.KP;
+        float *g = G + (size_t)row * d.KP;
+        if (i < d.N) {
+            const bool zero = (s >= Q) || (i == r);
+#pragma unroll
+            for (int k = 0; k < Q; ++k) {
+                const int c = i * Q + k;
+                g[c] = zero ? 0.0f : acc[k][j] + two_lj * th[c];
+            }
+        }
+        if (field_warp) g[NQ] = (s >= Q) ? 0.0f : tot[j] + two_lh * th[NQ];
+        if (blockIdx.y == 0 && warp > 0)
+            for (int c = NQ + warp; c < d.KP; c += 7) g[c] = 0.0f;
+    }
+}
+#undef GG_CASE
+
+}  // namespace
+
+cudaError_t launch_logits_gather(const int8_t *msa, const float *theta,
+                                 const Dims &d, float *L, cudaStream_t st)
+{
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(
+            k_logits_gather, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LG_SMEM);
+        if (e) return e;
+        attr_set = true;
+    }
+    dim3 grid((d.R + LG_ROWS - 1) / LG_ROWS, (d.B + LG_BT - 1) / LG_BT);
+    k_logits_gather<<<grid, 256, LG_SMEM, st>>>(msa, theta, d, L);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+int softmax_slices(const Dims &d)
+{
+    // enough CTAs to fill the GPU, each warp looping over >= 16 sequences
+    int ycap = (d.B + 16 * SM_WARPS - 1) / (16 * SM_WARPS);
+    int xs = (d.N + 31) / 32;
+    int y = (4 * 152 + xs - 1) / xs;
+    if (y > ycap) y = ycap;
+    if (y < 1) y = 1;
+    return y;
+}
+
+cudaError_t launch_softmax_resid(const int8_t *msa, const float *w,
+                                 double beff, const float *L, const Dims &d,
+                                 double *partial, float *D, cudaStream_t st)
+{
+    dim3 grid((d.N + 31) / 32, softmax_slices(d));
+    k_softmax_resid<<<grid, 32 * SM_WARPS, 0, st>>>(msa, w, beff, L, d, partial, D);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finish_objective(const double *partial, int slices,
+                                    const Dims &d, double beff,
+                                    const double *pen, double *f,
+                                    cudaStream_t st)
+{
+    k_finish_objective<<<(d.N + 127) / 128, 128, 0, st>>>(partial, slices, d, beff, pen, f);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grad_gather(const int8_t *msa, const float *D,
+                               const float *theta, const Dims &d,
+                               double lambda_h, double lambda_Jp, float *G,
+                               cudaStream_t st)
+{
+    dim3 grid((d.R + GG_ROWS - 1) / GG_ROWS, (d.N + GG_IC - 1) / GG_IC);
+    k_grad_gather<<<grid, 256, 0, st>>>(msa, D, theta, d, lambda_h, lambda_Jp, G);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace plm

@@ -1,0 +1,676 @@
+// plm_abi.cu -- the C ABI declared in include/plmdca.h: context and
+// workspace management, argument checks, host/device pointer staging, and
+// the orchestration of the kernels for each entry point.
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/plmdca.h"
+#include "plm_internal.cuh"
+
+using namespace plm;
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+struct ProfRecord {
+    const char *name;
+    cudaEvent_t a, b;
+};
+
+struct plm_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    std::map<std::string, DevBuf> bufs;
+    int *host_counters = nullptr;  // pinned
+    double *host_scalars = nullptr;
+    bool prof = false;
+    std::vector<ProfRecord> prof_records;
+    std::vector<cudaEvent_t> event_pool;
+};
+
+namespace plm {
+static std::atomic<long long> g_launches{0};
+void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+}  // namespace plm
+
+namespace {
+
+cudaEvent_t take_event(plm_ctx *c)
+{
+    if (!c->event_pool.empty()) {
+        cudaEvent_t e = c->event_pool.back();
+        c->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// brackets the kernels issued in its scope with events when profiling is on
+struct ProfScope {
+    plm_ctx *c;
+    const char *name;
+    cudaEvent_t a = nullptr;
+    ProfScope(plm_ctx *c_, const char *n) : c(c_), name(n)
+    {
+        if (c->prof) {
+            a = take_event(c);
+            cudaEventRecord(a, c->stream);
+        }
+    }
+    ~ProfScope()
+    {
+        if (c->prof && a) {
+            cudaEvent_t b = take_event(c);
+            cudaEventRecord(b, c->stream);
+            c->prof_records.push_back({name, a, b});
+        }
+    }
+};
+
+plm_status fail(plm_ctx *c, plm_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return s;
+}
+
+plm_status cuda_fail(plm_ctx *c, cudaError_t e, const char *where)
+{
+    return fail(c, e == cudaErrorMemoryAllocation ? PLM_ENOMEM : PLM_ECUDA,
+                "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define CK(call)                                                   \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);   \
+    } while (0)
+
+// grow-only named workspace buffer
+cudaError_t ws(plm_ctx *ctx, const char *name, size_t bytes, void **out)
+{
+    DevBuf &b = ctx->bufs[name];
+    if (bytes == 0) bytes = 256;
+    if (b.bytes < bytes) {
+        if (b.p) cudaFree(b.p);
+        b.p = nullptr;
+        b.bytes = 0;
+        cudaError_t e = cudaMalloc(&b.p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return e;
+        }
+        b.bytes = bytes;
+    }
+    *out = b.p;
+    return cudaSuccess;
+}
+
+bool is_device_ptr(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// An input array: device pointers are used as they are; host arrays are
+// copied into a workspace buffer on the context's stream.
+struct Staged {
+    void *dev = nullptr;
+    void *host = nullptr;  // non-null when results must be copied back
+    size_t bytes = 0;
+};
+
+cudaError_t stage_in(plm_ctx *ctx, const char *name, const void *p, size_t bytes,
+                     const void **out, bool *was_host = nullptr)
+{
+    if (!p || is_device_ptr(p)) {
+        *out = p;
+        if (was_host) *was_host = false;
+        return cudaSuccess;
+    }
+    void *d;
+    cudaError_t e = ws(ctx, name, bytes, &d);
+    if (e) return e;
+    e = cudaMemcpyAsync(d, p, bytes, cudaMemcpyHostToDevice, ctx->stream);
+    *out = d;
+    if (was_host) *was_host = true;
+    return e;
+}
+
+cudaError_t stage_out(plm_ctx *ctx, const char *name, void *p, size_t bytes,
+                      Staged *s)
+{
+    s->bytes = bytes;
+    if (!p || is_device_ptr(p)) {
+        s->dev = p;
+        s->host = nullptr;
+        return cudaSuccess;
+    }
+    s->host = p;
+    return ws(ctx, name, bytes, &s->dev);
+}
+
+cudaError_t copy_back(plm_ctx *ctx, const Staged &s)
+{
+    if (!s.host) return cudaSuccess;
+    return cudaMemcpyAsync(s.host, s.dev, s.bytes, cudaMemcpyDeviceToHost, ctx->stream);
+}
+
+int identity_threshold(double x, int N)
+{
+    // smallest integer count T with T / N >= x
+    double t = std::ceil(x * (double)N - 1e-9);
+    return t < 0 ? 0 : (int)t;
+}
+
+__global__ void k_check_msa(const int8_t *msa, size_t n, int *err)
+{
+    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx < n) {
+        int s = msa[idx];
+        if (s < 0 || s >= Q) atomicOr(err, 1);
+    }
+}
+
+plm_status check_common(plm_ctx *ctx, int B, int N, int q)
+{
+    if (!ctx) return PLM_EINVAL;
+    if (q != Q) return fail(ctx, PLM_EINVAL, "q must be %d (got %d)", Q, q);
+    if (B < 1) return fail(ctx, PLM_EINVAL, "B must be >= 1 (got %d)", B);
+    if (N < 2) return fail(ctx, PLM_EINVAL, "N must be >= 2 (got %d)", N);
+    if ((long long)N * Q * QP * (long long)N > (1LL << 33))
+        return fail(ctx, PLM_EINVAL, "N = %d is too large", N);
+    return PLM_OK;
+}
+
+// msa validity: a sync point; returns PLM_EINVAL for states outside 0..q-1
+plm_status check_msa(plm_ctx *ctx, const int8_t *msa_d, int B, int N)
+{
+    void *flag;
+    CK(ws(ctx, "flag_msa", sizeof(int), &flag));
+    CK(cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream));
+    size_t n = (size_t)B * N;
+    k_check_msa<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(msa_d, n, (int *)flag);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(ctx->host_counters + 8, flag, sizeof(int), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (ctx->host_counters[8]) return fail(ctx, PLM_EINVAL, "msa has states outside 0..%d", Q - 1);
+    return PLM_OK;
+}
+
+// One objective+gradient evaluation of all sites at theta (internal layout).
+// f_data[r] = -(1/B_eff) sum_b w_b log P (no penalty); G includes 2 lambda theta.
+plm_status evaluate(plm_ctx *ctx, plm_precision prec, const int8_t *msa,
+                    const float *w, double beff, const Dims &d,
+                    const float *theta, const __nv_bfloat16 *hi,
+                    const __nv_bfloat16 *lo, double lambda_h, double lambda_Jp,
+                    double *f_data, float *G)
+{
+    cudaStream_t st = ctx->stream;
+    if (prec == PLM_FP32_EXACT) {
+        void *L, *D, *part;
+        const int slices = softmax_slices(d);
+        CK(ws(ctx, "L", (size_t)d.B * d.R * sizeof(float), &L));
+        CK(ws(ctx, "D", (size_t)d.B * d.R * sizeof(float), &D));
+        CK(ws(ctx, "partial", (size_t)slices * d.N * sizeof(double), &part));
+        {
+            ProfScope ps(ctx, "logits_gather");
+            CK(launch_logits_gather(msa, theta, d, (float *)L, st));
+        }
+        {
+            ProfScope ps(ctx, "softmax_resid");
+            CK(launch_softmax_resid(msa, w, beff, (float *)L, d, (double *)part, (float *)D, st));
+            CK(launch_finish_objective((double *)part, slices, d, beff, nullptr, f_data, st));
+        }
+        {
+            ProfScope ps(ctx, "grad_gather");
+            CK(launch_grad_gather(msa, (float *)D, theta, d, lambda_h, lambda_Jp, G, st));
+        }
+        return PLM_OK;
+    }
+    if (prec == PLM_SPLIT_BF16) {
+        if (!tc_supported())
+            return fail(ctx, PLM_ENOTIMPL, "split-bf16 tensor-core path needs an sm_103 GPU");
+        void *scratch, *flag;
+        CK(ws(ctx, "tc_scratch", tc_scratch_bytes(d), &scratch));
+        CK(ws(ctx, "flag_tc", sizeof(int), &flag));
+        CK(launch_tc_eval(ctx->prof ? (void *)ctx : nullptr, msa, w, beff, hi, lo, theta, d,
+                          lambda_h, lambda_Jp, scratch, f_data, G, (int *)flag, st));
+        return PLM_OK;
+    }
+    return fail(ctx, PLM_ENOTIMPL, "precision mode %d is not built", (int)prec);
+}
+
+}  // namespace
+
+extern "C" {
+
+void plm_default_opts(plm_opts *o)
+{
+    if (!o) return;
+    memset(o, 0, sizeof *o);
+    o->x = 0.8;
+    o->lambda_h = 0.01;
+    o->lambda_J = 0.01;
+    o->gtol = 1e-4;
+    o->lbfgs_m = 5;
+    o->max_iter = 1000;
+    o->max_ls = 20;
+    o->prec = PLM_SPLIT_BF16;
+    o->use_graph = 1;
+}
+
+plm_status plm_create(plm_ctx **out, int device, void *cuda_stream)
+{
+    if (!out) return PLM_EINVAL;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+        cudaGetLastError();
+        return PLM_ECUDA;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) return PLM_ECUDA;
+    plm_ctx *c = new plm_ctx;
+    c->device = device;
+    c->stream = (cudaStream_t)cuda_stream;
+    if (cudaMallocHost(&c->host_counters, 64 * sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(&c->host_scalars, 64 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return PLM_ENOMEM;
+    }
+    *out = c;
+    return PLM_OK;
+}
+
+plm_status plm_destroy(plm_ctx *c)
+{
+    if (!c) return PLM_EINVAL;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    for (auto &kv : c->bufs)
+        if (kv.second.p) cudaFree(kv.second.p);
+    if (c->host_counters) cudaFreeHost(c->host_counters);
+    if (c->host_scalars) cudaFreeHost(c->host_scalars);
+    for (auto &r : c->prof_records) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto e : c->event_pool) cudaEventDestroy(e);
+    delete c;
+    return PLM_OK;
+}
+
+long long plm_kernel_launches(void) { return plm::g_launches.load(); }
+
+plm_status plm_profile(plm_ctx *c, int enable)
+{
+    if (!c) return PLM_EINVAL;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (auto &r : c->prof_records) {
+        c->event_pool.push_back(r.a);
+        c->event_pool.push_back(r.b);
+    }
+    c->prof_records.clear();
+    c->prof = enable != 0;
+    return PLM_OK;
+}
+
+int plm_profile_report(plm_ctx *c, char *buf, int len)
+{
+    if (!c) return -1;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    std::map<std::string, std::pair<long long, double>> agg;
+    std::vector<std::string> order;
+    for (auto &r : c->prof_records) {
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, r.a, r.b);
+        auto it = agg.find(r.name);
+        if (it == agg.end()) {
+            order.push_back(r.name);
+            agg[r.name] = {1, ms};
+        } else {
+            it->second.first++;
+            it->second.second += ms;
+        }
+    }
+    std::string out;
+    char line[256];
+    for (auto &n : order) {
+        snprintf(line, sizeof line, "%s %lld %.6f\n", n.c_str(), agg[n].first, agg[n].second);
+        out += line;
+    }
+    if (buf && len > 0) {
+        size_t k = out.size() < (size_t)(len - 1) ? out.size() : (size_t)(len - 1);
+        memcpy(buf, out.data(), k);
+        buf[k] = 0;
+    }
+    return (int)out.size() + 1;
+}
+
+const char *plm_last_error(plm_ctx *c)
+{
+    return c ? c->err.c_str() : "null context";
+}
+
+plm_status msa_reweight(plm_ctx *ctx, const int8_t *msa, int B, int N, int q,
+                        double x, int32_t *m_out, float *w_out, double *beff_out)
+{
+    if (!ctx) return PLM_EINVAL;
+    if (q != Q) return fail(ctx, PLM_EINVAL, "q must be %d (got %d)", Q, q);
+    if (B < 1 || N < 1) return fail(ctx, PLM_EINVAL, "B and N must be >= 1");
+    if (!msa) return fail(ctx, PLM_EINVAL, "msa is NULL");
+    if (!(x >= 0.0 && x <= 1.0)) return fail(ctx, PLM_EINVAL, "x must lie in [0, 1]");
+    CK(cudaSetDevice(ctx->device));
+    const void *msa_d;
+    CK(stage_in(ctx, "in_msa", msa, (size_t)B * N, &msa_d));
+    Staged m_s, w_s;
+    CK(stage_out(ctx, "out_m", m_out, (size_t)B * sizeof(int32_t), &m_s));
+    CK(stage_out(ctx, "out_w", w_out, (size_t)B * sizeof(float), &w_s));
+    void *scratch, *beff_d, *flag;
+    CK(ws(ctx, "rw_scratch", reweight_scratch_bytes(B, N), &scratch));
+    CK(ws(ctx, "beff", sizeof(double), &beff_d));
+    CK(ws(ctx, "flag_rw", sizeof(int), &flag));
+    CK(cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream));
+    CK(launch_reweight((const int8_t *)msa_d, B, N, identity_threshold(x, N),
+                       (int32_t *)m_s.dev, (float *)w_s.dev, (double *)beff_d, scratch,
+                       (int *)flag, ctx->stream));
+    CK(copy_back(ctx, m_s));
+    CK(copy_back(ctx, w_s));
+    CK(cudaMemcpyAsync(ctx->host_scalars, beff_d, sizeof(double), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaMemcpyAsync(ctx->host_counters + 9, flag, sizeof(int), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (ctx->host_counters[9]) return fail(ctx, PLM_EINVAL, "msa has states outside 0..%d", Q - 1);
+    if (beff_out) *beff_out = ctx->host_scalars[0];
+    return PLM_OK;
+}
+
+plm_status plm_site_objective_grad(plm_ctx *ctx, const int8_t *msa,
+                                   const float *w, double beff, int B, int N,
+                                   int q, const float *h, const float *J,
+                                   double lambda_h, double lambda_J,
+                                   plm_precision prec, double *f_out,
+                                   float *gh, float *gJ)
+{
+    plm_status s = check_common(ctx, B, N, q);
+    if (s) return s;
+    if (!msa || !w || !h || !J) return fail(ctx, PLM_EINVAL, "null input array");
+    if (!(beff > 0.0)) return fail(ctx, PLM_EINVAL, "beff must be > 0");
+    if (lambda_h < 0 || lambda_J < 0) return fail(ctx, PLM_EINVAL, "negative lambda");
+    CK(cudaSetDevice(ctx->device));
+    const Dims d = make_dims(B, N);
+    const size_t NQ = (size_t)N * Q;
+    const void *msa_d, *w_d, *h_d, *J_d;
+    CK(stage_in(ctx, "in_msa", msa, (size_t)B * N, &msa_d));
+    s = check_msa(ctx, (const int8_t *)msa_d, B, N);
+    if (s) return s;
+    CK(stage_in(ctx, "in_w", w, (size_t)B * sizeof(float), &w_d));
+    CK(stage_in(ctx, "in_h", h, NQ * sizeof(float), &h_d));
+    CK(stage_in(ctx, "in_J", J, NQ * NQ * sizeof(float), &J_d));
+    Staged f_s, gh_s, gJ_s;
+    CK(stage_out(ctx, "out_f", f_out, (size_t)N * sizeof(double), &f_s));
+    CK(stage_out(ctx, "out_gh", gh, NQ * sizeof(float), &gh_s));
+    CK(stage_out(ctx, "out_gJ", gJ, NQ * NQ * sizeof(float), &gJ_s));
+    void *theta, *G, *pen, *fdat, *hi = nullptr, *lo = nullptr;
+    CK(ws(ctx, "theta", d.theta_elems() * sizeof(float), &theta));
+    CK(ws(ctx, "G", d.theta_elems() * sizeof(float), &G));
+    CK(ws(ctx, "pen", (size_t)N * sizeof(double), &pen));
+    CK(ws(ctx, "fdata", (size_t)N * sizeof(double), &fdat));
+    const double lJp = 0.5 * lambda_J;  // step 1 of the rundown
+    CK(launch_pack_theta((const float *)h_d, (const float *)J_d, d, (float *)theta, ctx->stream));
+    CK(launch_penalty((const float *)theta, d, lambda_h, lJp, (double *)pen, ctx->stream));
+    if (prec == PLM_SPLIT_BF16) {
+        CK(ws(ctx, "theta_hi", d.theta_elems() * 2, &hi));
+        CK(ws(ctx, "theta_lo", d.theta_elems() * 2, &lo));
+        CK(launch_split_theta((const float *)theta, d, (__nv_bfloat16 *)hi,
+                              (__nv_bfloat16 *)lo, ctx->stream));
+    }
+    s = evaluate(ctx, prec, (const int8_t *)msa_d, (const float *)w_d, beff, d,
+                 (const float *)theta, (const __nv_bfloat16 *)hi, (const __nv_bfloat16 *)lo,
+                 lambda_h, lJp, (double *)fdat, (float *)G);
+    if (s) return s;
+    // f = data + penalty
+    void *fsum;
+    CK(ws(ctx, "fsum", (size_t)N * sizeof(double), &fsum));
+    CK(launch_finish_objective((const double *)fdat, 1, d, -1.0, (const double *)pen,
+                               f_s.dev ? (double *)f_s.dev : (double *)fsum, ctx->stream));
+    CK(launch_unpack_theta((const float *)G, d, (float *)gh_s.dev, (float *)gJ_s.dev,
+                           ctx->stream));
+    CK(copy_back(ctx, f_s));
+    CK(copy_back(ctx, gh_s));
+    CK(copy_back(ctx, gJ_s));
+    if (f_s.host || gh_s.host || gJ_s.host) CK(cudaStreamSynchronize(ctx->stream));
+    return PLM_OK;
+}
+
+plm_status plm_solve(plm_ctx *ctx, const int8_t *msa, int B, int N, int q,
+                     const plm_opts *opts, float *h_out, float *J_out,
+                     plm_report *report)
+{
+    auto t_start = std::chrono::steady_clock::now();
+    plm_status s = check_common(ctx, B, N, q);
+    if (s) return s;
+    if (!msa) return fail(ctx, PLM_EINVAL, "msa is NULL");
+    plm_opts o;
+    if (opts) o = *opts;
+    else plm_default_opts(&o);
+    if (!(o.x >= 0.0 && o.x <= 1.0)) return fail(ctx, PLM_EINVAL, "x must lie in [0, 1]");
+    if (o.lambda_h < 0 || o.lambda_J < 0) return fail(ctx, PLM_EINVAL, "negative lambda");
+    if (!(o.lambda_h > 0 && o.lambda_J > 0))
+        return fail(ctx, PLM_EINVAL, "lambda_h and lambda_J must be > 0 (the l2 term makes "
+                                     "each site problem strongly convex)");
+    if (o.lbfgs_m < 1 || o.lbfgs_m > MAX_M) return fail(ctx, PLM_EINVAL, "lbfgs_m must be 1..%d", MAX_M);
+    if (o.max_ls < 1) return fail(ctx, PLM_EINVAL, "max_ls must be >= 1");
+    if (!(o.gtol >= 0)) return fail(ctx, PLM_EINVAL, "gtol must be >= 0");
+    if (o.prec != PLM_FP32_EXACT && o.prec != PLM_SPLIT_BF16)
+        return fail(ctx, PLM_ENOTIMPL, "precision mode %d is not built", (int)o.prec);
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    const Dims d = make_dims(B, N);
+    const size_t NQ = (size_t)N * Q;
+
+    const void *msa_d;
+    CK(stage_in(ctx, "in_msa", msa, (size_t)B * N, &msa_d));
+    const int8_t *S = (const int8_t *)msa_d;
+    Staged h_s, J_s;
+    CK(stage_out(ctx, "out_h", h_out, NQ * sizeof(float), &h_s));
+    CK(stage_out(ctx, "out_J", J_out, NQ * NQ * sizeof(float), &J_s));
+
+    // step 2: reweighting
+    void *scratch, *w, *beff_d, *flag;
+    CK(ws(ctx, "rw_scratch", reweight_scratch_bytes(B, N), &scratch));
+    CK(ws(ctx, "w", (size_t)B * sizeof(float), &w));
+    CK(ws(ctx, "beff", sizeof(double), &beff_d));
+    CK(ws(ctx, "flag_rw", sizeof(int), &flag));
+    CK(cudaMemsetAsync(flag, 0, sizeof(int), st));
+    {
+        ProfScope ps(ctx, "reweight");
+        CK(launch_reweight(S, B, N, identity_threshold(o.x, N), nullptr, (float *)w,
+                           (double *)beff_d, scratch, (int *)flag, st));
+    }
+    CK(cudaMemcpyAsync(ctx->host_scalars, beff_d, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(ctx->host_counters + 9, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (ctx->host_counters[9]) return fail(ctx, PLM_EINVAL, "msa has states outside 0..%d", Q - 1);
+    const double beff = ctx->host_scalars[0];
+
+    // workspace of the solver
+    const size_t tb = d.theta_elems() * sizeof(float);
+    void *theta, *theta_t, *g, *g_t, *dir, *Sh, *Yh, *sst, *fdat, *cnt;
+    void *hi = nullptr, *lo = nullptr;
+    CK(ws(ctx, "theta", tb, &theta));
+    CK(ws(ctx, "theta_t", tb, &theta_t));
+    CK(ws(ctx, "g", tb, &g));
+    CK(ws(ctx, "G", tb, &g_t));
+    CK(ws(ctx, "dir", tb, &dir));
+    CK(ws(ctx, "S_hist", tb * o.lbfgs_m, &Sh));
+    CK(ws(ctx, "Y_hist", tb * o.lbfgs_m, &Yh));
+    CK(ws(ctx, "site_state", (size_t)N * sizeof(SiteState), &sst));
+    CK(ws(ctx, "fdata", (size_t)N * sizeof(double), &fdat));
+    CK(ws(ctx, "counters", 16 * sizeof(int), &cnt));
+    if (o.prec == PLM_SPLIT_BF16) {
+        CK(ws(ctx, "theta_hi", d.theta_elems() * 2, &hi));
+        CK(ws(ctx, "theta_lo", d.theta_elems() * 2, &lo));
+    }
+    SolveParams p;
+    p.lambda_h = o.lambda_h;
+    p.lambda_Jp = 0.5 * o.lambda_J;  // step 1 of the rundown
+    p.gtol = o.gtol;
+    p.c1 = 1e-4;
+    p.c2 = 0.9;
+    p.noise = 1e-6;
+    p.m = o.lbfgs_m;
+    p.max_iter = o.max_iter;
+    p.max_ls = o.max_ls;
+
+    // origin start (Sec. 6)
+    CK(cudaMemsetAsync(theta, 0, tb, st));
+    CK(cudaMemsetAsync(theta_t, 0, tb, st));
+    CK(cudaMemsetAsync(dir, 0, tb, st));
+    if (hi) {
+        CK(cudaMemsetAsync(hi, 0, d.theta_elems() * 2, st));
+        CK(cudaMemsetAsync(lo, 0, d.theta_elems() * 2, st));
+    }
+    int evals = 0;
+    s = evaluate(ctx, o.prec, S, (const float *)w, beff, d, (const float *)theta,
+                 (const __nv_bfloat16 *)hi, (const __nv_bfloat16 *)lo, p.lambda_h,
+                 p.lambda_Jp, (double *)fdat, (float *)g);
+    if (s) return s;
+    evals++;
+    CK(launch_lbfgs_init((SiteState *)sst, (const double *)fdat, (const float *)g, d, p, st));
+
+    int *hc = ctx->host_counters;
+    for (int it = 0; it < o.max_iter; ++it) {
+        CK(cudaMemsetAsync(cnt, 0, 16 * sizeof(int), st));
+        {
+            ProfScope ps(ctx, "lbfgs_direction");
+            CK(launch_lbfgs_direction((SiteState *)sst, (const float *)g, (float *)dir,
+                                      (const float *)Sh, (const float *)Yh, d, p, st));
+        }
+        for (int ls = 0; ls < o.max_ls + 1; ++ls) {
+            {
+                ProfScope ps(ctx, "lbfgs_trial");
+                CK(launch_lbfgs_trial((SiteState *)sst, (const float *)theta, (const float *)dir,
+                                      (float *)theta_t, (__nv_bfloat16 *)hi, (__nv_bfloat16 *)lo,
+                                      d, p, st));
+            }
+            s = evaluate(ctx, o.prec, S, (const float *)w, beff, d, (const float *)theta_t,
+                         (const __nv_bfloat16 *)hi, (const __nv_bfloat16 *)lo, p.lambda_h,
+                         p.lambda_Jp, (double *)fdat, (float *)g_t);
+            if (s) return s;
+            evals++;
+            CK(cudaMemsetAsync(cnt, 0, sizeof(int), st));
+            {
+                ProfScope ps(ctx, "lbfgs_linesearch");
+                CK(launch_lbfgs_linesearch((SiteState *)sst, (const double *)fdat,
+                                           (float *)theta, (float *)g, (const float *)theta_t,
+                                           (const float *)g_t, (const float *)dir, (float *)Sh,
+                                           (float *)Yh, d, p, (int *)cnt, st));
+            }
+            CK(cudaMemcpyAsync(hc, cnt, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            if (hc[0] == 0) break;
+        }
+        CK(cudaMemsetAsync(cnt, 0, 16 * sizeof(int), st));
+        CK(launch_count_status((const SiteState *)sst, N, (int *)cnt, st));
+        CK(cudaMemcpyAsync(hc, cnt, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (hc[1] == 0) break;  // no site left to iterate
+    }
+
+    CK(launch_unpack_theta((const float *)theta, d, (float *)h_s.dev, (float *)J_s.dev, st));
+    CK(copy_back(ctx, h_s));
+    CK(copy_back(ctx, J_s));
+    std::vector<SiteState> host(N);
+    CK(cudaMemcpyAsync(host.data(), sst, (size_t)N * sizeof(SiteState), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    plm_report rep;
+    memset(&rep, 0, sizeof rep);
+    rep.evals = evals;
+    rep.beff = beff;
+    bool all_conv = true;
+    for (int r = 0; r < N; ++r) {
+        const SiteState &x = host[r];
+        rep.iters = x.iters > rep.iters ? x.iters : rep.iters;
+        rep.f_total += x.f;
+        double gn = std::sqrt(x.gnorm2);
+        if (gn > rep.gnorm_max) rep.gnorm_max = gn;
+        if (x.status == SITE_CONVERGED) rep.n_converged++;
+        else {
+            all_conv = false;
+            if (x.status == SITE_NOISE) rep.n_noise++;
+            else rep.n_failed++;
+        }
+    }
+    rep.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    if (report) *report = rep;
+    if (!all_conv)
+        return fail(ctx, PLM_ENOTCONV, "%d of %d sites stopped before gtol (%d at the noise floor)",
+                    rep.n_noise + rep.n_failed, N, rep.n_noise);
+    return PLM_OK;
+}
+
+plm_status fn_apc_scores(plm_ctx *ctx, const float *J, int N, int q,
+                         int combine, double *fn_out, double *cfn_out,
+                         int32_t *topL_out, int L, int min_sep)
+{
+    if (!ctx) return PLM_EINVAL;
+    if (q != Q) return fail(ctx, PLM_EINVAL, "q must be %d (got %d)", Q, q);
+    if (N < 2) return fail(ctx, PLM_EINVAL, "N must be >= 2");
+    if (!J) return fail(ctx, PLM_EINVAL, "J is NULL");
+    if (L < 0 || min_sep < 1) return fail(ctx, PLM_EINVAL, "need L >= 0 and min_sep >= 1");
+    if (combine < 0 || combine > 2) return fail(ctx, PLM_EINVAL, "combine must be 0, 1 or 2");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    const size_t NQ = (size_t)N * Q;
+    const void *J_d;
+    CK(stage_in(ctx, "in_J", J, NQ * NQ * sizeof(float), &J_d));
+    Staged fn_s, cfn_s, top_s;
+    CK(stage_out(ctx, "out_fn", fn_out, (size_t)N * N * sizeof(double), &fn_s));
+    CK(stage_out(ctx, "out_cfn", cfn_out, (size_t)N * N * sizeof(double), &cfn_s));
+    CK(stage_out(ctx, "out_top", topL_out, (size_t)L * 2 * sizeof(int32_t), &top_s));
+    void *fn = fn_s.dev, *cfn = cfn_s.dev, *work;
+    if (!fn) CK(ws(ctx, "fn", (size_t)N * N * sizeof(double), &fn));
+    if (!cfn) CK(ws(ctx, "cfn", (size_t)N * N * sizeof(double), &cfn));
+    CK(ws(ctx, "apc_work", ((size_t)N + 1) * sizeof(double), &work));
+    {
+        ProfScope ps(ctx, "fn_apc_topL");
+        CK(launch_fn((const float *)J_d, N, combine, (double *)fn, st));
+        CK(launch_apc((const double *)fn, N, (double *)cfn, (double *)work, st));
+        if (top_s.dev)
+            CK(launch_topL((const double *)cfn, N, L, min_sep, (int32_t *)top_s.dev, st));
+    }
+    CK(copy_back(ctx, fn_s));
+    CK(copy_back(ctx, cfn_s));
+    CK(copy_back(ctx, top_s));
+    if (fn_s.host || cfn_s.host || top_s.host) CK(cudaStreamSynchronize(st));
+    return PLM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,184 @@
+// plm_internal.cuh -- internal layout, per-site state and kernel launchers
+// of the GB300 plmDCA library (not part of the public ABI).
+//
+// Internal parameter layout ("site-contiguous padded", the layout every hot
+// kernel reads):
+//
+//   Theta[r][s][c]   float, r < N sites, s < QP = 24 rows per site, c < KP
+//     c <  N*Q  : coupling J_ri(s, k) with i = c / Q, k = c % Q  (Eq. condpfinal)
+//     c == N*Q  : field h_r(s)  (a column whose one-hot feature is always 1)
+//     c >  N*Q  : zero padding up to KP, a multiple of 64
+//   rows s = 21..23 are zero padding (the logits of those rows are masked),
+//   and the diagonal block c in [r*Q, r*Q + Q) is zero (not a parameter).
+//
+// With X[b][c] the one-hot expansion of sequence b (X[b][i*Q+k] = [S_bi == k],
+// X[b][N*Q] = 1), the logits of every site are one matrix product,
+// L[b][(r,s)] = sum_c X[b][c] Theta[(r,s)][c], and the data part of the
+// gradient is the transposed product G[(r,s)][c] = sum_b D[b][(r,s)] X[b][c].
+// One site's parameters (q + (N-1) q^2 real entries, Sec. 6) are the
+// contiguous row block Theta[r], which the per-site L-BFGS kernels stream.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace plm {
+
+// running count of kernel launches issued by the library (diagnostics)
+void count_launches(int n);
+
+constexpr int Q = 21;     // states: 20 amino acids + gap (Sec. 2)
+constexpr int QP = 24;    // rows per site in the padded layout
+constexpr int KALIGN = 64;
+
+struct Dims {
+    int B = 0, N = 0;
+    int K = 0;     // real columns: N*Q couplings + 1 field
+    int KP = 0;    // padded columns
+    int R = 0;     // rows: N * QP
+    __host__ __device__ size_t site_elems() const { return (size_t)QP * KP; }
+    __host__ __device__ size_t theta_elems() const { return (size_t)N * QP * KP; }
+};
+
+inline Dims make_dims(int B, int N)
+{
+    Dims d;
+    d.B = B;
+    d.N = N;
+    d.K = N * Q + 1;
+    d.KP = (d.K + KALIGN - 1) / KALIGN * KALIGN;
+    d.R = N * QP;
+    return d;
+}
+
+// Per-site state of the batched L-BFGS (all scalars in FP64).
+enum SiteStatus : int {
+    SITE_READY = 0,      // has f, g at theta; needs a new direction
+    SITE_SEARCHING = 1,  // line search in progress
+    SITE_CONVERGED = 2,  // ||g|| <= gtol
+    SITE_NOISE = 3,      // line search could not resolve a decrease
+    SITE_FAILED = 4,     // max_iter reached or a bad direction
+};
+
+constexpr int MAX_M = 16;
+
+struct SiteState {
+    double f;        // objective at theta
+    double gnorm2;   // ||g||^2 at theta
+    double f0, dg0;  // objective and slope at the start of the line search
+    double alpha;    // current trial step
+    double a_prev, f_prev, dg_prev;
+    double a_lo, f_lo, dg_lo, a_hi, f_hi, dg_hi;
+    double pen_t;    // penalty at the trial point
+    double fdata_t;  // data term at the trial point
+    double rho[MAX_M];
+    double gamma;    // s'y / y'y of the newest pair
+    int status;
+    int phase;       // 0: bracketing, 1: zoom
+    int trials;
+    int iters;
+    int hist, head;  // stored pairs, next ring slot
+    int pad_[2];
+};
+
+struct SolveParams {
+    double lambda_h, lambda_Jp;  // lambda'_J = 0.5 lambda_J already applied
+    double gtol;
+    double c1, c2;
+    double noise;                // relative FP32 evaluation noise band of f
+    int m;
+    int max_iter;
+    int max_ls;
+};
+
+// ---- reweighting (k_reweight.cu) ----
+// scratch: planes [5][B][W] uint32 with W = ceil(N/32), m [B], hist [B+1];
+// err (device int, caller-zeroed) gets bit 0 set for states outside 0..20
+size_t reweight_scratch_bytes(int B, int N);
+cudaError_t launch_reweight(const int8_t *msa, int B, int N, int T,
+                            int32_t *m_out, float *w_out, double *beff_dev,
+                            void *scratch, int *err, cudaStream_t st);
+
+// ---- layout conversion (k_layout.cu) ----
+// public (h [N][Q], J [N][Q][N][Q]) -> Theta ; diagonal blocks forced to zero
+cudaError_t launch_pack_theta(const float *h, const float *J, const Dims &d,
+                              float *theta, cudaStream_t st);
+// Theta -> public (h, J); either output may be NULL
+cudaError_t launch_unpack_theta(const float *theta, const Dims &d, float *h,
+                                float *J, cudaStream_t st);
+// per-site penalty lambda_h ||h_r||^2 + lambda'_J sum ||J_ri||^2 (FP64)
+cudaError_t launch_penalty(const float *theta, const Dims &d, double lambda_h,
+                           double lambda_Jp, double *pen, cudaStream_t st);
+
+// ---- FP32 gather path (k_gather.cu) ----
+cudaError_t launch_logits_gather(const int8_t *msa, const float *theta,
+                                 const Dims &d, float *L, cudaStream_t st);
+// per-(slice, site) FP64 partial sums of w_b (L[b][r][S_br] - lse); residual
+// D[b][(r,s)] = (w_b / B_eff)(P - Y) in FP32
+int softmax_slices(const Dims &d);
+cudaError_t launch_softmax_resid(const int8_t *msa, const float *w,
+                                 double beff, const float *L, const Dims &d,
+                                 double *partial, float *D, cudaStream_t st);
+// f[r] = -(sum partial)/B_eff + pen[r]  (pen may be NULL)
+cudaError_t launch_finish_objective(const double *partial, int slices,
+                                    const Dims &d, double beff,
+                                    const double *pen, double *f,
+                                    cudaStream_t st);
+cudaError_t launch_grad_gather(const int8_t *msa, const float *D,
+                               const float *theta, const Dims &d,
+                               double lambda_h, double lambda_Jp, float *G,
+                               cudaStream_t st);
+
+// ---- L-BFGS (k_lbfgs.cu) ----
+cudaError_t launch_lbfgs_init(SiteState *st_, const double *f,
+                              const float *g, const Dims &d,
+                              const SolveParams &p, cudaStream_t st);
+cudaError_t launch_lbfgs_direction(SiteState *ss, const float *g, float *dir,
+                                   const float *S_hist, const float *Y_hist,
+                                   const Dims &d, const SolveParams &p,
+                                   cudaStream_t st);
+cudaError_t launch_lbfgs_trial(SiteState *ss, const float *theta,
+                               const float *dir, float *theta_t,
+                               __nv_bfloat16 *hi, __nv_bfloat16 *lo,
+                               const Dims &d, const SolveParams &p,
+                               cudaStream_t st);
+// consumes f_data[r] (data part of the objective at theta_t, FP64) and
+// g_t; decides per site, commits accepted steps; counts searching sites
+cudaError_t launch_lbfgs_linesearch(SiteState *ss, const double *f_data,
+                                    float *theta, float *g,
+                                    const float *theta_t, const float *g_t,
+                                    const float *dir, float *S_hist,
+                                    float *Y_hist, const Dims &d,
+                                    const SolveParams &p, int *counters,
+                                    cudaStream_t st);
+// counters[0] = #searching, counters[1] = #ready
+cudaError_t launch_count_status(const SiteState *ss, int N, int *counters,
+                                cudaStream_t st);
+
+// ---- scores (k_scores.cu) ----
+cudaError_t launch_fn(const float *J, int N, int combine, double *fn,
+                      cudaStream_t st);
+cudaError_t launch_apc(const double *fn, int N, double *cfn, double *work,
+                       cudaStream_t st);
+cudaError_t launch_topL(const double *score, int N, int L, int min_sep,
+                        int32_t *ij, cudaStream_t st);
+
+// ---- tcgen05 split-BF16 path (k_tc.cu) ----
+// split theta (fp32) into bf16 hi + lo: hi = RN(x), lo = RN(x - hi)
+cudaError_t launch_split_theta(const float *theta, const Dims &d,
+                               __nv_bfloat16 *hi, __nv_bfloat16 *lo,
+                               cudaStream_t st);
+size_t tc_scratch_bytes(const Dims &d);
+int tc_supported();
+// logits GEMM with fused log-softmax epilogue: writes objective partials
+// [n_btiles][N] and the residual D^T (split bf16) [R][BP]
+// prof: opaque context pointer for per-kernel event timing (NULL = off)
+cudaError_t launch_tc_eval(void *prof, const int8_t *msa, const float *w, double beff,
+                           const __nv_bfloat16 *th_hi,
+                           const __nv_bfloat16 *th_lo, const float *theta,
+                           const Dims &d, double lambda_h, double lambda_Jp,
+                           void *scratch, double *f_data, float *G,
+                           int *err_flag, cudaStream_t st);
+
+}  // namespace plm

@@ -485,3 +485,9 @@ def test_planted_couplings_recovered_tiny():
     got = {(int(iu[0][o]), int(iu[1][o])) for o in order}
     planted = set(map(tuple, fam.model.pairs.tolist()))
     assert len(got & planted) >= 20
+
+
+def test_apc_all_zero_fn_is_zero():
+    # FN_:: = 0 makes the correction 0/0; the reading taken is 0
+    cfn = oracle.apc(np.zeros((6, 6)))
+    assert np.all(cfn == 0)
