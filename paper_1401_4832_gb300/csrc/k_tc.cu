@@ -1,10 +1,602 @@
-// k_tc.cu -- split-BF16 tensor-core (tcgen05) path: placeholder until the
-// contraction kernels land; only the theta split is implemented.
+// k_tc.cu -- the split-BF16 tensor-core path (tcgen05 + TMA + TMEM, sm_103a).
+//
+// Logits (Eq. condpfinal for every site at once):
+//     L[b][(r,s)] = sum_c X[b][c] Theta[(r,s)][c]
+// with X the one-hot expansion of the MSA (exact in bf16) and Theta split as
+// Theta_hi + Theta_lo, hi = RN_bf16(Theta), lo = RN_bf16(Theta - hi); both
+// products accumulate into one FP32 accumulator in tensor memory.  The one-
+// hot tile of X is written into shared memory by the CTA itself (never
+// stored in HBM); the Theta tiles arrive by TMA.  The epilogue reads the
+// accumulator row by row (one sequence per thread), does the log-softmax
+// over the 21 states of each site, adds w_b (L[S_br] - lse) to a per-site
+// FP64 partial of the objective (Eq. g_regdef2) and writes the residual
+// D = (w_b / B_eff)(P - Y) (Eqs. g_gradh2, g_gradJ2) transposed and split
+// into bf16 hi + lo.
+//
+// Gradient (Eq. g_gradJ2):  G[(r,s)][c] = sum_b D^T[(r,s)][b] X^T[c][b]
+// with D^T hi/lo by TMA and the one-hot X^T tile built in shared memory from
+// the transposed MSA; the epilogue adds 2 lambda Theta and zeroes the
+// diagonal block and the padding.
+//
+// Both kernels: one 128-row output tile per CTA, 3-stage TMA/producer ->
+// MMA pipeline on mbarriers, operands K-major with the 128-byte swizzle,
+// M = 128, K = 16 per instruction.  Warp 0 issues TMA, warp 1 owns the
+// tensor memory and issues the MMAs, warps 2-5 produce the one-hot operand
+// and then run the epilogue.  Every mbarrier wait is bounded: on timeout
+// the CTA records an error code, stops issuing, lets in-flight copies and
+// MMAs finish, frees its tensor memory and exits.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "plm_device.cuh"
 #include "plm_internal.cuh"
 
 namespace plm {
 
+void *prof_start(void *ctx);
+void prof_stop(void *ctx, const char *name, void *start);
+
 namespace {
+
+constexpr int TC_M = 128;
+constexpr int TC_BK = 64;                  // K per stage: 64 bf16 = 128 bytes
+constexpr int STAGES = 3;
+constexpr int LG_SITES = 8;                // sites per logits tile
+constexpr int LG_N = LG_SITES * QP;        // 192 accumulator columns
+constexpr int GR_N = 256;                  // gradient tile columns
+constexpr int TMEM_COLS = 256;
+constexpr int LG_A_BYTES = TC_M * TC_BK * 2;          // 16 KB
+constexpr int LG_B_BYTES = LG_N * TC_BK * 2;          // 24 KB
+constexpr int LG_STAGE = LG_A_BYTES + 2 * LG_B_BYTES;  // 64 KB
+constexpr int GR_A_BYTES = TC_M * TC_BK * 2;          // 16 KB
+constexpr int GR_B_BYTES = GR_N * TC_BK * 2;          // 32 KB
+constexpr int GR_STAGE = 2 * GR_A_BYTES + GR_B_BYTES;  // 64 KB
+constexpr int TC_SMEM = STAGES * 65536 + 1024;         // + alignment slack
+constexpr long long WAIT_CYCLES = 4000000000LL;        // ~2 s at 2 GHz
+
+enum { ERR_TIMEOUT_TMA = 1 << 4, ERR_TIMEOUT_MMA = 1 << 5, ERR_TIMEOUT_PROD = 1 << 6,
+       ERR_TIMEOUT_EPI = 1 << 7 };
+
+// ---------------------------------------------------------------- PTX glue
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase of the given parity.  Gives up (false) when
+// the CTA's abort flag is raised or after WAIT_CYCLES, raising the flag and
+// recording `code` in the global error word.
+__device__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                          int *err, int code)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (clock64() - t0 > WAIT_CYCLES) {
+            *abort_flag = 1;
+            atomicOr(err, code);
+            return false;
+        }
+    }
+}
+
+// wait without the abort short-cut (used to drain in-flight work)
+__device__ bool mbar_drain(uint64_t *bar, uint32_t parity)
+{
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > WAIT_CYCLES) return false;
+    return true;
+}
+
+__device__ __forceinline__ void fence_proxy_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before()
+{
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after()
+{
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar,
+                                            int x, int y)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(dst)),
+                 "r"(ncols)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_relinquish()
+{
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+                 : "memory");
+}
+
+// Shared-memory operand descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (SBO); the leading offset is unused for this layout.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// Instruction descriptor, kind::f16: D f32, A and B bf16, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v)
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+#pragma unroll
+    for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+__device__ __forceinline__ void tmem_wait_ld()
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void epi_bar()
+{
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+}
+
+__device__ __forceinline__ uint8_t *align1024(uint8_t *p)
+{
+    return (uint8_t *)(((uintptr_t)p + 1023) & ~(uintptr_t)1023);
+}
+
+// element (row, pos) of a K-major tile with 128-byte rows, 128B-swizzled
+__device__ __forceinline__ uint32_t swz(int row, int chunk16)
+{
+    return (uint32_t)(row * 128 + ((chunk16 ^ (row & 7)) << 4));
+}
+
+// ---------------------------------------------------------------- logits
+__global__ void __launch_bounds__(192, 1)
+k_tc_logits(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo,
+            const int8_t *__restrict__ msa, const float *__restrict__ w, double inv_beff, Dims d,
+            int BP, __nv_bfloat16 *__restrict__ dt_hi, __nv_bfloat16 *__restrict__ dt_lo,
+            double *__restrict__ partial, int *__restrict__ err)
+{
+    extern __shared__ uint8_t dsmem[];
+    uint8_t *smem = align1024(dsmem);
+    __shared__ __align__(8) uint64_t full_b[STAGES], full_a[STAGES], empty_[STAGES], acc_full;
+    __shared__ uint32_t tmem_sh;
+    __shared__ int abort_sh;
+    __shared__ double red[4][LG_SITES];
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tb = blockIdx.x, tr = blockIdx.y;
+    const int b0 = tb * TC_M;
+    const int r0 = tr * LG_SITES;
+    const int row0 = r0 * QP;
+    const int NK = d.KP / TC_BK;
+    const int NQ = d.N * Q;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full_b[s], 1);
+            mbar_init(&full_a[s], 128);
+            mbar_init(&empty_[s], 1);
+        }
+        mbar_init(&acc_full, 1);
+        abort_sh = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(&tmem_sh, TMEM_COLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_sh;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int issued = 0;
+            for (int kc = 0; kc < NK; ++kc) {
+                const int s = kc % STAGES, n = kc / STAGES;
+                if (n > 0 && !mbar_wait(&empty_[s], (n - 1) & 1, &abort_sh, err, ERR_TIMEOUT_TMA))
+                    break;
+                uint8_t *st = smem + s * LG_STAGE;
+                mbar_expect_tx(&full_b[s], 2 * LG_B_BYTES);
+                tma_load_2d(st + LG_A_BYTES, &tm_hi, &full_b[s], kc * TC_BK, row0);
+                tma_load_2d(st + LG_A_BYTES + LG_B_BYTES, &tm_lo, &full_b[s], kc * TC_BK, row0);
+                issued = kc + 1;
+            }
+            // let the copies still in flight land before the CTA can exit
+            for (int kc = issued - STAGES < 0 ? 0 : issued - STAGES; kc < issued; ++kc)
+                mbar_drain(&full_b[kc % STAGES], (kc / STAGES) & 1);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16(TC_M, LG_N);
+            for (int kc = 0; kc < NK; ++kc) {
+                const int s = kc % STAGES, n = kc / STAGES;
+                if (!mbar_wait(&full_b[s], n & 1, &abort_sh, err, ERR_TIMEOUT_MMA)) break;
+                if (!mbar_wait(&full_a[s], n & 1, &abort_sh, err, ERR_TIMEOUT_MMA)) break;
+                tc_fence_after();
+                uint8_t *st = smem + s * LG_STAGE;
+                const uint32_t a = smem_u32(st);
+                const uint32_t bh = smem_u32(st + LG_A_BYTES);
+                const uint32_t bl = smem_u32(st + LG_A_BYTES + LG_B_BYTES);
+#pragma unroll
+                for (int k = 0; k < TC_BK / 16; ++k)
+                    mma_bf16(tmem, sdesc(a + 32 * k), sdesc(bh + 32 * k), idesc,
+                             (kc > 0 || k > 0) ? 1u : 0u);
+#pragma unroll
+                for (int k = 0; k < TC_BK / 16; ++k)
+                    mma_bf16(tmem, sdesc(a + 32 * k), sdesc(bl + 32 * k), idesc, 1u);
+                mma_commit(&empty_[s]);
+            }
+            mma_commit(&acc_full);  // arrives when every MMA above has completed
+        }
+    } else {
+        // ---- one-hot producer: thread p writes row p of X (sequence b0 + p)
+        const int p = threadIdx.x - 64;
+        const int b = b0 + p;
+        const bool valid = b < d.B;
+        const int8_t *srow = msa + (size_t)(valid ? b : 0) * d.N;
+        for (int kc = 0; kc < NK; ++kc) {
+            const int s = kc % STAGES, n = kc / STAGES;
+            if (n > 0 && !mbar_wait(&empty_[s], (n - 1) & 1, &abort_sh, err, ERR_TIMEOUT_PROD))
+                break;
+            uint8_t *rowp = smem + s * LG_STAGE + p * 128;
+            const uint4 z = make_uint4(0, 0, 0, 0);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) *(uint4 *)(rowp + j * 16) = z;
+            if (valid) {
+                const int c0 = kc * TC_BK;
+                const int i_lo = c0 / Q;
+                const int i_hi = min((c0 + TC_BK - 1) / Q, d.N - 1);
+                for (int i = i_lo; i <= i_hi; ++i) {
+                    const int pos = i * Q + srow[i] - c0;
+                    if (pos >= 0 && pos < TC_BK)
+                        *(uint16_t *)(rowp + ((((pos >> 3) ^ (p & 7)) << 4) | ((pos & 7) << 1))) =
+                            0x3F80;
+                }
+                const int pf = NQ - c0;  // the field column: feature 1
+                if (pf >= 0 && pf < TC_BK)
+                    *(uint16_t *)(rowp + ((((pf >> 3) ^ (p & 7)) << 4) | ((pf & 7) << 1))) = 0x3F80;
+            }
+            fence_proxy_async();
+            mbar_arrive(&full_a[s]);
+        }
+
+        // ---- epilogue: one sequence per thread, its TMEM lane
+        const int q4 = warp & 3;
+        const int er = q4 * 32 + lane;
+        const int eb = b0 + er;
+        const bool ev = eb < d.B;
+        bool ok = mbar_wait(&acc_full, 0, &abort_sh, err, ERR_TIMEOUT_EPI);
+        tc_fence_after();
+        const float wb = ev ? w[eb] : 0.0f;
+        const float scale = (float)((double)wb * inv_beff);
+        const uint32_t tl = tmem + ((uint32_t)(q4 * 32) << 16);
+#pragma unroll 1
+        for (int jp = 0; jp < LG_SITES / 2; ++jp) {
+            float v[48];
+            tmem_ld16(tl + jp * 48, v);
+            tmem_ld16(tl + jp * 48 + 16, v + 16);
+            tmem_ld16(tl + jp * 48 + 32, v + 32);
+            tmem_wait_ld();
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int j = 2 * jp + h;
+                const int r = r0 + j;
+                const float *l = v + 24 * h;
+                double contrib = 0.0;
+                if (r < d.N && ok) {
+                    float mx = l[0];
+#pragma unroll
+                    for (int s = 1; s < Q; ++s) mx = fmaxf(mx, l[s]);
+                    float z = 0.0f;
+#pragma unroll
+                    for (int s = 0; s < Q; ++s) z += __expf(l[s] - mx);
+                    const float lse = mx + __logf(z);
+                    const int sr = ev ? msa[(size_t)eb * d.N + r] : -1;
+                    float lsr = 0.0f;
+#pragma unroll
+                    for (int s = 0; s < Q; ++s)
+                        if (s == sr) lsr = l[s];
+                    if (ev) contrib = (double)wb * (double)(lsr - lse);
+                    const size_t base = (size_t)(row0 + j * QP) * BP + eb;
+#pragma unroll
+                    for (int s = 0; s < QP; ++s) {
+                        float dv = 0.0f;
+                        if (s < Q && ev) dv = scale * (__expf(l[s] - lse) - (s == sr ? 1.0f : 0.0f));
+                        const __nv_bfloat16 hi = __float2bfloat16_rn(dv);
+                        dt_hi[base + (size_t)s * BP] = hi;
+                        dt_lo[base + (size_t)s * BP] = __float2bfloat16_rn(dv - __bfloat162float(hi));
+                    }
+                }
+                contrib = warp_sum_d(contrib);
+                if (lane == 0) red[q4][j] = contrib;
+            }
+        }
+        epi_bar();
+        const int t = threadIdx.x - 64;
+        if (t < LG_SITES && r0 + t < d.N)
+            partial[(size_t)tb * d.N + r0 + t] = ((red[0][t] + red[1][t]) + red[2][t]) + red[3][t];
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        // every MMA must be complete before the tensor memory is released
+        if (lane == 0) mbar_drain(&acc_full, 0);
+        __syncwarp();
+        tc_fence_after();
+        tmem_dealloc(tmem, TMEM_COLS);
+    }
+}
+
+// ---------------------------------------------------------------- gradient
+__global__ void __launch_bounds__(192, 1)
+k_tc_grad(const __grid_constant__ CUtensorMap tm_dhi, const __grid_constant__ CUtensorMap tm_dlo,
+          const int8_t *__restrict__ msaT, const float *__restrict__ theta, Dims d, int BP,
+          float two_lh, float two_lj, float *__restrict__ G, int *__restrict__ err)
+{
+    extern __shared__ uint8_t dsmem[];
+    uint8_t *smem = align1024(dsmem);
+    __shared__ __align__(8) uint64_t full_b[STAGES], full_a[STAGES], empty_[STAGES], acc_full;
+    __shared__ uint32_t tmem_sh;
+    __shared__ int abort_sh;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c0 = blockIdx.x * GR_N;
+    const int rs0 = blockIdx.y * TC_M;
+    const int NK = BP / TC_BK;
+    const int NQ = d.N * Q;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full_b[s], 1);
+            mbar_init(&full_a[s], 128);
+            mbar_init(&empty_[s], 1);
+        }
+        mbar_init(&acc_full, 1);
+        abort_sh = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(&tmem_sh, TMEM_COLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_sh;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int issued = 0;
+            for (int kc = 0; kc < NK; ++kc) {
+                const int s = kc % STAGES, n = kc / STAGES;
+                if (n > 0 && !mbar_wait(&empty_[s], (n - 1) & 1, &abort_sh, err, ERR_TIMEOUT_TMA))
+                    break;
+                uint8_t *st = smem + s * GR_STAGE;
+                mbar_expect_tx(&full_b[s], 2 * GR_A_BYTES);
+                tma_load_2d(st, &tm_dhi, &full_b[s], kc * TC_BK, rs0);
+                tma_load_2d(st + GR_A_BYTES, &tm_dlo, &full_b[s], kc * TC_BK, rs0);
+                issued = kc + 1;
+            }
+            for (int kc = issued - STAGES < 0 ? 0 : issued - STAGES; kc < issued; ++kc)
+                mbar_drain(&full_b[kc % STAGES], (kc / STAGES) & 1);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16(TC_M, GR_N);
+            for (int kc = 0; kc < NK; ++kc) {
+                const int s = kc % STAGES, n = kc / STAGES;
+                if (!mbar_wait(&full_b[s], n & 1, &abort_sh, err, ERR_TIMEOUT_MMA)) break;
+                if (!mbar_wait(&full_a[s], n & 1, &abort_sh, err, ERR_TIMEOUT_MMA)) break;
+                tc_fence_after();
+                uint8_t *st = smem + s * GR_STAGE;
+                const uint32_t ah = smem_u32(st);
+                const uint32_t al = smem_u32(st + GR_A_BYTES);
+                const uint32_t bx = smem_u32(st + 2 * GR_A_BYTES);
+#pragma unroll
+                for (int k = 0; k < TC_BK / 16; ++k)
+                    mma_bf16(tmem, sdesc(ah + 32 * k), sdesc(bx + 32 * k), idesc,
+                             (kc > 0 || k > 0) ? 1u : 0u);
+#pragma unroll
+                for (int k = 0; k < TC_BK / 16; ++k)
+                    mma_bf16(tmem, sdesc(al + 32 * k), sdesc(bx + 32 * k), idesc, 1u);
+                mma_commit(&empty_[s]);
+            }
+            mma_commit(&acc_full);
+        }
+    } else {
+        // ---- one-hot X^T producer: thread p writes rows p and p + 128
+        const int p = threadIdx.x - 64;
+        int src_i[2];
+        uint32_t kk[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int c = c0 + p + 128 * u;
+            int i = 0;
+            uint32_t k = 0xFFu;  // never equals a stored state (0..20, or 0x7F padding)
+            if (c < NQ) {
+                i = c / Q;
+                k = (uint32_t)(c % Q);
+            } else if (c == NQ) {
+                i = d.N;  // the all-ones row of msaT
+                k = 0;
+            }
+            src_i[u] = i;
+            kk[u] = k * 0x01010101u;
+        }
+        for (int kc = 0; kc < NK; ++kc) {
+            const int s = kc % STAGES, n = kc / STAGES;
+            if (n > 0 && !mbar_wait(&empty_[s], (n - 1) & 1, &abort_sh, err, ERR_TIMEOUT_PROD))
+                break;
+            uint8_t *bt = smem + s * GR_STAGE + 2 * GR_A_BYTES;
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int row = p + 128 * u;
+                const uint4 *src = (const uint4 *)(msaT + (size_t)src_i[u] * BP + kc * TC_BK);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {  // 16 sequences per load
+                    const uint4 x = __ldg(src + q);
+                    const uint32_t xs[4] = {x.x, x.y, x.z, x.w};
+                    uint32_t o[8];
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const uint32_t m = __vcmpeq4(xs[t], kk[u]);
+                        o[2 * t] = __byte_perm(m, 0, 0x1100) & 0x3F803F80u;
+                        o[2 * t + 1] = __byte_perm(m, 0, 0x3322) & 0x3F803F80u;
+                    }
+                    *(uint4 *)(bt + swz(row, 2 * q)) = make_uint4(o[0], o[1], o[2], o[3]);
+                    *(uint4 *)(bt + swz(row, 2 * q + 1)) = make_uint4(o[4], o[5], o[6], o[7]);
+                }
+            }
+            fence_proxy_async();
+            mbar_arrive(&full_a[s]);
+        }
+
+        // ---- epilogue: one row (r,s) per thread, 256 columns in chunks of 16
+        const int q4 = warp & 3;
+        const int row = rs0 + q4 * 32 + lane;
+        const bool ok = mbar_wait(&acc_full, 0, &abort_sh, err, ERR_TIMEOUT_EPI);
+        tc_fence_after();
+        const uint32_t tl = tmem + ((uint32_t)(q4 * 32) << 16);
+        const int r = row / QP, sstate = row % QP;
+        const bool row_ok = ok && row < d.R;
+        const bool pad_row = sstate >= Q;
+#pragma unroll 1
+        for (int cc = 0; cc < GR_N / 16; ++cc) {
+            float v[16];
+            tmem_ld16(tl + cc * 16, v);
+            tmem_wait_ld();
+            const int cb = c0 + cc * 16;
+            if (!row_ok || cb >= d.KP) continue;
+            const float4 *th = (const float4 *)(theta + (size_t)row * d.KP + cb);
+            float4 *g = (float4 *)(G + (size_t)row * d.KP + cb);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float4 t = th[q];
+                const float tv[4] = {t.x, t.y, t.z, t.w};
+                float o[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int c = cb + 4 * q + e;
+                    float val;
+                    if (pad_row || c > NQ || (c >= r * Q && c < r * Q + Q)) val = 0.0f;
+                    else if (c == NQ) val = v[4 * q + e] + two_lh * tv[e];
+                    else val = v[4 * q + e] + two_lj * tv[e];
+                    o[e] = val;
+                }
+                g[q] = make_float4(o[0], o[1], o[2], o[3]);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        // every MMA must be complete before the tensor memory is released
+        if (lane == 0) mbar_drain(&acc_full, 0);
+        __syncwarp();
+        tc_fence_after();
+        tmem_dealloc(tmem, TMEM_COLS);
+    }
+}
+
+// ---------------------------------------------------------------- helpers
 __global__ void k_split(const float *__restrict__ theta, size_t n,
                         __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo)
 {
@@ -15,11 +607,59 @@ __global__ void k_split(const float *__restrict__ theta, size_t n,
     hi[idx] = h;
     lo[idx] = __float2bfloat16_rn(x - __bfloat162float(h));
 }
+
+// msaT[i][b] = S[b][i] (b < B), 0x7F beyond B; row N is the constant-feature
+// row (0 for b < B, 0x7F beyond)
+__global__ void k_msa_transpose(const int8_t *__restrict__ msa, Dims d, int BP,
+                                int8_t *__restrict__ msaT)
+{
+    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    size_t total = (size_t)(d.N + 1) * BP;
+    if (idx >= total) return;
+    int i = (int)(idx / BP), b = (int)(idx % BP);
+    int8_t v = 0x7F;
+    if (b < d.B) v = (i < d.N) ? msa[(size_t)b * d.N + i] : 0;
+    msaT[idx] = v;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+// 2D bf16 map over a row-major [outer][inner] array, 128-byte swizzled boxes
+bool make_map(CUtensorMap *m, const void *base, uint64_t inner, uint64_t outer,
+              uint32_t box_inner, uint32_t box_outer)
+{
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {inner, outer};
+    cuuint64_t strides[1] = {inner * 2};
+    cuuint32_t box[2] = {box_inner, box_outer};
+    cuuint32_t es[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides,
+              box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
+
+int padded_B(const Dims &d) { return (d.B + TC_M - 1) / TC_M * TC_M; }
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
 }  // namespace
 
-cudaError_t launch_split_theta(const float *theta, const Dims &d,
-                               __nv_bfloat16 *hi, __nv_bfloat16 *lo,
-                               cudaStream_t st)
+cudaError_t launch_split_theta(const float *theta, const Dims &d, __nv_bfloat16 *hi,
+                               __nv_bfloat16 *lo, cudaStream_t st)
 {
     size_t n = d.theta_elems();
     k_split<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(theta, n, hi, lo);
@@ -27,15 +667,73 @@ cudaError_t launch_split_theta(const float *theta, const Dims &d,
     return cudaGetLastError();
 }
 
-size_t tc_scratch_bytes(const Dims &) { return 256; }
-int tc_supported() { return 0; }
-
-cudaError_t launch_tc_eval(void *, const int8_t *, const float *, double,
-                           const __nv_bfloat16 *, const __nv_bfloat16 *,
-                           const float *, const Dims &, double, double, void *,
-                           double *, float *, int *, cudaStream_t)
+// scratch: D^T hi | D^T lo | partial | msaT
+size_t tc_scratch_bytes(const Dims &d)
 {
-    return cudaErrorNotSupported;
+    const size_t BP = padded_B(d);
+    const size_t nbt = BP / TC_M;
+    return 2 * align256((size_t)d.R * BP * 2) + align256(nbt * d.N * sizeof(double)) +
+           align256((size_t)(d.N + 1) * BP);
+}
+
+int tc_supported()
+{
+    int dev = 0, major = 0, minor = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    return (major == 10 && minor == 3 && encode_fn() != nullptr) ? 1 : 0;
+}
+
+cudaError_t launch_tc_eval(void *prof, const int8_t *msa, const float *w, double beff,
+                           const __nv_bfloat16 *th_hi, const __nv_bfloat16 *th_lo,
+                           const float *theta, const Dims &d, double lambda_h,
+                           double lambda_Jp, void *scratch, double *f_data, float *G, int *err,
+                           cudaStream_t st)
+{
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_tc_logits,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+        if (e) return e;
+        e = cudaFuncSetAttribute(k_tc_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+        if (e) return e;
+        attr = true;
+    }
+    const int BP = padded_B(d);
+    const int nbt = BP / TC_M;
+    char *p = (char *)scratch;
+    __nv_bfloat16 *dt_hi = (__nv_bfloat16 *)p;
+    p += align256((size_t)d.R * BP * 2);
+    __nv_bfloat16 *dt_lo = (__nv_bfloat16 *)p;
+    p += align256((size_t)d.R * BP * 2);
+    double *partial = (double *)p;
+    p += align256((size_t)nbt * d.N * sizeof(double));
+    int8_t *msaT = (int8_t *)p;
+
+    CUtensorMap m_hi, m_lo, m_dhi, m_dlo;
+    if (!make_map(&m_hi, th_hi, d.KP, d.R, TC_BK, LG_N) ||
+        !make_map(&m_lo, th_lo, d.KP, d.R, TC_BK, LG_N) ||
+        !make_map(&m_dhi, dt_hi, BP, d.R, TC_BK, TC_M) ||
+        !make_map(&m_dlo, dt_lo, BP, d.R, TC_BK, TC_M))
+        return cudaErrorInvalidValue;
+
+    size_t nT = (size_t)(d.N + 1) * BP;
+    k_msa_transpose<<<(unsigned)((nT + 255) / 256), 256, 0, st>>>(msa, d, BP, msaT);
+    void *t0 = prof ? prof_start(prof) : nullptr;
+    dim3 g1(nbt, (d.N + LG_SITES - 1) / LG_SITES);
+    k_tc_logits<<<g1, 192, TC_SMEM, st>>>(m_hi, m_lo, msa, w, 1.0 / beff, d, BP, dt_hi, dt_lo,
+                                          partial, err);
+    if (prof) prof_stop(prof, "tc_logits", t0);
+    cudaError_t e = launch_finish_objective(partial, nbt, d, beff, nullptr, f_data, st);
+    if (e) return e;
+    void *t1 = prof ? prof_start(prof) : nullptr;
+    dim3 g2((d.KP + GR_N - 1) / GR_N, (d.R + TC_M - 1) / TC_M);
+    k_tc_grad<<<g2, 192, TC_SMEM, st>>>(m_dhi, m_dlo, msaT, theta, d, BP, (float)(2.0 * lambda_h),
+                                        (float)(2.0 * lambda_Jp), G, err);
+    if (prof) prof_stop(prof, "tc_grad", t1);
+    count_launches(3);
+    return cudaGetLastError();
 }
 
 }  // namespace plm

@@ -79,6 +79,29 @@ struct ProfScope {
     }
 };
 
+}  // namespace
+
+namespace plm {
+// event hooks for kernels launched outside this file (tensor-core path)
+void *prof_start(void *ctx)
+{
+    plm_ctx *c = (plm_ctx *)ctx;
+    cudaEvent_t e = take_event(c);
+    cudaEventRecord(e, c->stream);
+    return (void *)e;
+}
+
+void prof_stop(void *ctx, const char *name, void *start)
+{
+    plm_ctx *c = (plm_ctx *)ctx;
+    cudaEvent_t b = take_event(c);
+    cudaEventRecord(b, c->stream);
+    c->prof_records.push_back({name, (cudaEvent_t)start, b});
+}
+}  // namespace plm
+
+namespace {
+
 plm_status fail(plm_ctx *c, plm_status s, const char *fmt, ...)
 {
     char buf[512];
@@ -225,7 +248,7 @@ plm_status evaluate(plm_ctx *ctx, plm_precision prec, const int8_t *msa,
                     const float *w, double beff, const Dims &d,
                     const float *theta, const __nv_bfloat16 *hi,
                     const __nv_bfloat16 *lo, double lambda_h, double lambda_Jp,
-                    double *f_data, float *G)
+                    double *f_data, float *G, int *tc_err)
 {
     cudaStream_t st = ctx->stream;
     if (prec == PLM_FP32_EXACT) {
@@ -252,11 +275,10 @@ plm_status evaluate(plm_ctx *ctx, plm_precision prec, const int8_t *msa,
     if (prec == PLM_SPLIT_BF16) {
         if (!tc_supported())
             return fail(ctx, PLM_ENOTIMPL, "split-bf16 tensor-core path needs an sm_103 GPU");
-        void *scratch, *flag;
+        void *scratch;
         CK(ws(ctx, "tc_scratch", tc_scratch_bytes(d), &scratch));
-        CK(ws(ctx, "flag_tc", sizeof(int), &flag));
         CK(launch_tc_eval(ctx->prof ? (void *)ctx : nullptr, msa, w, beff, hi, lo, theta, d,
-                          lambda_h, lambda_Jp, scratch, f_data, G, (int *)flag, st));
+                          lambda_h, lambda_Jp, scratch, f_data, G, tc_err, st));
         return PLM_OK;
     }
     return fail(ctx, PLM_ENOTIMPL, "precision mode %d is not built", (int)prec);
@@ -451,9 +473,12 @@ plm_status plm_site_objective_grad(plm_ctx *ctx, const int8_t *msa,
         CK(launch_split_theta((const float *)theta, d, (__nv_bfloat16 *)hi,
                               (__nv_bfloat16 *)lo, ctx->stream));
     }
+    void *tcflag;
+    CK(ws(ctx, "flag_tc", sizeof(int), &tcflag));
+    CK(cudaMemsetAsync(tcflag, 0, sizeof(int), ctx->stream));
     s = evaluate(ctx, prec, (const int8_t *)msa_d, (const float *)w_d, beff, d,
                  (const float *)theta, (const __nv_bfloat16 *)hi, (const __nv_bfloat16 *)lo,
-                 lambda_h, lJp, (double *)fdat, (float *)G);
+                 lambda_h, lJp, (double *)fdat, (float *)G, (int *)tcflag);
     if (s) return s;
     // f = data + penalty
     void *fsum;
@@ -465,7 +490,16 @@ plm_status plm_site_objective_grad(plm_ctx *ctx, const int8_t *msa,
     CK(copy_back(ctx, f_s));
     CK(copy_back(ctx, gh_s));
     CK(copy_back(ctx, gJ_s));
-    if (f_s.host || gh_s.host || gJ_s.host) CK(cudaStreamSynchronize(ctx->stream));
+    if (prec == PLM_SPLIT_BF16) {
+        CK(cudaMemcpyAsync(ctx->host_counters + 10, tcflag, sizeof(int), cudaMemcpyDeviceToHost,
+                           ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        if (ctx->host_counters[10])
+            return fail(ctx, PLM_ETIMEOUT, "tensor-core pipeline wait timed out (code 0x%x)",
+                        ctx->host_counters[10]);
+    } else if (f_s.host || gh_s.host || gJ_s.host) {
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
     return PLM_OK;
 }
 
@@ -558,16 +592,18 @@ plm_status plm_solve(plm_ctx *ctx, const int8_t *msa, int B, int N, int q,
         CK(cudaMemsetAsync(lo, 0, d.theta_elems() * 2, st));
     }
     int evals = 0;
+    int *tc_err = (int *)cnt + 4;  // tensor-core timeout word, read back with the counters
+    CK(cudaMemsetAsync(cnt, 0, 16 * sizeof(int), st));
     s = evaluate(ctx, o.prec, S, (const float *)w, beff, d, (const float *)theta,
                  (const __nv_bfloat16 *)hi, (const __nv_bfloat16 *)lo, p.lambda_h,
-                 p.lambda_Jp, (double *)fdat, (float *)g);
+                 p.lambda_Jp, (double *)fdat, (float *)g, tc_err);
     if (s) return s;
     evals++;
     CK(launch_lbfgs_init((SiteState *)sst, (const double *)fdat, (const float *)g, d, p, st));
 
     int *hc = ctx->host_counters;
     for (int it = 0; it < o.max_iter; ++it) {
-        CK(cudaMemsetAsync(cnt, 0, 16 * sizeof(int), st));
+        CK(cudaMemsetAsync(cnt, 0, 2 * sizeof(int), st));
         {
             ProfScope ps(ctx, "lbfgs_direction");
             CK(launch_lbfgs_direction((SiteState *)sst, (const float *)g, (float *)dir,
@@ -582,7 +618,7 @@ plm_status plm_solve(plm_ctx *ctx, const int8_t *msa, int B, int N, int q,
             }
             s = evaluate(ctx, o.prec, S, (const float *)w, beff, d, (const float *)theta_t,
                          (const __nv_bfloat16 *)hi, (const __nv_bfloat16 *)lo, p.lambda_h,
-                         p.lambda_Jp, (double *)fdat, (float *)g_t);
+                         p.lambda_Jp, (double *)fdat, (float *)g_t, tc_err);
             if (s) return s;
             evals++;
             CK(cudaMemsetAsync(cnt, 0, sizeof(int), st));
@@ -593,11 +629,14 @@ plm_status plm_solve(plm_ctx *ctx, const int8_t *msa, int B, int N, int q,
                                            (const float *)g_t, (const float *)dir, (float *)Sh,
                                            (float *)Yh, d, p, (int *)cnt, st));
             }
-            CK(cudaMemcpyAsync(hc, cnt, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+            CK(cudaMemcpyAsync(hc, cnt, 5 * sizeof(int), cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
+            if (hc[4])
+                return fail(ctx, PLM_ETIMEOUT, "tensor-core pipeline wait timed out (code 0x%x)",
+                            hc[4]);
             if (hc[0] == 0) break;
         }
-        CK(cudaMemsetAsync(cnt, 0, 16 * sizeof(int), st));
+        CK(cudaMemsetAsync(cnt, 0, 2 * sizeof(int), st));
         CK(launch_count_status((const SiteState *)sst, N, (int *)cnt, st));
         CK(cudaMemcpyAsync(hc, cnt, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
