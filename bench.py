@@ -40,6 +40,8 @@ def parse_args():
     ap.add_argument("--prec", default="auto", choices=["auto", "fp32", "split_bf16"])
     ap.add_argument("--gtol", type=float, default=1e-4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp32-cmp", action="store_true",
+                    help="skip timing the plain FP32 path beside the split-bf16 one")
     ap.add_argument("--cpu-sites", type=int, default=0,
                     help="sites per CPU-oracle sample (0 = one per host core, at most 16)")
     return ap.parse_args()
@@ -242,6 +244,32 @@ def main():
     value = total_max / (args.steps * world)  # seconds per solve for the whole job
     evals = statistics.mean(r["evals"] for r in reps)
 
+    # the plain FP32 GPU path at the same gtol (the comparison the metric names)
+    fp32_cmp = None
+    if prec != "fp32" and not args.no_fp32_cmp:
+        def step32():
+            h, J, rep = api.plm_solve(ctx, msa, gtol=args.gtol, prec="fp32")
+            fn, cfn, top = api.fn_apc_scores(ctx, J)
+            return rep, top
+        with torch.cuda.stream(stream):
+            step32()
+            t32, top32 = [], None
+            for _ in range(args.steps):
+                flush.zero_()
+                torch.cuda.synchronize(device)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                rep32, top32 = step32()
+                e1.record(stream)
+                torch.cuda.synchronize(device)
+                t32.append(e0.elapsed_time(e1) / 1000.0)
+        same = bool(torch.equal(top32.cpu(), top.cpu()))
+        fp32_cmp = {"value": statistics.mean(t32), "unit": "s",
+                    "speedup_of_split_bf16": statistics.mean(t32) / mean_t,
+                    "evals_per_solve": rep32["evals"], "gnorm_max": rep32["gnorm_max"],
+                    "top_L_identical_to_split_bf16": same}
+
     # end to end through the C ABI with host buffers (pinned MSA in, J/h/scores out)
     msa_host = torch.from_numpy(fam.msa).pin_memory()
     msa_np = msa_host.numpy()
@@ -300,6 +328,7 @@ def main():
                        "x": 0.8, "l2": "flushed between timed steps (256 MiB write)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "evals_per_s": evals / mean_t,
+            "fp32_path": fp32_cmp,
             "evals_per_solve": evals,
             "iters": statistics.mean(r["iters"] for r in reps),
             "sites_converged": reps[-1]["n_converged"], "sites_noise": reps[-1]["n_noise"],
