@@ -170,6 +170,32 @@ plm_status fn_apc_scores(plm_ctx *ctx, const float *J, int N, int q,
                          int combine, double *fn_out, double *cfn_out,
                          int32_t *topL_out, int L, int min_sep);
 
+/* msa_reweight_static -- the paper has no counterpart to this call.
+ * The same reweighting as msa_reweight (identical m, w and B_eff), for
+ * callers that cannot allocate memory when they need it: code running while
+ * another component owns the allocator (inside a pool or caching-allocator
+ * callback), programs that forbid allocation after start-up, and callers
+ * that hold only a raw stream.  It needs no context and calls no cudaMalloc,
+ * cudaFree or other allocating routine: its scratch is one file-scope
+ * device array of 16 MiB that every GPU loading the library holds until the
+ * process exits.  The scratch needed is
+ *     round256(20 B ceil(N/32)) + round256(4 B) + round256(4 (B + 1)) + 256
+ * bytes; larger problems return PLM_ENOMEM before anything is launched.
+ *   msa [B][N] int8, m_out [B] int32 (may be NULL), w_out [B] float (may be
+ *   NULL), beff_out: one double -- all DEVICE pointers, owned by the caller.
+ *   cuda_stream: the cudaStream_t the work is ordered on (NULL = legacy).
+ * Work is queued on the stream; the call does not synchronise.  States
+ * outside 0..20 make *beff_out NaN.  PLM_EINVAL for q != 21, B < 1, N < 1,
+ * x outside [0,1] or a NULL msa/beff_out; PLM_ECUDA if a CUDA call fails.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call shares the array and it keeps the
+ * previous call's contents (each call clears what must start at zero), so
+ * calls whose work overlaps on the GPU race: order them on one stream. */
+plm_status msa_reweight_static(const int8_t *msa, int B, int N, int q, double x,
+                               int32_t *m_out, float *w_out, double *beff_out,
+                               void *cuda_stream);
+
 /* ---- diagnostics (no counterpart in the paper) ----
  * plm_kernel_launches: number of CUDA kernels this library has launched in
  * this process so far (all contexts).
