@@ -69,7 +69,7 @@ typedef struct {
     double lambda_J;   /* coupling strength as the user gives it (paper: 0.01);
                           halved inside, lambda'_J = 0.5 lambda_J (step 1) */
     double gtol;       /* stop a site when ||grad g_r^(reg)||_2 <= gtol */
-    int lbfgs_m;       /* L-BFGS memory, 1..16 */
+    int lbfgs_m;       /* L-BFGS memory, 1..8 */
     int max_iter;      /* iteration cap per site */
     int max_ls;        /* trial steps per line search before a site fails */
     plm_precision prec;

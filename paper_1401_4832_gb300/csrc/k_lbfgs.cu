@@ -6,17 +6,30 @@
 // origin (Sec. 6).  All sites share each objective+gradient evaluation; a
 // site keeps its own curvature pairs, step length and stopping state.
 //
-// One CTA per site streams that site's contiguous segment of the vectors
-// (FP32 storage); every inner product and every scalar of the recursion and
-// of the line search is FP64, reduced in a fixed order.
+// Vectors are FP32.  Inner products are accumulated per thread in
+// double-float (error-free FP32 products and sums, ~44 significant bits),
+// then reduced across threads and chunks in FP64; every scalar of the
+// recursion and of the line search is FP64.  Each site's segment is cut
+// into chunks; one CTA per (chunk, site) streams the vectors and writes
+// partial sums, and a one-warp-per-site kernel reduces them in a fixed
+// order and does the scalar work, so results do not depend on scheduling.
 //
-// Direction: the two-loop recursion (Nocedal & Wright, Alg. 7.4) with
-// H0 = (s'y / y'y) I.  Step: a strong-Wolfe search (c1, c2) in the style of
-// Nocedal & Wright Alg. 3.5/3.6, driven by the directional derivative: the
-// objective is convex, so phi'(alpha) is nondecreasing and brackets the
-// minimiser along the line even where FP32 rounding makes differences of f
-// unresolvable.  The sufficient-decrease test allows a noise band of
-// `noise * max(1, |f0|)` on f.
+// Direction: the compact representation of the L-BFGS inverse Hessian
+// (Byrd, Nocedal & Schnabel 1994; Nocedal & Wright Eq. 7.24) with
+// H0 = gamma I, gamma = s'y / y'y of the newest pair:
+//     H g = gamma g + S p - gamma Y R^{-1} u,
+//     u = S'g, v = Y'g, p = R^{-T} ((D + gamma Y'Y) R^{-1} u - gamma v),
+// R the upper triangle of S'Y (age order), D its diagonal.  One streaming
+// pass forms S'g, Y'g and the dot products of the newest y with every
+// stored pair (which keep S'Y and Y'Y current), a second pass forms d.
+// The result equals the two-loop recursion's.
+//
+// Step: strong-Wolfe search (c1, c2) in the style of Nocedal & Wright
+// Alg. 3.5/3.6, driven by the directional derivative: the objective is
+// convex, so phi'(alpha) is nondecreasing and brackets the minimiser along
+// the line even where FP32 rounding makes differences of f unresolvable.
+// Sufficient decrease allows a noise band `noise * max(1, |f0|)` on f, or
+// is certified by phi'(alpha) <= c1 phi'(0) (convexity).
 #include "plm_device.cuh"
 #include "plm_internal.cuh"
 
@@ -24,242 +37,380 @@ namespace plm {
 
 namespace {
 
-constexpr int LB_THREADS = 512;
+constexpr int LB_THREADS = 256;
+constexpr int LB_CHUNK4 = 2048;  // float4 elements per chunk
 
-__device__ __forceinline__ double dot4(const float4 a, const float4 b)
+// sum K per-thread values over the block (fixed order) and write them
+template <int K>
+__device__ __forceinline__ void block_write(double (&v)[K], double *out)
 {
-    return (double)a.x * b.x + (double)a.y * b.y + (double)a.z * b.z +
-           (double)a.w * b.w;
+    __shared__ double red[LB_THREADS / 32][K];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = warp_sum_d(v[k]);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k) red[wid][k] = v[k];
+    __syncthreads();
+    if (threadIdx.x < K) {
+        double t = 0.0;
+        for (int w = 0; w < LB_THREADS / 32; ++w) t += red[w][threadIdx.x];
+        out[threadIdx.x] = t;
+    }
 }
 
-__global__ void __launch_bounds__(LB_THREADS)
-k_init(SiteState *ss, const double *__restrict__ f, const float *__restrict__ g,
-       Dims d, SolveParams p)
+// fixed-order sum over the chunks of one site (one warp): returns the
+// total of slot k of the partial records
+__device__ __forceinline__ double chunk_sum(const double *part, int nch, int k)
 {
-    __shared__ double red[LB_THREADS / 32];
+    const int lane = threadIdx.x & 31;
+    double t = 0.0;
+    for (int c = lane; c < nch; c += 32) t += part[(size_t)c * LB_PART + k];
+    return warp_sum_d(t);
+}
+
+struct Chunk {
+    size_t base4, e0, e1, vec4;
+};
+
+__device__ __forceinline__ Chunk chunk_of(const Dims &d)
+{
+    Chunk ch;
+    const size_t seg4 = d.site_elems() / 4;
+    ch.base4 = (size_t)blockIdx.y * seg4;
+    ch.e0 = (size_t)blockIdx.x * LB_CHUNK4;
+    ch.e1 = min(ch.e0 + LB_CHUNK4, seg4);
+    ch.vec4 = d.theta_elems() / 4;
+    return ch;
+}
+
+__device__ __forceinline__ double *part_rec(double *part, int nch)
+{
+    return part + ((size_t)blockIdx.y * nch + blockIdx.x) * LB_PART;
+}
+
+// ------------------------------------------------------------ start
+__global__ void __launch_bounds__(LB_THREADS)
+k_init_dots(const float *__restrict__ g, Dims d, double *part, int nch)
+{
+    const Chunk ch = chunk_of(d);
+    const float4 *g4 = (const float4 *)g + ch.base4;
+    DF acc;
+    for (size_t e = ch.e0 + threadIdx.x; e < ch.e1; e += LB_THREADS) df_dot4(acc, g4[e], g4[e]);
+    double v[1] = {df_value(acc)};
+    block_write<1>(v, part_rec(part, nch));
+}
+
+__global__ void k_init_finish(SiteState *ss, const double *__restrict__ f, const double *part,
+                              int nch, SolveParams p)
+{
     const int r = blockIdx.x;
-    const size_t n4 = d.site_elems() / 4;
-    const float4 *g4 = (const float4 *)(g + (size_t)r * d.site_elems());
-    double gg = 0.0;
-    for (size_t e = threadIdx.x; e < n4; e += blockDim.x) {
-        float4 v = g4[e];
-        gg += dot4(v, v);
-    }
-    gg = block_sum_d(gg, red);
-    if (threadIdx.x == 0) {
-        SiteState &s = ss[r];
-        s.f = f[r];
-        s.gnorm2 = gg;
-        s.hist = 0;
-        s.head = 0;
-        s.iters = 0;
-        s.trials = 0;
-        s.phase = 0;
-        s.gamma = 1.0;
-        s.status = (sqrt(gg) <= p.gtol) ? SITE_CONVERGED
-                   : (p.max_iter <= 0 ? SITE_FAILED : SITE_READY);
-    }
+    const double gg = chunk_sum(part + (size_t)r * nch * LB_PART, nch, 0);
+    if (threadIdx.x != 0) return;
+    SiteState &s = ss[r];
+    s.f = f[r];
+    s.gnorm2 = gg;
+    s.hist = 0;
+    s.head = 0;
+    s.iters = 0;
+    s.trials = 0;
+    s.phase = 0;
+    s.gamma = 1.0;
+    s.neg_g = 0;
+    s.commit_round = -1;
+    s.commit_slot = 0;
+    for (int i = 0; i < MAX_M; ++i)
+        for (int j = 0; j < MAX_M; ++j) {
+            s.SY[i][j] = 0.0;
+            s.YY[i][j] = 0.0;
+        }
+    s.status = (sqrt(gg) <= p.gtol) ? SITE_CONVERGED
+               : (p.max_iter <= 0 ? SITE_FAILED : SITE_READY);
 }
 
-// d = -H g by the two-loop recursion; sets up the line search.
-__global__ void __launch_bounds__(LB_THREADS)
-k_direction(SiteState *ss, const float *__restrict__ g, float *__restrict__ dir,
-            const float *__restrict__ S_hist, const float *__restrict__ Y_hist,
-            Dims d, SolveParams p)
+// ------------------------------------------------------------ direction
+__device__ __forceinline__ bool slot_valid(int j, int head, int hist, int M)
 {
-    __shared__ double red[LB_THREADS / 16];
-    __shared__ double alph[MAX_M];
+    return ((head - 1 - j + 2 * M) % M) < hist;  // distance from the newest slot
+}
+
+// pass 1: S'g, Y'g, S'y_new, Y'y_new
+template <int M>
+__global__ void __launch_bounds__(LB_THREADS)
+k_dir_dots(const SiteState *ss, const float *__restrict__ g, const float *__restrict__ S,
+           const float *__restrict__ Y, Dims d, double *part, int nch)
+{
+    const SiteState &s = ss[blockIdx.y];
+    if (s.status != SITE_READY || s.hist == 0) return;
+    const int hist = s.hist, head = s.head;
+    const int newest = (head - 1 + M) % M;
+    const Chunk ch = chunk_of(d);
+    const float4 *g4 = (const float4 *)g + ch.base4;
+    const float4 *S4 = (const float4 *)S + ch.base4;
+    const float4 *Y4 = (const float4 *)Y + ch.base4;
+    bool valid[M];
+#pragma unroll
+    for (int j = 0; j < M; ++j) valid[j] = slot_valid(j, head, hist, M);
+    DF acc[4 * M];
+    for (size_t e = ch.e0 + threadIdx.x; e < ch.e1; e += LB_THREADS) {
+        const float4 gv = g4[e];
+        const float4 yn = Y4[(size_t)newest * ch.vec4 + e];
+#pragma unroll
+        for (int j = 0; j < M; ++j) {
+            if (!valid[j]) continue;
+            const float4 sv = S4[(size_t)j * ch.vec4 + e];
+            const float4 yv = Y4[(size_t)j * ch.vec4 + e];
+            df_dot4(acc[j], sv, gv);
+            df_dot4(acc[M + j], yv, gv);
+            df_dot4(acc[2 * M + j], sv, yn);
+            df_dot4(acc[3 * M + j], yv, yn);
+        }
+    }
+    double v[4 * M];
+#pragma unroll
+    for (int k = 0; k < 4 * M; ++k) v[k] = df_value(acc[k]);
+    block_write<4 * M>(v, part_rec(part, nch));
+}
+
+// the small FP64 algebra of the compact form, one warp per site
+template <int M>
+__global__ void k_dir_solve(SiteState *ss, const double *part, int nch)
+{
     const int r = blockIdx.x;
     SiteState &s = ss[r];
     if (s.status != SITE_READY) return;
-    const size_t seg = d.site_elems();
-    const size_t n4 = seg / 4;
-    const size_t vec = d.theta_elems();  // stride between history slots
-    const int m = p.m;
-    const int hist = s.hist, head = s.head;
-    const float4 *g4 = (const float4 *)(g + (size_t)r * seg);
-    float4 *q4 = (float4 *)(dir + (size_t)r * seg);
-    auto S4 = [&](int j) { return (const float4 *)(S_hist + (size_t)j * vec + (size_t)r * seg); };
-    auto Y4 = [&](int j) { return (const float4 *)(Y_hist + (size_t)j * vec + (size_t)r * seg); };
-
-    double dg0 = 0.0;
-    if (hist == 0) {
-        double gd = 0.0;
-        for (size_t e = threadIdx.x; e < n4; e += blockDim.x) {
-            float4 v = g4[e];
-            q4[e] = make_float4(-v.x, -v.y, -v.z, -v.w);
-            gd -= dot4(v, v);
-        }
-        dg0 = block_sum_d(gd, red);
-    } else {
-        // newest .. oldest: slot j_t = (head - 1 - t) mod m
-        int j0 = (head - 1 + m) % m;
-        double t0 = 0.0;
-        {
-            const float4 *s0 = S4(j0);
-            for (size_t e = threadIdx.x; e < n4; e += blockDim.x) t0 += dot4(s0[e], g4[e]);
-        }
-        t0 = block_sum_d(t0, red);
-        if (threadIdx.x == 0) alph[j0] = s.rho[j0] * t0;
-        __syncthreads();
-        double carry = 0.0;  // dot computed in the previous pass
-        for (int t = 0; t < hist; ++t) {
-            const int j = (head - 1 - t + 2 * m) % m;
-            const float a = (float)alph[j];
-            const float4 *y = Y4(j);
-            const bool last = (t + 1 == hist);
-            const int jn = (head - 2 - t + 2 * m) % m;
-            const float4 *nxt = last ? Y4(j) : S4(jn);
-            const float4 *src = (t == 0) ? g4 : q4;
-            double acc = 0.0;
-            for (size_t e = threadIdx.x; e < n4; e += blockDim.x) {
-                float4 v = src[e], yy = y[e];
-                v.x -= a * yy.x; v.y -= a * yy.y; v.z -= a * yy.z; v.w -= a * yy.w;
-                q4[e] = v;
-                acc += dot4(nxt[e], v);
-            }
-            acc = block_sum_d(acc, red);
-            if (!last) {
-                if (threadIdx.x == 0) alph[jn] = s.rho[jn] * acc;
-                __syncthreads();
-            } else {
-                carry = acc;  // y_oldest . q
-            }
-        }
-        // second loop, oldest .. newest, starting from r = gamma q
-        const double gamma = s.gamma;
-        carry *= gamma;
-        for (int t = hist - 1; t >= 0; --t) {
-            const int j = (head - 1 - t + 2 * m) % m;
-            const double beta = s.rho[j] * carry;
-            const float coef = (float)(alph[j] - beta);
-            const float4 *sj = S4(j);
-            const bool first = (t == hist - 1);
-            const bool last = (t == 0);
-            const int jn = (head - t + 2 * m) % m;  // next newer slot
-            const float sc = first ? (float)gamma : 1.0f;
-            double acc = 0.0;
-            for (size_t e = threadIdx.x; e < n4; e += blockDim.x) {
-                float4 v = q4[e], sv = sj[e];
-                v.x = sc * v.x + coef * sv.x;
-                v.y = sc * v.y + coef * sv.y;
-                v.z = sc * v.z + coef * sv.z;
-                v.w = sc * v.w + coef * sv.w;
-                if (last) {
-                    v = make_float4(-v.x, -v.y, -v.z, -v.w);
-                    acc += dot4(g4[e], v);
-                } else {
-                    acc += dot4(Y4(jn)[e], v);
-                }
-                q4[e] = v;
-            }
-            acc = block_sum_d(acc, red);
-            carry = acc;
-        }
-        dg0 = carry;  // g . d
-        if (!(dg0 < 0.0)) {
-            // not a descent direction (rounding): drop the history, use -g
-            double gd = 0.0;
-            for (size_t e = threadIdx.x; e < n4; e += blockDim.x) {
-                float4 v = g4[e];
-                q4[e] = make_float4(-v.x, -v.y, -v.z, -v.w);
-                gd -= dot4(v, v);
-            }
-            dg0 = block_sum_d(gd, red);
-            if (threadIdx.x == 0) {
-                s.hist = 0;
-                s.head = 0;
-            }
+    __shared__ double tot[4 * M];
+    if (s.hist > 0) {
+        for (int k = 0; k < 4 * M; ++k) {
+            double t = chunk_sum(part + (size_t)r * nch * LB_PART, nch, k);
+            if (threadIdx.x == 0) tot[k] = t;
         }
     }
-    if (threadIdx.x == 0) {
-        s.f0 = s.f;
-        s.dg0 = dg0;
-        s.alpha = (s.iters == 0 && s.hist == 0) ? 1.0 / sqrt(s.gnorm2) : 1.0;
-        s.a_prev = 0.0;
-        s.f_prev = s.f;
-        s.dg_prev = dg0;
-        s.a_lo = 0.0;
-        s.f_lo = s.f;
-        s.dg_lo = dg0;
-        s.a_hi = 0.0;
-        s.f_hi = 0.0;
-        s.dg_hi = 0.0;
-        s.phase = 0;
-        s.trials = 0;
-        s.status = SITE_SEARCHING;
+    __syncwarp();
+    if (threadIdx.x != 0) return;
+    for (int j = 0; j < MAX_M; ++j) s.cs[j] = s.cy[j] = 0.0;
+    s.cg = 1.0;
+    int hist = s.hist, head = s.head;
+    if (hist == 0) return;
+    const int n = (head - 1 + M) % M;
+    for (int j = 0; j < M; ++j) {
+        if (!slot_valid(j, head, hist, M)) continue;
+        s.SY[j][n] = tot[2 * M + j];
+        s.YY[j][n] = tot[3 * M + j];
+        s.YY[n][j] = tot[3 * M + j];
+    }
+    if (!(s.SY[n][n] > 0.0) || !(s.YY[n][n] > 0.0)) {
+        // newest pair violates the curvature condition: restart from -g
+        s.hist = 0;
+        s.head = 0;
+        return;
+    }
+    const double gamma = s.SY[n][n] / s.YY[n][n];
+    int idx[M];
+    double u[M], v[M], t1[M], t2[M], pp[M];
+    for (int a = 0; a < hist; ++a) {
+        idx[a] = (head - hist + a + 2 * M) % M;  // oldest first
+        u[a] = tot[idx[a]];
+        v[a] = tot[M + idx[a]];
+    }
+    // t1 = R^{-1} u, R[a][b] = s_a . y_b (a <= b in age order)
+    for (int a = hist - 1; a >= 0; --a) {
+        double x = u[a];
+        for (int b = a + 1; b < hist; ++b) x -= s.SY[idx[a]][idx[b]] * t1[b];
+        t1[a] = x / s.SY[idx[a]][idx[a]];
+    }
+    // t2 = (D + gamma Y'Y) t1 - gamma v
+    for (int a = 0; a < hist; ++a) {
+        double x = s.SY[idx[a]][idx[a]] * t1[a] - gamma * v[a];
+        for (int b = 0; b < hist; ++b) x += gamma * s.YY[idx[a]][idx[b]] * t1[b];
+        t2[a] = x;
+    }
+    // p = R^{-T} t2
+    for (int a = 0; a < hist; ++a) {
+        double x = t2[a];
+        for (int b = 0; b < a; ++b) x -= s.SY[idx[b]][idx[a]] * pp[b];
+        pp[a] = x / s.SY[idx[a]][idx[a]];
+    }
+    s.gamma = gamma;
+    s.cg = gamma;
+    for (int a = 0; a < hist; ++a) {
+        s.cs[idx[a]] = pp[a];
+        s.cy[idx[a]] = -gamma * t1[a];
     }
 }
 
-// theta_t = theta + alpha d (and its bf16 hi/lo split); penalty at theta_t
+// pass 2: d = -(cg g + sum cs_j s_j + sum cy_j y_j); partial g.d
+template <int M>
 __global__ void __launch_bounds__(LB_THREADS)
-k_trial(SiteState *ss, const float *__restrict__ theta,
-        const float *__restrict__ dir, float *__restrict__ theta_t,
-        __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo,
-        Dims d, SolveParams p)
+k_dir_apply(const SiteState *ss, const float *__restrict__ g, const float *__restrict__ S,
+            const float *__restrict__ Y, float *__restrict__ dir, Dims d, double *part, int nch)
 {
-    __shared__ double red[LB_THREADS / 16];
+    const SiteState &s = ss[blockIdx.y];
+    if (s.status != SITE_READY) return;
+    const int hist = s.hist, head = s.head;
+    const Chunk ch = chunk_of(d);
+    const float4 *g4 = (const float4 *)g + ch.base4;
+    const float4 *S4 = (const float4 *)S + ch.base4;
+    const float4 *Y4 = (const float4 *)Y + ch.base4;
+    float4 *d4 = (float4 *)dir + ch.base4;
+    const float cg = (float)s.cg;
+    bool valid[M];
+    float cs[M], cy[M];
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+        valid[j] = slot_valid(j, head, hist, M);
+        cs[j] = (float)s.cs[j];
+        cy[j] = (float)s.cy[j];
+    }
+    DF acc;
+    for (size_t e = ch.e0 + threadIdx.x; e < ch.e1; e += LB_THREADS) {
+        const float4 gv = g4[e];
+        float4 a = make_float4(cg * gv.x, cg * gv.y, cg * gv.z, cg * gv.w);
+#pragma unroll
+        for (int j = 0; j < M; ++j) {
+            if (!valid[j]) continue;
+            const float4 sv = S4[(size_t)j * ch.vec4 + e];
+            const float4 yv = Y4[(size_t)j * ch.vec4 + e];
+            a.x += cs[j] * sv.x + cy[j] * yv.x;
+            a.y += cs[j] * sv.y + cy[j] * yv.y;
+            a.z += cs[j] * sv.z + cy[j] * yv.z;
+            a.w += cs[j] * sv.w + cy[j] * yv.w;
+        }
+        const float4 dv = make_float4(-a.x, -a.y, -a.z, -a.w);
+        d4[e] = dv;
+        df_dot4(acc, gv, dv);
+    }
+    double v[1] = {df_value(acc)};
+    block_write<1>(v, part_rec(part, nch));
+}
+
+// line-search set-up; a direction that is not a descent direction (rounding
+// in FP32) is replaced by -g and the history is dropped
+__global__ void k_dir_finish(SiteState *ss, const double *part, int nch)
+{
     const int r = blockIdx.x;
     SiteState &s = ss[r];
+    if (s.status != SITE_READY) return;
+    double dg0 = chunk_sum(part + (size_t)r * nch * LB_PART, nch, 0);
+    if (threadIdx.x != 0) return;
+    s.neg_g = 0;
+    if (!(dg0 < 0.0)) {
+        s.neg_g = 1;
+        s.hist = 0;
+        s.head = 0;
+        dg0 = -s.gnorm2;
+    }
+    s.f0 = s.f;
+    s.dg0 = dg0;
+    s.alpha = (s.iters == 0 && s.hist == 0) ? 1.0 / sqrt(s.gnorm2) : 1.0;
+    s.a_prev = 0.0;
+    s.f_prev = s.f;
+    s.dg_prev = dg0;
+    s.a_lo = 0.0;
+    s.f_lo = s.f;
+    s.dg_lo = dg0;
+    s.a_hi = 0.0;
+    s.f_hi = 0.0;
+    s.dg_hi = 0.0;
+    s.phase = 0;
+    s.trials = 0;
+    s.status = SITE_SEARCHING;
+}
+
+// ------------------------------------------------------------ line search
+// theta_t = theta + alpha d (and its bf16 hi/lo split); penalty partials
+__global__ void __launch_bounds__(LB_THREADS)
+k_trial(const SiteState *ss, const float *__restrict__ theta, const float *__restrict__ g,
+        float *__restrict__ dir, float *__restrict__ theta_t, __nv_bfloat16 *__restrict__ hi,
+        __nv_bfloat16 *__restrict__ lo, Dims d, double *part, int nch)
+{
+    const SiteState &s = ss[blockIdx.y];
     if (s.status != SITE_SEARCHING) return;
-    const size_t seg = d.site_elems();
-    const size_t n4 = seg / 4;
-    const int NQ = d.N * Q;
+    const Chunk ch = chunk_of(d);
     const float a = (float)s.alpha;
-    const float4 *t4 = (const float4 *)(theta + (size_t)r * seg);
-    const float4 *d4 = (const float4 *)(dir + (size_t)r * seg);
-    float4 *o4 = (float4 *)(theta_t + (size_t)r * seg);
-    double pj = 0.0, ph = 0.0;
-    for (size_t e = threadIdx.x; e < n4; e += blockDim.x) {
-        float4 t = t4[e], dv = d4[e];
-        float4 v = make_float4(fmaf(a, dv.x, t.x), fmaf(a, dv.y, t.y),
-                               fmaf(a, dv.z, t.z), fmaf(a, dv.w, t.w));
-        o4[e] = v;
-        const float vv[4] = {v.x, v.y, v.z, v.w};
+    const bool neg = s.neg_g != 0;
+    const int NQ = d.N * Q;
+    const float4 *t4 = (const float4 *)theta + ch.base4;
+    const float4 *g4 = (const float4 *)g + ch.base4;
+    float4 *d4 = (float4 *)dir + ch.base4;
+    float4 *o4 = (float4 *)theta_t + ch.base4;
+    DF pj, ph;  // sums of squares: couplings, fields
+    for (size_t e = ch.e0 + threadIdx.x; e < ch.e1; e += LB_THREADS) {
+        const float4 t = t4[e];
+        float4 dv;
+        if (neg) {
+            const float4 gv = g4[e];
+            dv = make_float4(-gv.x, -gv.y, -gv.z, -gv.w);
+            d4[e] = dv;
+        } else {
+            dv = d4[e];
+        }
+        const float4 x = make_float4(fmaf(a, dv.x, t.x), fmaf(a, dv.y, t.y), fmaf(a, dv.z, t.z),
+                                     fmaf(a, dv.w, t.w));
+        o4[e] = x;
+        const float xv[4] = {x.x, x.y, x.z, x.w};
         const int c0 = (int)((4 * e) % d.KP);
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            double x = vv[u];
-            if (c0 + u == NQ) ph += x * x;
-            else pj += x * x;
+            if (c0 + u == NQ) df_fma(ph, xv[u], xv[u]);
+            else df_fma(pj, xv[u], xv[u]);
         }
         if (hi) {
-            size_t base = (size_t)r * seg + 4 * e;
+            const size_t at = 4 * (ch.base4 + e);
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                __nv_bfloat16 h = __float2bfloat16_rn(vv[u]);
-                hi[base + u] = h;
-                lo[base + u] = __float2bfloat16_rn(vv[u] - __bfloat162float(h));
+                const __nv_bfloat16 h = __float2bfloat16_rn(xv[u]);
+                hi[at + u] = h;
+                lo[at + u] = __float2bfloat16_rn(xv[u] - __bfloat162float(h));
             }
         }
     }
-    block_sum2_d(pj, ph, red);
-    if (threadIdx.x == 0) s.pen_t = p.lambda_h * ph + p.lambda_Jp * pj;
+    double v[2] = {df_value(pj), df_value(ph)};
+    block_write<2>(v, part_rec(part, nch));
 }
 
-__device__ double safe_interp(double lo, double flo, double dlo, double hi,
-                              double fhi, double dhi)
+// partial g_t . d and ||g_t||^2 (slots 2 and 3; slots 0, 1 hold the penalty)
+__global__ void __launch_bounds__(LB_THREADS)
+k_ls_dots(const SiteState *ss, const float *__restrict__ g_t, const float *__restrict__ dir,
+          Dims d, double *part, int nch)
+{
+    const SiteState &s = ss[blockIdx.y];
+    if (s.status != SITE_SEARCHING) return;
+    const Chunk ch = chunk_of(d);
+    const float4 *gt4 = (const float4 *)g_t + ch.base4;
+    const float4 *d4 = (const float4 *)dir + ch.base4;
+    DF dgt, gn2;
+    for (size_t e = ch.e0 + threadIdx.x; e < ch.e1; e += LB_THREADS) {
+        const float4 gv = gt4[e];
+        df_dot4(dgt, gv, d4[e]);
+        df_dot4(gn2, gv, gv);
+    }
+    double v[2] = {df_value(dgt), df_value(gn2)};
+    block_write<2>(v, part_rec(part, nch) + 2);
+}
+
+__device__ double safe_interp(double lo, double flo, double dlo, double hi, double fhi,
+                              double dhi)
 {
     // minimiser of the cubic through (lo, flo, dlo) and (hi, fhi, dhi),
-    // kept inside the middle 80% of the interval; bisection otherwise
-    double a = lo, b = hi;
-    double d1 = dlo + dhi - 3.0 * (flo - fhi) / (a - b);
-    double disc = d1 * d1 - dlo * dhi;
-    double L = fmin(a, b), H = fmax(a, b);
+    // kept inside the middle 80% of the interval; secant on phi' or
+    // bisection otherwise
+    const double a = lo, b = hi;
+    const double d1 = dlo + dhi - 3.0 * (flo - fhi) / (a - b);
+    const double disc = d1 * d1 - dlo * dhi;
+    const double L = fmin(a, b), H = fmax(a, b);
+    const double mg = 0.1 * (H - L);
     if (disc >= 0.0 && isfinite(disc)) {
         double d2 = sqrt(disc);
         if (b < a) d2 = -d2;
-        double den = dhi - dlo + 2.0 * d2;
+        const double den = dhi - dlo + 2.0 * d2;
         if (den != 0.0) {
-            double t = b - (b - a) * (dhi + d2 - d1) / den;
-            double mg = 0.1 * (H - L);
+            const double t = b - (b - a) * (dhi + d2 - d1) / den;
             if (isfinite(t) && t >= L + mg && t <= H - mg) return t;
         }
     }
-    // secant on the derivative (phi' is monotone for a convex objective)
     if (dlo < 0.0 && dhi > 0.0) {
-        double t = a - dlo * (b - a) / (dhi - dlo);
-        double mg = 0.1 * (H - L);
+        const double t = a - dlo * (b - a) / (dhi - dlo);
         if (isfinite(t) && t >= L + mg && t <= H - mg) return t;
     }
     return 0.5 * (a + b);
@@ -267,184 +418,181 @@ __device__ double safe_interp(double lo, double flo, double dlo, double hi,
 
 enum { LS_CONTINUE = 0, LS_ACCEPT = 1, LS_FAIL = 2 };
 
-// consumes the evaluation at theta_t; one thread per site makes the decision
-__global__ void __launch_bounds__(LB_THREADS)
-k_linesearch(SiteState *ss, const double *__restrict__ f_data,
-             float *__restrict__ theta, float *__restrict__ g,
-             const float *__restrict__ theta_t, const float *__restrict__ g_t,
-             const float *__restrict__ dir, float *__restrict__ S_hist,
-             float *__restrict__ Y_hist, Dims d, SolveParams p,
-             int *__restrict__ counters)
+__global__ void k_ls_decide(SiteState *ss, const double *__restrict__ f_data, const double *part,
+                            int nch, SolveParams p, int round, int *counters)
 {
-    __shared__ double red[LB_THREADS / 16];
-    __shared__ int action;
     const int r = blockIdx.x;
     SiteState &s = ss[r];
     if (s.status != SITE_SEARCHING) return;
-    const size_t seg = d.site_elems();
-    const size_t n4 = seg / 4;
-    const float4 *gt4 = (const float4 *)(g_t + (size_t)r * seg);
-    const float4 *d4 = (const float4 *)(dir + (size_t)r * seg);
-    double dgt = 0.0, gn2 = 0.0;
-    for (size_t e = threadIdx.x; e < n4; e += blockDim.x) {
-        float4 gv = gt4[e];
-        dgt += dot4(gv, d4[e]);
-        gn2 += dot4(gv, gv);
-    }
-    block_sum2_d(dgt, gn2, red);
-
-    if (threadIdx.x == 0) {
-        const double ft = f_data[r] + s.pen_t;
-        const double a = s.alpha, f0 = s.f0, dg0 = s.dg0;
-        const double eps = p.noise * fmax(1.0, fabs(f0));
-        const bool decrease = (ft <= f0 + p.c1 * a * dg0 + eps) || (dgt <= p.c1 * dg0);
-        const bool curv = fabs(dgt) <= p.c2 * fabs(dg0);
-        int act = LS_CONTINUE;
-        s.trials++;
-        if (!isfinite(ft) || !isfinite(dgt)) {
-            // step far too long: shrink towards the last good point
-            s.a_hi = a;
-            s.f_hi = INFINITY;
-            s.dg_hi = INFINITY;
+    const double *pr = part + (size_t)r * nch * LB_PART;
+    const double pj = chunk_sum(pr, nch, 0);
+    const double ph = chunk_sum(pr, nch, 1);
+    const double dgt = chunk_sum(pr, nch, 2);
+    const double gn2 = chunk_sum(pr, nch, 3);
+    if (threadIdx.x != 0) return;
+    s.pen_t = p.lambda_h * ph + p.lambda_Jp * pj;
+    const double ft = f_data[r] + s.pen_t;
+    const double a = s.alpha, f0 = s.f0, dg0 = s.dg0;
+    const double eps = p.noise * fmax(1.0, fabs(f0));
+    const bool decrease = (ft <= f0 + p.c1 * a * dg0 + eps) || (dgt <= p.c1 * dg0);
+    const bool curv = fabs(dgt) <= p.c2 * fabs(dg0);
+    int act = LS_CONTINUE;
+    s.trials++;
+    if (!isfinite(ft) || !isfinite(dgt)) {
+        s.a_hi = a;
+        s.f_hi = INFINITY;
+        s.dg_hi = INFINITY;
+        s.phase = 1;
+        s.alpha = 0.5 * (s.a_lo + a);
+    } else if (decrease && curv) {
+        act = LS_ACCEPT;
+    } else if (s.phase == 0) {
+        if (!decrease || dgt > 0.0) {
+            s.a_lo = s.a_prev; s.f_lo = s.f_prev; s.dg_lo = s.dg_prev;
+            s.a_hi = a; s.f_hi = ft; s.dg_hi = dgt;
             s.phase = 1;
-            s.alpha = 0.5 * (s.a_lo + a);
-        } else if (decrease && curv) {
-            act = LS_ACCEPT;
-        } else if (s.phase == 0) {
-            if (!decrease || dgt > 0.0) {
-                // the minimiser along the line lies in (a_prev, a)
-                s.a_lo = s.a_prev; s.f_lo = s.f_prev; s.dg_lo = s.dg_prev;
-                s.a_hi = a; s.f_hi = ft; s.dg_hi = dgt;
-                s.phase = 1;
-            } else {
-                s.a_prev = a; s.f_prev = ft; s.dg_prev = dgt;
-                s.a_lo = a; s.f_lo = ft; s.dg_lo = dgt;
-                s.alpha = 4.0 * a;
-            }
         } else {
-            if (decrease && dgt < 0.0) {
-                s.a_lo = a; s.f_lo = ft; s.dg_lo = dgt;
-            } else {
-                s.a_hi = a; s.f_hi = ft; s.dg_hi = dgt;
-            }
+            s.a_prev = a; s.f_prev = ft; s.dg_prev = dgt;
+            s.a_lo = a; s.f_lo = ft; s.dg_lo = dgt;
+            s.alpha = 4.0 * a;
         }
-        if (act == LS_CONTINUE && s.phase == 1 && isfinite(s.f_hi))
-            s.alpha = safe_interp(s.a_lo, s.f_lo, s.dg_lo, s.a_hi, s.f_hi, s.dg_hi);
-        if (act == LS_CONTINUE && s.trials >= p.max_ls) act = LS_FAIL;
-        if (act == LS_CONTINUE && s.phase == 1 &&
-            fabs(s.a_hi - s.a_lo) <= 1e-12 * fmax(s.a_lo, s.a_hi))
-            act = LS_FAIL;
-        if (act == LS_ACCEPT) {
-            s.f = ft;
-            s.gnorm2 = gn2;
-        } else if (act == LS_FAIL) {
-            // a failed search near the optimum is the FP32 noise floor
-            s.status = (fabs(ft - f0) <= eps) ? SITE_NOISE : SITE_FAILED;
+    } else {
+        if (decrease && dgt < 0.0) {
+            s.a_lo = a; s.f_lo = ft; s.dg_lo = dgt;
+        } else {
+            s.a_hi = a; s.f_hi = ft; s.dg_hi = dgt;
         }
-        action = act;
     }
-    __syncthreads();
-    if (action == LS_CONTINUE) {
-        if (threadIdx.x == 0) atomicAdd(&counters[0], 1);
-        return;
+    if (act == LS_CONTINUE && s.phase == 1 && isfinite(s.f_hi))
+        s.alpha = safe_interp(s.a_lo, s.f_lo, s.dg_lo, s.a_hi, s.f_hi, s.dg_hi);
+    if (act == LS_CONTINUE && s.trials >= p.max_ls) act = LS_FAIL;
+    if (act == LS_CONTINUE && s.phase == 1 &&
+        fabs(s.a_hi - s.a_lo) <= 1e-12 * fmax(s.a_lo, s.a_hi))
+        act = LS_FAIL;
+    if (act == LS_CONTINUE) {
+        atomicAdd(&counters[0], 1);
+    } else if (act == LS_ACCEPT) {
+        s.commit_round = round;
+        s.commit_slot = s.head;
+        s.head = (s.head + 1) % p.m;
+        if (s.hist < p.m) s.hist++;
+        s.f = ft;
+        s.gnorm2 = gn2;
+        s.neg_g = 0;
+        s.iters++;
+        if (sqrt(gn2) <= p.gtol) s.status = SITE_CONVERGED;
+        else if (s.iters >= p.max_iter) s.status = SITE_FAILED;
+        else {
+            s.status = SITE_READY;
+            atomicAdd(&counters[1], 1);
+        }
+    } else {
+        // a failed search near the optimum is the FP32 noise floor
+        s.status = (fabs(ft - f0) <= eps) ? SITE_NOISE : SITE_FAILED;
     }
-    if (action != LS_ACCEPT) return;
+}
 
-    // commit: s = theta_t - theta, y = g_t - g, theta <- theta_t, g <- g_t
-    const int slot = s.head;
-    const size_t vec = d.theta_elems();
-    float4 *th4 = (float4 *)(theta + (size_t)r * seg);
-    float4 *g4 = (float4 *)(g + (size_t)r * seg);
-    const float4 *tt4 = (const float4 *)(theta_t + (size_t)r * seg);
-    float4 *sh4 = (float4 *)(S_hist + (size_t)slot * vec + (size_t)r * seg);
-    float4 *yh4 = (float4 *)(Y_hist + (size_t)slot * vec + (size_t)r * seg);
-    double sy = 0.0, yy = 0.0;
-    for (size_t e = threadIdx.x; e < n4; e += blockDim.x) {
-        float4 tn = tt4[e], to = th4[e], gn = gt4[e], go = g4[e];
-        float4 sv = make_float4(tn.x - to.x, tn.y - to.y, tn.z - to.z, tn.w - to.w);
-        float4 yv = make_float4(gn.x - go.x, gn.y - go.y, gn.z - go.z, gn.w - go.w);
-        sh4[e] = sv;
-        yh4[e] = yv;
+// commit the accepted trial points of this round: s = theta_t - theta,
+// y = g_t - g into the ring slot, theta <- theta_t, g <- g_t
+__global__ void __launch_bounds__(LB_THREADS)
+k_commit(const SiteState *ss, float *__restrict__ theta, float *__restrict__ g,
+         const float *__restrict__ theta_t, const float *__restrict__ g_t,
+         float *__restrict__ S, float *__restrict__ Y, Dims d, int round)
+{
+    const SiteState &s = ss[blockIdx.y];
+    if (s.commit_round != round) return;
+    const Chunk ch = chunk_of(d);
+    const size_t slot = (size_t)s.commit_slot;
+    float4 *th4 = (float4 *)theta + ch.base4;
+    float4 *g4 = (float4 *)g + ch.base4;
+    const float4 *tt4 = (const float4 *)theta_t + ch.base4;
+    const float4 *gt4 = (const float4 *)g_t + ch.base4;
+    float4 *s4 = (float4 *)S + slot * ch.vec4 + ch.base4;
+    float4 *y4 = (float4 *)Y + slot * ch.vec4 + ch.base4;
+    for (size_t e = ch.e0 + threadIdx.x; e < ch.e1; e += LB_THREADS) {
+        const float4 tn = tt4[e], to = th4[e], gn = gt4[e], go = g4[e];
+        s4[e] = make_float4(tn.x - to.x, tn.y - to.y, tn.z - to.z, tn.w - to.w);
+        y4[e] = make_float4(gn.x - go.x, gn.y - go.y, gn.z - go.z, gn.w - go.w);
         th4[e] = tn;
         g4[e] = gn;
-        sy += dot4(sv, yv);
-        yy += dot4(yv, yv);
-    }
-    block_sum2_d(sy, yy, red);
-    if (threadIdx.x == 0) {
-        if (sy > 0.0 && yy > 0.0) {
-            s.rho[slot] = 1.0 / sy;
-            s.gamma = sy / yy;
-            s.head = (slot + 1) % p.m;
-            if (s.hist < p.m) s.hist++;
-        }
-        s.iters++;
-        if (sqrt(s.gnorm2) <= p.gtol) s.status = SITE_CONVERGED;
-        else if (s.iters >= p.max_iter) s.status = SITE_FAILED;
-        else s.status = SITE_READY;
     }
 }
 
-__global__ void k_count(const SiteState *ss, int N, int *counters)
-{
-    int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= N) return;
-    int st = ss[r].status;
-    if (st == SITE_SEARCHING) atomicAdd(&counters[0], 1);
-    if (st == SITE_READY) atomicAdd(&counters[1], 1);
-}
+dim3 vec_grid(const Dims &d, int nch) { return dim3(nch, d.N); }
 
 }  // namespace
 
-cudaError_t launch_lbfgs_init(SiteState *ss, const double *f, const float *g,
-                              const Dims &d, const SolveParams &p,
-                              cudaStream_t st)
+int lbfgs_chunks(const Dims &d)
 {
-    k_init<<<d.N, LB_THREADS, 0, st>>>(ss, f, g, d, p);
-    count_launches(1);
+    const size_t seg4 = d.site_elems() / 4;
+    return (int)((seg4 + LB_CHUNK4 - 1) / LB_CHUNK4);
+}
+
+cudaError_t launch_lbfgs_init(SiteState *ss, const double *f, const float *g, const Dims &d,
+                              const SolveParams &p, double *part, cudaStream_t st)
+{
+    const int nch = lbfgs_chunks(d);
+    k_init_dots<<<vec_grid(d, nch), LB_THREADS, 0, st>>>(g, d, part, nch);
+    k_init_finish<<<d.N, 32, 0, st>>>(ss, f, part, nch, p);
+    count_launches(2);
     return cudaGetLastError();
+}
+
+template <int M>
+static void direction_m(SiteState *ss, const float *g, float *dir, const float *S,
+                        const float *Y, const Dims &d, double *part, int nch, cudaStream_t st)
+{
+    k_dir_dots<M><<<vec_grid(d, nch), LB_THREADS, 0, st>>>(ss, g, S, Y, d, part, nch);
+    k_dir_solve<M><<<d.N, 32, 0, st>>>(ss, part, nch);
+    k_dir_apply<M><<<vec_grid(d, nch), LB_THREADS, 0, st>>>(ss, g, S, Y, dir, d, part, nch);
 }
 
 cudaError_t launch_lbfgs_direction(SiteState *ss, const float *g, float *dir,
-                                   const float *S_hist, const float *Y_hist,
-                                   const Dims &d, const SolveParams &p,
-                                   cudaStream_t st)
+                                   const float *S_hist, const float *Y_hist, const Dims &d,
+                                   const SolveParams &p, double *part, cudaStream_t st)
 {
-    k_direction<<<d.N, LB_THREADS, 0, st>>>(ss, g, dir, S_hist, Y_hist, d, p);
-    count_launches(1);
+    const int nch = lbfgs_chunks(d);
+    switch (p.m) {
+    case 1: direction_m<1>(ss, g, dir, S_hist, Y_hist, d, part, nch, st); break;
+    case 2: direction_m<2>(ss, g, dir, S_hist, Y_hist, d, part, nch, st); break;
+    case 3: direction_m<3>(ss, g, dir, S_hist, Y_hist, d, part, nch, st); break;
+    case 4: direction_m<4>(ss, g, dir, S_hist, Y_hist, d, part, nch, st); break;
+    case 5: direction_m<5>(ss, g, dir, S_hist, Y_hist, d, part, nch, st); break;
+    case 6: direction_m<6>(ss, g, dir, S_hist, Y_hist, d, part, nch, st); break;
+    case 7: direction_m<7>(ss, g, dir, S_hist, Y_hist, d, part, nch, st); break;
+    case 8: direction_m<8>(ss, g, dir, S_hist, Y_hist, d, part, nch, st); break;
+    default: return cudaErrorInvalidValue;
+    }
+    k_dir_finish<<<d.N, 32, 0, st>>>(ss, part, nch);
+    count_launches(4);
     return cudaGetLastError();
 }
 
-cudaError_t launch_lbfgs_trial(SiteState *ss, const float *theta,
-                               const float *dir, float *theta_t,
-                               __nv_bfloat16 *hi, __nv_bfloat16 *lo,
-                               const Dims &d, const SolveParams &p,
+cudaError_t launch_lbfgs_trial(SiteState *ss, const float *theta, const float *g, float *dir,
+                               float *theta_t, __nv_bfloat16 *hi, __nv_bfloat16 *lo,
+                               const Dims &d, const SolveParams &p, double *part,
                                cudaStream_t st)
 {
-    k_trial<<<d.N, LB_THREADS, 0, st>>>(ss, theta, dir, theta_t, hi, lo, d, p);
+    (void)p;
+    const int nch = lbfgs_chunks(d);
+    k_trial<<<vec_grid(d, nch), LB_THREADS, 0, st>>>(ss, theta, g, dir, theta_t, hi, lo, d, part,
+                                                      nch);
     count_launches(1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_lbfgs_linesearch(SiteState *ss, const double *f_data,
-                                    float *theta, float *g,
-                                    const float *theta_t, const float *g_t,
-                                    const float *dir, float *S_hist,
-                                    float *Y_hist, const Dims &d,
-                                    const SolveParams &p, int *counters,
-                                    cudaStream_t st)
+cudaError_t launch_lbfgs_linesearch(SiteState *ss, const double *f_data, float *theta, float *g,
+                                    const float *theta_t, const float *g_t, const float *dir,
+                                    float *S_hist, float *Y_hist, const Dims &d,
+                                    const SolveParams &p, double *part, int round,
+                                    int *counters, cudaStream_t st)
 {
-    k_linesearch<<<d.N, LB_THREADS, 0, st>>>(ss, f_data, theta, g, theta_t, g_t,
-                                            dir, S_hist, Y_hist, d, p, counters);
-    count_launches(1);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_count_status(const SiteState *ss, int N, int *counters,
-                                cudaStream_t st)
-{
-    k_count<<<(N + 127) / 128, 128, 0, st>>>(ss, N, counters);
-    count_launches(1);
+    const int nch = lbfgs_chunks(d);
+    k_ls_dots<<<vec_grid(d, nch), LB_THREADS, 0, st>>>(ss, g_t, dir, d, part, nch);
+    k_ls_decide<<<d.N, 32, 0, st>>>(ss, f_data, part, nch, p, round, counters);
+    k_commit<<<vec_grid(d, nch), LB_THREADS, 0, st>>>(ss, theta, g, theta_t, g_t, S_hist, Y_hist,
+                                                       d, round);
+    count_launches(3);
     return cudaGetLastError();
 }
 

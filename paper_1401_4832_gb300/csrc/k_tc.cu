@@ -338,8 +338,9 @@ k_tc_logits(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ C
                 break;
             uint8_t *rowp = smem + s * LG_STAGE + p * 128;
             const uint4 z = make_uint4(0, 0, 0, 0);
+            // rotate the chunk order by row so a warp's stores spread over the banks
 #pragma unroll
-            for (int j = 0; j < 8; ++j) *(uint4 *)(rowp + j * 16) = z;
+            for (int j = 0; j < 8; ++j) *(uint4 *)(rowp + ((j + p) & 7) * 16) = z;
             if (valid) {
                 const int c0 = kc * TC_BK;
                 const int i_lo = c0 / Q;
@@ -358,13 +359,17 @@ k_tc_logits(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ C
             mbar_arrive(&full_a[s]);
         }
 
-        // ---- epilogue: one sequence per thread, its TMEM lane
+        // ---- epilogue: one sequence per thread, its TMEM lane.  The residual
+        // tile is staged in the (now idle) pipeline buffers as D^T rows of
+        // 128 sequences, then written out with 16-byte stores.
         const int q4 = warp & 3;
         const int er = q4 * 32 + lane;
         const int eb = b0 + er;
         const bool ev = eb < d.B;
-        bool ok = mbar_wait(&acc_full, 0, &abort_sh, err, ERR_TIMEOUT_EPI);
+        const bool ok = mbar_wait(&acc_full, 0, &abort_sh, err, ERR_TIMEOUT_EPI);
         tc_fence_after();
+        __nv_bfloat16 *st_hi = (__nv_bfloat16 *)smem;            // [LG_N][128]
+        __nv_bfloat16 *st_lo = st_hi + LG_N * TC_M;              // [LG_N][128]
         const float wb = ev ? w[eb] : 0.0f;
         const float scale = (float)((double)wb * inv_beff);
         const uint32_t tl = tmem + ((uint32_t)(q4 * 32) << 16);
@@ -381,29 +386,28 @@ k_tc_logits(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ C
                 const int r = r0 + j;
                 const float *l = v + 24 * h;
                 double contrib = 0.0;
-                if (r < d.N && ok) {
-                    float mx = l[0];
+                float mx = l[0];
 #pragma unroll
-                    for (int s = 1; s < Q; ++s) mx = fmaxf(mx, l[s]);
-                    float z = 0.0f;
+                for (int s2 = 1; s2 < Q; ++s2) mx = fmaxf(mx, l[s2]);
+                float z = 0.0f;
 #pragma unroll
-                    for (int s = 0; s < Q; ++s) z += __expf(l[s] - mx);
-                    const float lse = mx + __logf(z);
-                    const int sr = ev ? msa[(size_t)eb * d.N + r] : -1;
-                    float lsr = 0.0f;
+                for (int s2 = 0; s2 < Q; ++s2) z += __expf(l[s2] - mx);
+                const float lse = mx + __logf(z);
+                const int sr = (ev && r < d.N) ? msa[(size_t)eb * d.N + r] : -1;
+                float lsr = 0.0f;
 #pragma unroll
-                    for (int s = 0; s < Q; ++s)
-                        if (s == sr) lsr = l[s];
-                    if (ev) contrib = (double)wb * (double)(lsr - lse);
-                    const size_t base = (size_t)(row0 + j * QP) * BP + eb;
+                for (int s2 = 0; s2 < Q; ++s2)
+                    if (s2 == sr) lsr = l[s2];
+                if (ev && r < d.N && ok) contrib = (double)wb * (double)(lsr - lse);
 #pragma unroll
-                    for (int s = 0; s < QP; ++s) {
-                        float dv = 0.0f;
-                        if (s < Q && ev) dv = scale * (__expf(l[s] - lse) - (s == sr ? 1.0f : 0.0f));
-                        const __nv_bfloat16 hi = __float2bfloat16_rn(dv);
-                        dt_hi[base + (size_t)s * BP] = hi;
-                        dt_lo[base + (size_t)s * BP] = __float2bfloat16_rn(dv - __bfloat162float(hi));
-                    }
+                for (int s2 = 0; s2 < QP; ++s2) {
+                    float dv = 0.0f;
+                    if (s2 < Q && ev && r < d.N)
+                        dv = scale * (__expf(l[s2] - lse) - (s2 == sr ? 1.0f : 0.0f));
+                    const __nv_bfloat16 hi = __float2bfloat16_rn(dv);
+                    st_hi[(j * QP + s2) * TC_M + er] = hi;
+                    st_lo[(j * QP + s2) * TC_M + er] =
+                        __float2bfloat16_rn(dv - __bfloat162float(hi));
                 }
                 contrib = warp_sum_d(contrib);
                 if (lane == 0) red[q4][j] = contrib;
@@ -413,6 +417,17 @@ k_tc_logits(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ C
         const int t = threadIdx.x - 64;
         if (t < LG_SITES && r0 + t < d.N)
             partial[(size_t)tb * d.N + r0 + t] = ((red[0][t] + red[1][t]) + red[2][t]) + red[3][t];
+        // copy-out: row (r,s) of the tile = 128 sequences = 256 bytes = 16 x 16 B
+        const int nrows = min(LG_N, d.R - row0);
+        for (int e = t; e < 2 * LG_N * 16; e += 128) {
+            const int half = e / (LG_N * 16);
+            const int rem = e % (LG_N * 16);
+            const int row = rem / 16, c16 = rem % 16;
+            if (row >= nrows) continue;
+            const __nv_bfloat16 *src = (half ? st_lo : st_hi) + row * TC_M + c16 * 8;
+            __nv_bfloat16 *dst = (half ? dt_lo : dt_hi) + (size_t)(row0 + row) * BP + b0 + c16 * 8;
+            *(uint4 *)dst = *(const uint4 *)src;
+        }
     }
     tc_fence_before();
     __syncthreads();
@@ -549,40 +564,48 @@ k_tc_grad(const __grid_constant__ CUtensorMap tm_dhi, const __grid_constant__ CU
             mbar_arrive(&full_a[s]);
         }
 
-        // ---- epilogue: one row (r,s) per thread, 256 columns in chunks of 16
+        // ---- epilogue: TMEM -> shared (rows padded to 260 floats so the
+        // lane-per-row stores spread over the banks), then a coalesced pass
+        // adds 2 lambda Theta, applies the masks and writes G.
         const int q4 = warp & 3;
-        const int row = rs0 + q4 * 32 + lane;
+        const int trow = q4 * 32 + lane;
         const bool ok = mbar_wait(&acc_full, 0, &abort_sh, err, ERR_TIMEOUT_EPI);
         tc_fence_after();
+        constexpr int GS = GR_N + 4;
+        float *acc_s = (float *)smem;  // [128][GS]
         const uint32_t tl = tmem + ((uint32_t)(q4 * 32) << 16);
-        const int r = row / QP, sstate = row % QP;
-        const bool row_ok = ok && row < d.R;
-        const bool pad_row = sstate >= Q;
 #pragma unroll 1
         for (int cc = 0; cc < GR_N / 16; ++cc) {
             float v[16];
             tmem_ld16(tl + cc * 16, v);
             tmem_wait_ld();
-            const int cb = c0 + cc * 16;
-            if (!row_ok || cb >= d.KP) continue;
-            const float4 *th = (const float4 *)(theta + (size_t)row * d.KP + cb);
-            float4 *g = (float4 *)(G + (size_t)row * d.KP + cb);
+            float4 *dst = (float4 *)(acc_s + trow * GS + cc * 16);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const float4 t = th[q];
-                const float tv[4] = {t.x, t.y, t.z, t.w};
-                float o[4];
+            for (int q = 0; q < 4; ++q)
+                dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        }
+        epi_bar();
+        const int t = threadIdx.x - 64;
+        for (int e = t; e < TC_M * (GR_N / 4); e += 128) {
+            const int rr = e / (GR_N / 4), c4 = e % (GR_N / 4);
+            const int row = rs0 + rr;
+            const int cb = c0 + 4 * c4;
+            if (!ok || row >= d.R || cb >= d.KP) continue;
+            const int r = row / QP, sstate = row % QP;
+            const float4 a = *(const float4 *)(acc_s + rr * GS + 4 * c4);
+            const float4 th = *(const float4 *)(theta + (size_t)row * d.KP + cb);
+            const float av[4] = {a.x, a.y, a.z, a.w}, tv[4] = {th.x, th.y, th.z, th.w};
+            float o[4];
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int c = cb + 4 * q + e;
-                    float val;
-                    if (pad_row || c > NQ || (c >= r * Q && c < r * Q + Q)) val = 0.0f;
-                    else if (c == NQ) val = v[4 * q + e] + two_lh * tv[e];
-                    else val = v[4 * q + e] + two_lj * tv[e];
-                    o[e] = val;
-                }
-                g[q] = make_float4(o[0], o[1], o[2], o[3]);
+            for (int u = 0; u < 4; ++u) {
+                const int c = cb + u;
+                float val;
+                if (sstate >= Q || c > NQ || (c >= r * Q && c < r * Q + Q)) val = 0.0f;
+                else if (c == NQ) val = av[u] + two_lh * tv[u];
+                else val = av[u] + two_lj * tv[u];
+                o[u] = val;
             }
+            *(float4 *)(G + (size_t)row * d.KP + cb) = make_float4(o[0], o[1], o[2], o[3]);
         }
     }
     tc_fence_before();

@@ -593,28 +593,34 @@ plm_status plm_solve(plm_ctx *ctx, const int8_t *msa, int B, int N, int q,
     }
     int evals = 0;
     int *tc_err = (int *)cnt + 4;  // tensor-core timeout word, read back with the counters
+    void *part;
+    CK(ws(ctx, "lb_part", (size_t)N * lbfgs_chunks(d) * LB_PART * sizeof(double), &part));
     CK(cudaMemsetAsync(cnt, 0, 16 * sizeof(int), st));
     s = evaluate(ctx, o.prec, S, (const float *)w, beff, d, (const float *)theta,
                  (const __nv_bfloat16 *)hi, (const __nv_bfloat16 *)lo, p.lambda_h,
                  p.lambda_Jp, (double *)fdat, (float *)g, tc_err);
     if (s) return s;
     evals++;
-    CK(launch_lbfgs_init((SiteState *)sst, (const double *)fdat, (const float *)g, d, p, st));
+    CK(launch_lbfgs_init((SiteState *)sst, (const double *)fdat, (const float *)g, d, p,
+                         (double *)part, st));
 
     int *hc = ctx->host_counters;
+    int round = 0;
     for (int it = 0; it < o.max_iter; ++it) {
         CK(cudaMemsetAsync(cnt, 0, 2 * sizeof(int), st));
         {
             ProfScope ps(ctx, "lbfgs_direction");
             CK(launch_lbfgs_direction((SiteState *)sst, (const float *)g, (float *)dir,
-                                      (const float *)Sh, (const float *)Yh, d, p, st));
+                                      (const float *)Sh, (const float *)Yh, d, p,
+                                      (double *)part, st));
         }
         for (int ls = 0; ls < o.max_ls + 1; ++ls) {
+            ++round;
             {
                 ProfScope ps(ctx, "lbfgs_trial");
-                CK(launch_lbfgs_trial((SiteState *)sst, (const float *)theta, (const float *)dir,
-                                      (float *)theta_t, (__nv_bfloat16 *)hi, (__nv_bfloat16 *)lo,
-                                      d, p, st));
+                CK(launch_lbfgs_trial((SiteState *)sst, (const float *)theta, (const float *)g,
+                                      (float *)dir, (float *)theta_t, (__nv_bfloat16 *)hi,
+                                      (__nv_bfloat16 *)lo, d, p, (double *)part, st));
             }
             s = evaluate(ctx, o.prec, S, (const float *)w, beff, d, (const float *)theta_t,
                          (const __nv_bfloat16 *)hi, (const __nv_bfloat16 *)lo, p.lambda_h,
@@ -627,7 +633,8 @@ plm_status plm_solve(plm_ctx *ctx, const int8_t *msa, int B, int N, int q,
                 CK(launch_lbfgs_linesearch((SiteState *)sst, (const double *)fdat,
                                            (float *)theta, (float *)g, (const float *)theta_t,
                                            (const float *)g_t, (const float *)dir, (float *)Sh,
-                                           (float *)Yh, d, p, (int *)cnt, st));
+                                           (float *)Yh, d, p, (double *)part, round, (int *)cnt,
+                                           st));
             }
             CK(cudaMemcpyAsync(hc, cnt, 5 * sizeof(int), cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
@@ -636,10 +643,6 @@ plm_status plm_solve(plm_ctx *ctx, const int8_t *msa, int B, int N, int q,
                             hc[4]);
             if (hc[0] == 0) break;
         }
-        CK(cudaMemsetAsync(cnt, 0, 2 * sizeof(int), st));
-        CK(launch_count_status((const SiteState *)sst, N, (int *)cnt, st));
-        CK(cudaMemcpyAsync(hc, cnt, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
         if (hc[1] == 0) break;  // no site left to iterate
     }
 

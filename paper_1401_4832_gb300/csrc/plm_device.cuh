@@ -1,5 +1,6 @@
 // plm_device.cuh -- small device helpers shared by the library's kernels:
-// fixed-order (deterministic) block reductions in FP64.
+// fixed-order (deterministic) block reductions in FP64, and double-float
+// accumulation of FP32 products.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -47,6 +48,41 @@ __device__ __forceinline__ void block_sum2_d(double &a, double &b, double *red)
     }
     a = ta;
     b = tb;
+}
+
+// Double-float accumulator of products of FP32 numbers, in FP32 arithmetic.
+// Each product is split exactly into p + e (Dekker's two-product, with the
+// FMA giving the rounding error of a*b) and added to (hi, lo) with Knuth's
+// two-sum, so hi + lo carries about 44 significant bits -- FP64-class inner
+// products at FP32 throughput (the FP64 pipe of this GPU is ~1/64 of FP32).
+// The _rn intrinsics keep the compiler from fusing or reassociating the
+// error-free transformations.
+struct DF {
+    float hi = 0.0f, lo = 0.0f;
+};
+
+__device__ __forceinline__ void df_fma(DF &s, float a, float b)
+{
+    const float p = __fmul_rn(a, b);
+    const float e = fmaf(a, b, -p);  // a*b - p, exact
+    const float t = __fadd_rn(s.hi, p);
+    const float bp = __fsub_rn(t, s.hi);
+    const float err = __fadd_rn(__fsub_rn(s.hi, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+    s.hi = t;
+    s.lo = __fadd_rn(s.lo, __fadd_rn(err, e));
+}
+
+__device__ __forceinline__ void df_dot4(DF &s, const float4 a, const float4 b)
+{
+    df_fma(s, a.x, b.x);
+    df_fma(s, a.y, b.y);
+    df_fma(s, a.z, b.z);
+    df_fma(s, a.w, b.w);
+}
+
+__device__ __forceinline__ double df_value(const DF &s)
+{
+    return (double)s.hi + (double)s.lo;
 }
 
 }  // namespace plm

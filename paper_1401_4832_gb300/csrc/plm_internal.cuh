@@ -61,7 +61,8 @@ enum SiteStatus : int {
     SITE_FAILED = 4,     // max_iter reached or a bad direction
 };
 
-constexpr int MAX_M = 16;
+constexpr int MAX_M = 8;             // largest L-BFGS memory
+constexpr int LB_PART = 4 * MAX_M;   // doubles per (site, chunk) partial record
 
 struct SiteState {
     double f;        // objective at theta
@@ -71,15 +72,20 @@ struct SiteState {
     double a_prev, f_prev, dg_prev;
     double a_lo, f_lo, dg_lo, a_hi, f_hi, dg_hi;
     double pen_t;    // penalty at the trial point
-    double fdata_t;  // data term at the trial point
-    double rho[MAX_M];
     double gamma;    // s'y / y'y of the newest pair
+    double SY[MAX_M][MAX_M];  // s_i . y_j by ring slot (entries with i older than or equal to j used)
+    double YY[MAX_M][MAX_M];  // y_i . y_j by ring slot
+    double cg;                 // direction: d = -(cg g + sum cs_j s_j + sum cy_j y_j)
+    double cs[MAX_M], cy[MAX_M];
     int status;
     int phase;       // 0: bracketing, 1: zoom
     int trials;
     int iters;
     int hist, head;  // stored pairs, next ring slot
-    int pad_[2];
+    int neg_g;       // 1: the computed direction was not a descent direction; use -g
+    int commit_round;  // line-search round whose trial point is committed (-1: none)
+    int commit_slot;
+    int pad_;
 };
 
 struct SolveParams {
@@ -131,30 +137,35 @@ cudaError_t launch_grad_gather(const int8_t *msa, const float *D,
                                cudaStream_t st);
 
 // ---- L-BFGS (k_lbfgs.cu) ----
-cudaError_t launch_lbfgs_init(SiteState *st_, const double *f,
-                              const float *g, const Dims &d,
-                              const SolveParams &p, cudaStream_t st);
+// Every vector kernel runs on a (chunk, site) grid: the site's segment of
+// QP*KP floats is cut into lbfgs_chunks(d) chunks; partial FP64 sums go to
+// part[(site * nchunks + chunk) * LB_PART + k] and are reduced per site in
+// a fixed order by the one-warp-per-site scalar kernels.
+int lbfgs_chunks(const Dims &d);
+cudaError_t launch_lbfgs_init(SiteState *ss, const double *f, const float *g,
+                              const Dims &d, const SolveParams &p, double *part,
+                              cudaStream_t st);
+// direction d = -H g (compact representation) and line-search set-up
 cudaError_t launch_lbfgs_direction(SiteState *ss, const float *g, float *dir,
                                    const float *S_hist, const float *Y_hist,
                                    const Dims &d, const SolveParams &p,
-                                   cudaStream_t st);
+                                   double *part, cudaStream_t st);
 cudaError_t launch_lbfgs_trial(SiteState *ss, const float *theta,
-                               const float *dir, float *theta_t,
+                               const float *g, float *dir, float *theta_t,
                                __nv_bfloat16 *hi, __nv_bfloat16 *lo,
-                               const Dims &d, const SolveParams &p,
+                               const Dims &d, const SolveParams &p, double *part,
                                cudaStream_t st);
-// consumes f_data[r] (data part of the objective at theta_t, FP64) and
-// g_t; decides per site, commits accepted steps; counts searching sites
+// consumes f_data[r] (data part of the objective at theta_t) and g_t; the
+// decision is taken per site; accepted steps are committed in the same call
+// (S, Y, theta, g updated).  counters[0] += #sites still searching,
+// counters[1] += #sites that became ready for a new direction.
 cudaError_t launch_lbfgs_linesearch(SiteState *ss, const double *f_data,
                                     float *theta, float *g,
                                     const float *theta_t, const float *g_t,
                                     const float *dir, float *S_hist,
                                     float *Y_hist, const Dims &d,
-                                    const SolveParams &p, int *counters,
-                                    cudaStream_t st);
-// counters[0] = #searching, counters[1] = #ready
-cudaError_t launch_count_status(const SiteState *ss, int N, int *counters,
-                                cudaStream_t st);
+                                    const SolveParams &p, double *part,
+                                    int round, int *counters, cudaStream_t st);
 
 // ---- scores (k_scores.cu) ----
 cudaError_t launch_fn(const float *J, int N, int combine, double *fn,
