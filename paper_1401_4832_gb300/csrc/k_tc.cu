@@ -332,8 +332,21 @@ k_tc_logits(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ C
         const int b = b0 + p;
         const bool valid = b < d.B;
         const int8_t *srow = msa + (size_t)(valid ? b : 0) * d.N;
+        // states of the (at most 5) positions a chunk of 64 columns touches,
+        // fetched one chunk ahead
+        auto fetch = [&](int kc, int (&st5)[5]) {
+            const int i_lo = (kc * TC_BK) / Q;
+#pragma unroll
+            for (int u = 0; u < 5; ++u) {
+                const int i = i_lo + u;
+                st5[u] = (valid && i < d.N) ? (int)srow[i] : 0;
+            }
+        };
+        int cur5[5], nxt5[5];
+        fetch(0, cur5);
         for (int kc = 0; kc < NK; ++kc) {
             const int s = kc % STAGES, n = kc / STAGES;
+            fetch(kc + 1 < NK ? kc + 1 : kc, nxt5);
             if (n > 0 && !mbar_wait(&empty_[s], (n - 1) & 1, &abort_sh, err, ERR_TIMEOUT_PROD))
                 break;
             uint8_t *rowp = smem + s * LG_STAGE + p * 128;
@@ -344,10 +357,11 @@ k_tc_logits(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ C
             if (valid) {
                 const int c0 = kc * TC_BK;
                 const int i_lo = c0 / Q;
-                const int i_hi = min((c0 + TC_BK - 1) / Q, d.N - 1);
-                for (int i = i_lo; i <= i_hi; ++i) {
-                    const int pos = i * Q + srow[i] - c0;
-                    if (pos >= 0 && pos < TC_BK)
+#pragma unroll
+                for (int u = 0; u < 5; ++u) {
+                    const int i = i_lo + u;
+                    const int pos = i * Q + cur5[u] - c0;
+                    if (i < d.N && pos >= 0 && pos < TC_BK)
                         *(uint16_t *)(rowp + ((((pos >> 3) ^ (p & 7)) << 4) | ((pos & 7) << 1))) =
                             0x3F80;
                 }
@@ -357,6 +371,8 @@ k_tc_logits(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ C
             }
             fence_proxy_async();
             mbar_arrive(&full_a[s]);
+#pragma unroll
+            for (int u = 0; u < 5; ++u) cur5[u] = nxt5[u];
         }
 
         // ---- epilogue: one sequence per thread, its TMEM lane.  The residual
@@ -536,18 +552,32 @@ k_tc_grad(const __grid_constant__ CUtensorMap tm_dhi, const __grid_constant__ CU
             src_i[u] = i;
             kk[u] = k * 0x01010101u;
         }
+        // the next stage's MSA bytes are fetched while the current stage is
+        // written, so the global-load latency overlaps the pipeline
+        uint4 cur[2][4], nxt[2][4];
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                cur[u][q] = __ldg((const uint4 *)(msaT + (size_t)src_i[u] * BP) + q);
         for (int kc = 0; kc < NK; ++kc) {
             const int s = kc % STAGES, n = kc / STAGES;
+            const int kn = kc + 1 < NK ? kc + 1 : kc;
+#pragma unroll
+            for (int u = 0; u < 2; ++u)
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    nxt[u][q] =
+                        __ldg((const uint4 *)(msaT + (size_t)src_i[u] * BP + kn * TC_BK) + q);
             if (n > 0 && !mbar_wait(&empty_[s], (n - 1) & 1, &abort_sh, err, ERR_TIMEOUT_PROD))
                 break;
             uint8_t *bt = smem + s * GR_STAGE + 2 * GR_A_BYTES;
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
                 const int row = p + 128 * u;
-                const uint4 *src = (const uint4 *)(msaT + (size_t)src_i[u] * BP + kc * TC_BK);
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {  // 16 sequences per load
-                    const uint4 x = __ldg(src + q);
+                for (int q = 0; q < 4; ++q) {  // 16 sequences per word group
+                    const uint4 x = cur[u][q];
                     const uint32_t xs[4] = {x.x, x.y, x.z, x.w};
                     uint32_t o[8];
 #pragma unroll
@@ -562,6 +592,10 @@ k_tc_grad(const __grid_constant__ CUtensorMap tm_dhi, const __grid_constant__ CU
             }
             fence_proxy_async();
             mbar_arrive(&full_a[s]);
+#pragma unroll
+            for (int u = 0; u < 2; ++u)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) cur[u][q] = nxt[u][q];
         }
 
         // ---- epilogue: TMEM -> shared (rows padded to 260 floats so the
@@ -586,26 +620,41 @@ k_tc_grad(const __grid_constant__ CUtensorMap tm_dhi, const __grid_constant__ CU
         }
         epi_bar();
         const int t = threadIdx.x - 64;
-        for (int e = t; e < TC_M * (GR_N / 4); e += 128) {
-            const int rr = e / (GR_N / 4), c4 = e % (GR_N / 4);
-            const int row = rs0 + rr;
-            const int cb = c0 + 4 * c4;
-            if (!ok || row >= d.R || cb >= d.KP) continue;
-            const int r = row / QP, sstate = row % QP;
-            const float4 a = *(const float4 *)(acc_s + rr * GS + 4 * c4);
-            const float4 th = *(const float4 *)(theta + (size_t)row * d.KP + cb);
-            const float av[4] = {a.x, a.y, a.z, a.w}, tv[4] = {th.x, th.y, th.z, th.w};
-            float o[4];
+        constexpr int UNR = 8;
+        for (int e0 = t; e0 < TC_M * (GR_N / 4); e0 += 128 * UNR) {
+            float4 th[UNR];
+            bool live[UNR];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int c = cb + u;
-                float val;
-                if (sstate >= Q || c > NQ || (c >= r * Q && c < r * Q + Q)) val = 0.0f;
-                else if (c == NQ) val = av[u] + two_lh * tv[u];
-                else val = av[u] + two_lj * tv[u];
-                o[u] = val;
+            for (int k = 0; k < UNR; ++k) {  // issue all loads first
+                const int e = e0 + 128 * k;
+                const int rr = e / (GR_N / 4), c4 = e % (GR_N / 4);
+                const int row = rs0 + rr, cb = c0 + 4 * c4;
+                live[k] = ok && e < TC_M * (GR_N / 4) && row < d.R && cb < d.KP;
+                th[k] = live[k] ? *(const float4 *)(theta + (size_t)row * d.KP + cb)
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
             }
-            *(float4 *)(G + (size_t)row * d.KP + cb) = make_float4(o[0], o[1], o[2], o[3]);
+#pragma unroll
+            for (int k = 0; k < UNR; ++k) {
+                if (!live[k]) continue;
+                const int e = e0 + 128 * k;
+                const int rr = e / (GR_N / 4), c4 = e % (GR_N / 4);
+                const int row = rs0 + rr, cb = c0 + 4 * c4;
+                const int r = row / QP, sstate = row % QP;
+                const float4 a = *(const float4 *)(acc_s + rr * GS + 4 * c4);
+                const float av[4] = {a.x, a.y, a.z, a.w};
+                const float tv[4] = {th[k].x, th[k].y, th[k].z, th[k].w};
+                float o[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int c = cb + u;
+                    float val;
+                    if (sstate >= Q || c > NQ || (c >= r * Q && c < r * Q + Q)) val = 0.0f;
+                    else if (c == NQ) val = av[u] + two_lh * tv[u];
+                    else val = av[u] + two_lj * tv[u];
+                    o[u] = val;
+                }
+                *(float4 *)(G + (size_t)row * d.KP + cb) = make_float4(o[0], o[1], o[2], o[3]);
+            }
         }
     }
     tc_fence_before();
