@@ -164,8 +164,8 @@ plm_status plm_solve(plm_ctx *ctx, const int8_t *msa, int B, int N, int q,
  *   cfn_out  [N][N] double        out (may be NULL)
  *   topL_out [L][2] int32         out (may be NULL); rows beyond the number
  *                                 of eligible pairs are set to -1
- * Errors: PLM_EINVAL for N < 2, q != 21, L < 0, min_sep < 1, combine
- * outside 0..2. */
+ * Errors: PLM_EINVAL for N < 2, q != 21, L < 0 or L > 8192, min_sep < 1,
+ * combine outside 0..2. */
 plm_status fn_apc_scores(plm_ctx *ctx, const float *J, int N, int q,
                          int combine, double *fn_out, double *cfn_out,
                          int32_t *topL_out, int L, int min_sep);

@@ -106,52 +106,181 @@ __global__ void k_apc_apply(const double *__restrict__ fn, int N,
     cfn[idx] = (i == j) ? 0.0 : fn[idx] - (tot > 0.0 ? row[j] * row[i] / tot : 0.0);
 }
 
-// rank of pair (i,j) = number of eligible pairs ordered before it
-// (score descending, then i ascending, then j ascending)
-constexpr int TL_CHUNK = 1024;
+// ---- top-L selection ----------------------------------------------------
+// Order: score descending, then (i, j) ascending.  Each eligible pair gets a
+// 96-bit composite key (hi: the score's bits mapped to an order-preserving
+// unsigned integer; lo: 0xFFFFFFFF - (i N + j)), unique per pair, larger =
+// earlier.  A most-significant-byte-first radix select finds the L-th
+// largest key in 12 histogram passes; the pairs at or above it (exactly L)
+// are gathered and sorted by one CTA (bitonic sort).
 
-__global__ void __launch_bounds__(256)
-k_topL(const double *__restrict__ score, int N, int L, int min_sep,
-       int32_t *__restrict__ ij)
+struct SelState {
+    unsigned long long pre_hi;  // determined high part of the L-th key
+    unsigned int pre_lo;
+    unsigned int k;             // rank still to find inside the current prefix
+    unsigned int count;         // gathered candidates
+    unsigned int eligible;
+    unsigned int hist[256];
+};
+
+__device__ __forceinline__ unsigned long long score_key(double v)
 {
-    __shared__ double cs[TL_CHUNK];
-    __shared__ int ci[TL_CHUNK];
-    const long long total = (long long)N * N;
-    long long me = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    int mi = (int)(me / N), mj = (int)(me % N);
-    const bool valid = me < total && mj - mi >= min_sep;
-    const double ms = valid ? score[me] : 0.0;
-    long long rank = 0;
-    for (long long c0 = 0; c0 < total; c0 += TL_CHUNK) {
-        __syncthreads();
-        for (int t = threadIdx.x; t < TL_CHUNK; t += blockDim.x) {
-            long long o = c0 + t;
-            int oi = (int)(o / N), oj = (int)(o % N);
-            bool ok = o < total && oj - oi >= min_sep;
-            cs[t] = ok ? score[o] : 0.0;
-            ci[t] = ok ? 1 : 0;
-        }
-        __syncthreads();
-        if (valid) {
-            for (int t = 0; t < TL_CHUNK; ++t) {
-                if (!ci[t]) continue;
-                long long o = c0 + t;
-                double v = cs[t];
-                // row-major index order equals (i, j) ascending
-                if (v > ms || (v == ms && o < me)) rank++;
-            }
-        }
+    unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+__device__ __forceinline__ bool eligible(long long idx, int N, int min_sep)
+{
+    const int i = (int)(idx / N), j = (int)(idx % N);
+    return j - i >= min_sep;
+}
+
+// byte t (0 = most significant) of the composite key
+__device__ __forceinline__ unsigned int key_byte(unsigned long long hi, unsigned int lo, int t)
+{
+    return t < 8 ? (unsigned int)(hi >> (56 - 8 * t)) & 0xFFu
+                 : (lo >> (24 - 8 * (t - 8))) & 0xFFu;
+}
+
+// does the key agree with the prefix on bytes 0..t-1?
+__device__ __forceinline__ bool prefix_match(unsigned long long hi, unsigned int lo,
+                                             const SelState *st, int t)
+{
+    if (t == 0) return true;
+    if (t <= 8) {
+        const int sh = 64 - 8 * t;
+        return (hi >> sh) == (st->pre_hi >> sh);
     }
-    if (valid && rank < L) {
-        ij[2 * rank] = mi;
-        ij[2 * rank + 1] = mj;
+    if (hi != st->pre_hi) return false;
+    const int sh = 32 - 8 * (t - 8);
+    return (lo >> sh) == (st->pre_lo >> sh);
+}
+
+__global__ void k_sel_init(SelState *st, const double *score, int N, int L, int min_sep)
+{
+    // one block: count eligible pairs
+    __shared__ unsigned int cnt;
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    unsigned int c = 0;
+    for (long long idx = threadIdx.x; idx < (long long)N * N; idx += blockDim.x)
+        if (eligible(idx, N, min_sep)) c++;
+    atomicAdd(&cnt, c);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        st->eligible = cnt;
+        st->k = (unsigned int)min((unsigned int)L, cnt);
+        st->pre_hi = 0;
+        st->pre_lo = 0;
+        st->count = 0;
+    }
+    for (int b = threadIdx.x; b < 256; b += blockDim.x) st->hist[b] = 0;
+}
+
+__global__ void k_sel_hist(SelState *st, const double *__restrict__ score, int N, int min_sep,
+                           int t)
+{
+    __shared__ unsigned int h[256];
+    for (int b = threadIdx.x; b < 256; b += blockDim.x) h[b] = 0;
+    __syncthreads();
+    const long long total = (long long)N * N;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        if (!eligible(idx, N, min_sep)) continue;
+        const unsigned long long hi = score_key(score[idx]);
+        const unsigned int lo = 0xFFFFFFFFu - (unsigned int)idx;
+        if (prefix_match(hi, lo, st, t)) atomicAdd(&h[key_byte(hi, lo, t)], 1u);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < 256; b += blockDim.x)
+        if (h[b]) atomicAdd(&st->hist[b], h[b]);
+}
+
+__global__ void k_sel_pick(SelState *st, int t)
+{
+    if (threadIdx.x != 0) return;
+    if (st->k == 0) return;  // nothing to select
+    unsigned int k = st->k, acc = 0;
+    int digit = 0;
+    for (int b = 255; b >= 0; --b) {
+        const unsigned int c = st->hist[b];
+        if (acc + c >= k) {
+            digit = b;
+            break;
+        }
+        acc += c;
+    }
+    st->k = k - acc;
+    if (t < 8) st->pre_hi |= (unsigned long long)digit << (56 - 8 * t);
+    else st->pre_lo |= (unsigned int)digit << (24 - 8 * (t - 8));
+    for (int b = 0; b < 256; ++b) st->hist[b] = 0;
+}
+
+struct Cand {
+    unsigned long long hi;
+    unsigned int lo;
+    unsigned int pad;
+};
+
+__device__ __forceinline__ bool cand_before(const Cand &a, const Cand &b)
+{
+    return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo);
+}
+
+__global__ void k_sel_gather(SelState *st, const double *__restrict__ score, int N, int min_sep,
+                             Cand *cand, int L)
+{
+    if (st->k == 0 && st->eligible == 0) return;
+    const long long total = (long long)N * N;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        if (!eligible(idx, N, min_sep)) continue;
+        const unsigned long long hi = score_key(score[idx]);
+        const unsigned int lo = 0xFFFFFFFFu - (unsigned int)idx;
+        const bool ge = hi > st->pre_hi || (hi == st->pre_hi && lo >= st->pre_lo);
+        if (st->eligible <= (unsigned int)L || ge) {
+            const unsigned int pos = atomicAdd(&st->count, 1u);
+            if (pos < (unsigned int)L) cand[pos] = Cand{hi, lo, 0};
+        }
     }
 }
 
-__global__ void k_fill_i32(int32_t *p, size_t n, int32_t v)
+// one CTA: bitonic sort of the gathered candidates (power-of-two padded)
+__global__ void k_sel_sort(const SelState *st, Cand *cand, int n2, int L, int N, int32_t *ij)
 {
-    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx < n) p[idx] = v;
+    extern __shared__ Cand sh[];
+    const unsigned int n = min(st->count, (unsigned int)L);
+    for (int t = threadIdx.x; t < n2; t += blockDim.x)
+        sh[t] = (t < (int)n) ? cand[t] : Cand{0ull, 0u, 0u};
+    __syncthreads();
+    for (int size = 2; size <= n2; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = threadIdx.x; t < n2; t += blockDim.x) {
+                const int partner = t ^ stride;
+                if (partner > t) {
+                    const bool desc = (t & size) == 0;
+                    const bool swap = desc ? cand_before(sh[partner], sh[t])
+                                           : cand_before(sh[t], sh[partner]);
+                    if (swap) {
+                        const Cand tmp = sh[t];
+                        sh[t] = sh[partner];
+                        sh[partner] = tmp;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int t = threadIdx.x; t < L; t += blockDim.x) {
+        if (t < (int)n) {
+            const unsigned int idx = 0xFFFFFFFFu - sh[t].lo;
+            ij[2 * t] = (int32_t)(idx / N);
+            ij[2 * t + 1] = (int32_t)(idx % N);
+        } else {
+            ij[2 * t] = -1;
+            ij[2 * t + 1] = -1;
+        }
+    }
 }
 
 }  // namespace
@@ -176,15 +305,39 @@ cudaError_t launch_apc(const double *fn, int N, double *cfn, double *work,
     return cudaGetLastError();
 }
 
-cudaError_t launch_topL(const double *score, int N, int L, int min_sep,
-                        int32_t *ij, cudaStream_t st)
+constexpr int TOPL_MAX = 8192;  // largest L sorted in one CTA
+
+size_t topL_scratch_bytes(int L)
+{
+    return sizeof(SelState) + 256 + (size_t)(L > 0 ? L : 1) * sizeof(Cand);
+}
+
+cudaError_t launch_topL(const double *score, int N, int L, int min_sep, int32_t *ij,
+                        void *scratch, cudaStream_t st)
 {
     if (L <= 0) return cudaSuccess;
-    size_t n = 2 * (size_t)L;
-    k_fill_i32<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ij, n, -1);
-    size_t total = (size_t)N * N;
-    k_topL<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(score, N, L, min_sep, ij);
-    count_launches(2);
+    if (L > TOPL_MAX || (long long)N * N >= 0xFFFFFFFFll) return cudaErrorInvalidValue;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_sel_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             TOPL_MAX * (int)sizeof(Cand));
+        if (e) return e;
+        attr = true;
+    }
+    SelState *ss = (SelState *)scratch;
+    Cand *cand = (Cand *)((char *)scratch + ((sizeof(SelState) + 255) / 256) * 256);
+    k_sel_init<<<1, 256, 0, st>>>(ss, score, N, L, min_sep);
+    const long long total = (long long)N * N;
+    const int grid = (int)min((total + 255) / 256, 4LL * 152);
+    for (int t = 0; t < 12; ++t) {
+        k_sel_hist<<<grid, 256, 0, st>>>(ss, score, N, min_sep, t);
+        k_sel_pick<<<1, 32, 0, st>>>(ss, t);
+    }
+    k_sel_gather<<<grid, 256, 0, st>>>(ss, score, N, min_sep, cand, L);
+    int n2 = 1;
+    while (n2 < L) n2 <<= 1;
+    k_sel_sort<<<1, 1024, (size_t)n2 * sizeof(Cand), st>>>(ss, cand, n2, L, N, ij);
+    count_launches(1 + 2 * 12 + 2);
     return cudaGetLastError();
 }
 

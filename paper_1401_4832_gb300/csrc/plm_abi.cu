@@ -687,6 +687,7 @@ plm_status fn_apc_scores(plm_ctx *ctx, const float *J, int N, int q,
     if (N < 2) return fail(ctx, PLM_EINVAL, "N must be >= 2");
     if (!J) return fail(ctx, PLM_EINVAL, "J is NULL");
     if (L < 0 || min_sep < 1) return fail(ctx, PLM_EINVAL, "need L >= 0 and min_sep >= 1");
+    if (L > 8192) return fail(ctx, PLM_EINVAL, "L must be <= 8192 (got %d)", L);
     if (combine < 0 || combine > 2) return fail(ctx, PLM_EINVAL, "combine must be 0, 1 or 2");
     CK(cudaSetDevice(ctx->device));
     cudaStream_t st = ctx->stream;
@@ -705,8 +706,11 @@ plm_status fn_apc_scores(plm_ctx *ctx, const float *J, int N, int q,
         ProfScope ps(ctx, "fn_apc_topL");
         CK(launch_fn((const float *)J_d, N, combine, (double *)fn, st));
         CK(launch_apc((const double *)fn, N, (double *)cfn, (double *)work, st));
-        if (top_s.dev)
-            CK(launch_topL((const double *)cfn, N, L, min_sep, (int32_t *)top_s.dev, st));
+        if (top_s.dev) {
+            void *tsc;
+            CK(ws(ctx, "topL_scratch", topL_scratch_bytes(L), &tsc));
+            CK(launch_topL((const double *)cfn, N, L, min_sep, (int32_t *)top_s.dev, tsc, st));
+        }
     }
     CK(copy_back(ctx, fn_s));
     CK(copy_back(ctx, cfn_s));

@@ -172,8 +172,11 @@ cudaError_t launch_fn(const float *J, int N, int combine, double *fn,
                       cudaStream_t st);
 cudaError_t launch_apc(const double *fn, int N, double *cfn, double *work,
                        cudaStream_t st);
+// top-L pairs (j - i >= min_sep) by score descending, ties (i, j) ascending;
+// L <= 8192; rows beyond the number of eligible pairs are -1
+size_t topL_scratch_bytes(int L);
 cudaError_t launch_topL(const double *score, int N, int L, int min_sep,
-                        int32_t *ij, cudaStream_t st);
+                        int32_t *ij, void *scratch, cudaStream_t st);
 
 // ---- tcgen05 split-BF16 path (k_tc.cu) ----
 // split theta (fp32) into bf16 hi + lo: hi = RN(x), lo = RN(x - hi)
