@@ -151,6 +151,24 @@ plm_status plm_solve(plm_ctx *ctx, const int8_t *msa, int B, int N, int q,
                      const plm_opts *opts, float *h_out, float *J_out,
                      plm_report *report);
 
+/* One protein family of a batched solve. */
+typedef struct {
+    const int8_t *msa;  /* [B][N] int8, states 0..q-1 (device or host) */
+    int B, N;
+    float *h_out;       /* [N][q] out */
+    float *J_out;       /* [N][q][N][q] out, asymmetric estimates */
+} plm_family;
+
+/* plm_solve for many independent families of uneven N and B at once (the
+ * paper solves families one at a time; this batches them).  Every site of
+ * every family is one problem of the same batched L-BFGS; each evaluation
+ * covers all families in one launch per kernel (up to 64 families per
+ * launch).  The sites' trajectories are the same as in separate plm_solve
+ * calls.  reports: [nfam] (host, may be NULL).  Returns PLM_ENOTCONV if any
+ * site of any family stopped before gtol (outputs valid). */
+plm_status plm_solve_batch(plm_ctx *ctx, const plm_family *fams, int nfam,
+                           int q, const plm_opts *opts, plm_report *reports);
+
 /* Steps 4-6 of the rundown: Ising gauge of every estimate (Eq.
  * gauge_change2), combination of J^i_ij with J^j_ij = (J^j_ji)^T (Eq.
  * average2; combine = 1 / 2 selects the elementwise min / max alternatives

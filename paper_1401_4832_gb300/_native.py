@@ -47,6 +47,11 @@ class plm_report(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class plm_family(ctypes.Structure):
+    _fields_ = [("msa", ctypes.c_void_p), ("B", ctypes.c_int), ("N", ctypes.c_int),
+                ("h_out", ctypes.c_void_p), ("J_out", ctypes.c_void_p)]
+
+
 class PlmError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -91,6 +96,9 @@ def load():
         lib.plm_solve.argtypes = [P, P, I, I, I, ctypes.POINTER(plm_opts), P, P,
                                   ctypes.POINTER(plm_report)]
         lib.plm_solve.restype = I
+        lib.plm_solve_batch.argtypes = [P, ctypes.POINTER(plm_family), I, I,
+                                        ctypes.POINTER(plm_opts), ctypes.POINTER(plm_report)]
+        lib.plm_solve_batch.restype = I
         lib.fn_apc_scores.argtypes = [P, P, I, I, I, P, P, P, I, I]
         lib.fn_apc_scores.restype = I
         lib.plm_kernel_launches.argtypes = []

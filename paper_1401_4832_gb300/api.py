@@ -162,6 +162,37 @@ def plm_solve(ctx: Context, msa, raise_on_notconv: bool = False, **opts):
     return h, J, d
 
 
+def plm_solve_batch(ctx: Context, msas, raise_on_notconv: bool = False, **opts):
+    """plm_solve for many families at once (one batched L-BFGS, one launch
+    per evaluation kernel for all families).  Returns a list of
+    (h, J, report) per family."""
+    msas = [_as_input(m, np.int8) for m in msas]
+    o = default_opts(**opts)
+    n = len(msas)
+    fams = (N_.plm_family * n)()
+    outs = []
+    for k, m in enumerate(msas):
+        B, N = m.shape
+        h = _like(m, (N, Q), np.float32)
+        J = _like(m, (N, Q, N, Q), np.float32)
+        fams[k].msa = _ptr(m)
+        fams[k].B = B
+        fams[k].N = N
+        fams[k].h_out = _ptr(h)
+        fams[k].J_out = _ptr(J)
+        outs.append((h, J))
+    reps = (N_.plm_report * n)()
+    st = ctx.lib.plm_solve_batch(ctx.handle, fams, n, Q, ctypes.byref(o), reps)
+    if st != N_.PLM_OK and (st != N_.PLM_ENOTCONV or raise_on_notconv):
+        ctx.check(st)
+    res = []
+    for k in range(n):
+        d = reps[k].as_dict()
+        d["status"] = N_.STATUS_NAMES.get(st, st)
+        res.append((outs[k][0], outs[k][1], d))
+    return res
+
+
 def fn_apc_scores(ctx: Context, J, combine: str = "mean", L: int | None = None,
                   min_sep: int = 5):
     """Steps 4-6 of the rundown: returns (FN[N,N], CFN[N,N], top[L,2])."""

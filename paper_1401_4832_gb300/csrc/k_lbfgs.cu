@@ -38,7 +38,6 @@ namespace plm {
 namespace {
 
 constexpr int LB_THREADS = 256;
-constexpr int LB_CHUNK4 = 2048;  // float4 elements per chunk
 
 // sum K per-thread values over the block (fixed order) and write them
 template <int K>
@@ -60,52 +59,53 @@ __device__ __forceinline__ void block_write(double (&v)[K], double *out)
 }
 
 // fixed-order sum over the chunks of one site (one warp): returns the
-// total of slot k of the partial records
-__device__ __forceinline__ double chunk_sum(const double *part, int nch, int k)
+// total of slot k of the site's partial records
+__device__ __forceinline__ double chunk_sum(const double *part, const SiteInfo &si, int k)
 {
     const int lane = threadIdx.x & 31;
     double t = 0.0;
-    for (int c = lane; c < nch; c += 32) t += part[(size_t)c * LB_PART + k];
+    for (int c = lane; c < si.nchunks; c += 32) t += part[(size_t)(si.chunk0 + c) * LB_PART + k];
     return warp_sum_d(t);
 }
 
 struct Chunk {
-    size_t base4, e0, e1, vec4;
+    size_t base4, e0, e1;
+    int site;
 };
 
-__device__ __forceinline__ Chunk chunk_of(const Dims &d)
+__device__ __forceinline__ Chunk chunk_of(const SiteInfo *si, const ChunkInfo *ci)
 {
+    const ChunkInfo c = ci[blockIdx.x];
     Chunk ch;
-    const size_t seg4 = d.site_elems() / 4;
-    ch.base4 = (size_t)blockIdx.y * seg4;
-    ch.e0 = (size_t)blockIdx.x * LB_CHUNK4;
-    ch.e1 = min(ch.e0 + LB_CHUNK4, seg4);
-    ch.vec4 = d.theta_elems() / 4;
+    ch.site = c.site;
+    ch.base4 = (size_t)si[c.site].off4;
+    ch.e0 = (size_t)c.e0;
+    ch.e1 = (size_t)c.e1;
     return ch;
 }
 
-__device__ __forceinline__ double *part_rec(double *part, int nch)
+__device__ __forceinline__ double *part_rec(double *part)
 {
-    return part + ((size_t)blockIdx.y * nch + blockIdx.x) * LB_PART;
+    return part + (size_t)blockIdx.x * LB_PART;
 }
 
 // ------------------------------------------------------------ start
 __global__ void __launch_bounds__(LB_THREADS)
-k_init_dots(const float *__restrict__ g, Dims d, double *part, int nch)
+k_init_dots(const float *__restrict__ g, const SiteInfo *si, const ChunkInfo *ci, double *part)
 {
-    const Chunk ch = chunk_of(d);
+    const Chunk ch = chunk_of(si, ci);
     const float4 *g4 = (const float4 *)g + ch.base4;
     DF acc;
     for (size_t e = ch.e0 + threadIdx.x; e < ch.e1; e += LB_THREADS) df_dot4(acc, g4[e], g4[e]);
     double v[1] = {df_value(acc)};
-    block_write<1>(v, part_rec(part, nch));
+    block_write<1>(v, part_rec(part));
 }
 
 __global__ void k_init_finish(SiteState *ss, const double *__restrict__ f, const double *part,
-                              int nch, SolveParams p)
+                              const SiteInfo *si, SolveParams p)
 {
     const int r = blockIdx.x;
-    const double gg = chunk_sum(part + (size_t)r * nch * LB_PART, nch, 0);
+    const double gg = chunk_sum(part, si[r], 0);
     if (threadIdx.x != 0) return;
     SiteState &s = ss[r];
     s.f = f[r];
@@ -138,13 +138,14 @@ __device__ __forceinline__ bool slot_valid(int j, int head, int hist, int M)
 template <int M>
 __global__ void __launch_bounds__(LB_THREADS)
 k_dir_dots(const SiteState *ss, const float *__restrict__ g, const float *__restrict__ S,
-           const float *__restrict__ Y, Dims d, double *part, int nch)
+           const float *__restrict__ Y, const SiteInfo *si, const ChunkInfo *ci, long long vec4,
+           double *part)
 {
-    const SiteState &s = ss[blockIdx.y];
+    const Chunk ch = chunk_of(si, ci);
+    const SiteState &s = ss[ch.site];
     if (s.status != SITE_READY || s.hist == 0) return;
     const int hist = s.hist, head = s.head;
     const int newest = (head - 1 + M) % M;
-    const Chunk ch = chunk_of(d);
     const float4 *g4 = (const float4 *)g + ch.base4;
     const float4 *S4 = (const float4 *)S + ch.base4;
     const float4 *Y4 = (const float4 *)Y + ch.base4;
@@ -154,12 +155,12 @@ k_dir_dots(const SiteState *ss, const float *__restrict__ g, const float *__rest
     DF acc[4 * M];
     for (size_t e = ch.e0 + threadIdx.x; e < ch.e1; e += LB_THREADS) {
         const float4 gv = g4[e];
-        const float4 yn = Y4[(size_t)newest * ch.vec4 + e];
+        const float4 yn = Y4[(size_t)newest * vec4 + e];
 #pragma unroll
         for (int j = 0; j < M; ++j) {
             if (!valid[j]) continue;
-            const float4 sv = S4[(size_t)j * ch.vec4 + e];
-            const float4 yv = Y4[(size_t)j * ch.vec4 + e];
+            const float4 sv = S4[(size_t)j * vec4 + e];
+            const float4 yv = Y4[(size_t)j * vec4 + e];
             df_dot4(acc[j], sv, gv);
             df_dot4(acc[M + j], yv, gv);
             df_dot4(acc[2 * M + j], sv, yn);
@@ -169,12 +170,12 @@ k_dir_dots(const SiteState *ss, const float *__restrict__ g, const float *__rest
     double v[4 * M];
 #pragma unroll
     for (int k = 0; k < 4 * M; ++k) v[k] = df_value(acc[k]);
-    block_write<4 * M>(v, part_rec(part, nch));
+    block_write<4 * M>(v, part_rec(part));
 }
 
 // the small FP64 algebra of the compact form, one warp per site
 template <int M>
-__global__ void k_dir_solve(SiteState *ss, const double *part, int nch)
+__global__ void k_dir_solve(SiteState *ss, const double *part, const SiteInfo *si)
 {
     const int r = blockIdx.x;
     SiteState &s = ss[r];
@@ -182,7 +183,7 @@ __global__ void k_dir_solve(SiteState *ss, const double *part, int nch)
     __shared__ double tot[4 * M];
     if (s.hist > 0) {
         for (int k = 0; k < 4 * M; ++k) {
-            double t = chunk_sum(part + (size_t)r * nch * LB_PART, nch, k);
+            double t = chunk_sum(part, si[r], k);
             if (threadIdx.x == 0) tot[k] = t;
         }
     }
@@ -243,12 +244,13 @@ __global__ void k_dir_solve(SiteState *ss, const double *part, int nch)
 template <int M>
 __global__ void __launch_bounds__(LB_THREADS)
 k_dir_apply(const SiteState *ss, const float *__restrict__ g, const float *__restrict__ S,
-            const float *__restrict__ Y, float *__restrict__ dir, Dims d, double *part, int nch)
+            const float *__restrict__ Y, float *__restrict__ dir, const SiteInfo *si,
+            const ChunkInfo *ci, long long vec4, double *part)
 {
-    const SiteState &s = ss[blockIdx.y];
+    const Chunk ch = chunk_of(si, ci);
+    const SiteState &s = ss[ch.site];
     if (s.status != SITE_READY) return;
     const int hist = s.hist, head = s.head;
-    const Chunk ch = chunk_of(d);
     const float4 *g4 = (const float4 *)g + ch.base4;
     const float4 *S4 = (const float4 *)S + ch.base4;
     const float4 *Y4 = (const float4 *)Y + ch.base4;
@@ -269,8 +271,8 @@ k_dir_apply(const SiteState *ss, const float *__restrict__ g, const float *__res
 #pragma unroll
         for (int j = 0; j < M; ++j) {
             if (!valid[j]) continue;
-            const float4 sv = S4[(size_t)j * ch.vec4 + e];
-            const float4 yv = Y4[(size_t)j * ch.vec4 + e];
+            const float4 sv = S4[(size_t)j * vec4 + e];
+            const float4 yv = Y4[(size_t)j * vec4 + e];
             a.x += cs[j] * sv.x + cy[j] * yv.x;
             a.y += cs[j] * sv.y + cy[j] * yv.y;
             a.z += cs[j] * sv.z + cy[j] * yv.z;
@@ -281,17 +283,17 @@ k_dir_apply(const SiteState *ss, const float *__restrict__ g, const float *__res
         df_dot4(acc, gv, dv);
     }
     double v[1] = {df_value(acc)};
-    block_write<1>(v, part_rec(part, nch));
+    block_write<1>(v, part_rec(part));
 }
 
 // line-search set-up; a direction that is not a descent direction (rounding
 // in FP32) is replaced by -g and the history is dropped
-__global__ void k_dir_finish(SiteState *ss, const double *part, int nch)
+__global__ void k_dir_finish(SiteState *ss, const double *part, const SiteInfo *si)
 {
     const int r = blockIdx.x;
     SiteState &s = ss[r];
     if (s.status != SITE_READY) return;
-    double dg0 = chunk_sum(part + (size_t)r * nch * LB_PART, nch, 0);
+    double dg0 = chunk_sum(part, si[r], 0);
     if (threadIdx.x != 0) return;
     s.neg_g = 0;
     if (!(dg0 < 0.0)) {
@@ -322,14 +324,14 @@ __global__ void k_dir_finish(SiteState *ss, const double *part, int nch)
 __global__ void __launch_bounds__(LB_THREADS)
 k_trial(const SiteState *ss, const float *__restrict__ theta, const float *__restrict__ g,
         float *__restrict__ dir, float *__restrict__ theta_t, __nv_bfloat16 *__restrict__ hi,
-        __nv_bfloat16 *__restrict__ lo, Dims d, double *part, int nch)
+        __nv_bfloat16 *__restrict__ lo, const SiteInfo *si, const ChunkInfo *ci, double *part)
 {
-    const SiteState &s = ss[blockIdx.y];
+    const Chunk ch = chunk_of(si, ci);
+    const SiteState &s = ss[ch.site];
     if (s.status != SITE_SEARCHING) return;
-    const Chunk ch = chunk_of(d);
     const float a = (float)s.alpha;
     const bool neg = s.neg_g != 0;
-    const int NQ = d.N * Q;
+    const int NQ = si[ch.site].NQ, KP = si[ch.site].KP;
     const float4 *t4 = (const float4 *)theta + ch.base4;
     const float4 *g4 = (const float4 *)g + ch.base4;
     float4 *d4 = (float4 *)dir + ch.base4;
@@ -349,7 +351,7 @@ k_trial(const SiteState *ss, const float *__restrict__ theta, const float *__res
                                      fmaf(a, dv.w, t.w));
         o4[e] = x;
         const float xv[4] = {x.x, x.y, x.z, x.w};
-        const int c0 = (int)((4 * e) % d.KP);
+        const int c0 = (int)((4 * e) % KP);
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             if (c0 + u == NQ) df_fma(ph, xv[u], xv[u]);
@@ -366,17 +368,17 @@ k_trial(const SiteState *ss, const float *__restrict__ theta, const float *__res
         }
     }
     double v[2] = {df_value(pj), df_value(ph)};
-    block_write<2>(v, part_rec(part, nch));
+    block_write<2>(v, part_rec(part));
 }
 
 // partial g_t . d and ||g_t||^2 (slots 2 and 3; slots 0, 1 hold the penalty)
 __global__ void __launch_bounds__(LB_THREADS)
 k_ls_dots(const SiteState *ss, const float *__restrict__ g_t, const float *__restrict__ dir,
-          Dims d, double *part, int nch)
+          const SiteInfo *si, const ChunkInfo *ci, double *part)
 {
-    const SiteState &s = ss[blockIdx.y];
+    const Chunk ch = chunk_of(si, ci);
+    const SiteState &s = ss[ch.site];
     if (s.status != SITE_SEARCHING) return;
-    const Chunk ch = chunk_of(d);
     const float4 *gt4 = (const float4 *)g_t + ch.base4;
     const float4 *d4 = (const float4 *)dir + ch.base4;
     DF dgt, gn2;
@@ -386,7 +388,7 @@ k_ls_dots(const SiteState *ss, const float *__restrict__ g_t, const float *__res
         df_dot4(gn2, gv, gv);
     }
     double v[2] = {df_value(dgt), df_value(gn2)};
-    block_write<2>(v, part_rec(part, nch) + 2);
+    block_write<2>(v, part_rec(part) + 2);
 }
 
 __device__ double safe_interp(double lo, double flo, double dlo, double hi, double fhi,
@@ -419,16 +421,15 @@ __device__ double safe_interp(double lo, double flo, double dlo, double hi, doub
 enum { LS_CONTINUE = 0, LS_ACCEPT = 1, LS_FAIL = 2 };
 
 __global__ void k_ls_decide(SiteState *ss, const double *__restrict__ f_data, const double *part,
-                            int nch, SolveParams p, int round, int *counters)
+                            const SiteInfo *si, SolveParams p, int round, int *counters)
 {
     const int r = blockIdx.x;
     SiteState &s = ss[r];
     if (s.status != SITE_SEARCHING) return;
-    const double *pr = part + (size_t)r * nch * LB_PART;
-    const double pj = chunk_sum(pr, nch, 0);
-    const double ph = chunk_sum(pr, nch, 1);
-    const double dgt = chunk_sum(pr, nch, 2);
-    const double gn2 = chunk_sum(pr, nch, 3);
+    const double pj = chunk_sum(part, si[r], 0);
+    const double ph = chunk_sum(part, si[r], 1);
+    const double dgt = chunk_sum(part, si[r], 2);
+    const double gn2 = chunk_sum(part, si[r], 3);
     if (threadIdx.x != 0) return;
     s.pen_t = p.lambda_h * ph + p.lambda_Jp * pj;
     const double ft = f_data[r] + s.pen_t;
@@ -497,18 +498,19 @@ __global__ void k_ls_decide(SiteState *ss, const double *__restrict__ f_data, co
 __global__ void __launch_bounds__(LB_THREADS)
 k_commit(const SiteState *ss, float *__restrict__ theta, float *__restrict__ g,
          const float *__restrict__ theta_t, const float *__restrict__ g_t,
-         float *__restrict__ S, float *__restrict__ Y, Dims d, int round)
+         float *__restrict__ S, float *__restrict__ Y, const SiteInfo *si, const ChunkInfo *ci,
+         long long vec4, int round)
 {
-    const SiteState &s = ss[blockIdx.y];
+    const Chunk ch = chunk_of(si, ci);
+    const SiteState &s = ss[ch.site];
     if (s.commit_round != round) return;
-    const Chunk ch = chunk_of(d);
     const size_t slot = (size_t)s.commit_slot;
     float4 *th4 = (float4 *)theta + ch.base4;
     float4 *g4 = (float4 *)g + ch.base4;
     const float4 *tt4 = (const float4 *)theta_t + ch.base4;
     const float4 *gt4 = (const float4 *)g_t + ch.base4;
-    float4 *s4 = (float4 *)S + slot * ch.vec4 + ch.base4;
-    float4 *y4 = (float4 *)Y + slot * ch.vec4 + ch.base4;
+    float4 *s4 = (float4 *)S + slot * vec4 + ch.base4;
+    float4 *y4 = (float4 *)Y + slot * vec4 + ch.base4;
     for (size_t e = ch.e0 + threadIdx.x; e < ch.e1; e += LB_THREADS) {
         const float4 tn = tt4[e], to = th4[e], gn = gt4[e], go = g4[e];
         s4[e] = make_float4(tn.x - to.x, tn.y - to.y, tn.z - to.z, tn.w - to.w);
@@ -518,80 +520,68 @@ k_commit(const SiteState *ss, float *__restrict__ theta, float *__restrict__ g,
     }
 }
 
-dim3 vec_grid(const Dims &d, int nch) { return dim3(nch, d.N); }
-
 }  // namespace
 
-int lbfgs_chunks(const Dims &d)
-{
-    const size_t seg4 = d.site_elems() / 4;
-    return (int)((seg4 + LB_CHUNK4 - 1) / LB_CHUNK4);
-}
-
-cudaError_t launch_lbfgs_init(SiteState *ss, const double *f, const float *g, const Dims &d,
+cudaError_t launch_lbfgs_init(SiteState *ss, const double *f, const float *g, const LbLayout &L,
                               const SolveParams &p, double *part, cudaStream_t st)
 {
-    const int nch = lbfgs_chunks(d);
-    k_init_dots<<<vec_grid(d, nch), LB_THREADS, 0, st>>>(g, d, part, nch);
-    k_init_finish<<<d.N, 32, 0, st>>>(ss, f, part, nch, p);
+    k_init_dots<<<L.nchunks, LB_THREADS, 0, st>>>(g, L.si, L.ci, part);
+    k_init_finish<<<L.nsites, 32, 0, st>>>(ss, f, part, L.si, p);
     count_launches(2);
     return cudaGetLastError();
 }
 
 template <int M>
 static void direction_m(SiteState *ss, const float *g, float *dir, const float *S,
-                        const float *Y, const Dims &d, double *part, int nch, cudaStream_t st)
+                        const float *Y, const LbLayout &L, double *part, cudaStream_t st)
 {
-    k_dir_dots<M><<<vec_grid(d, nch), LB_THREADS, 0, st>>>(ss, g, S, Y, d, part, nch);
-    k_dir_solve<M><<<d.N, 32, 0, st>>>(ss, part, nch);
-    k_dir_apply<M><<<vec_grid(d, nch), LB_THREADS, 0, st>>>(ss, g, S, Y, dir, d, part, nch);
+    k_dir_dots<M><<<L.nchunks, LB_THREADS, 0, st>>>(ss, g, S, Y, L.si, L.ci, L.vec4, part);
+    k_dir_solve<M><<<L.nsites, 32, 0, st>>>(ss, part, L.si);
+    k_dir_apply<M><<<L.nchunks, LB_THREADS, 0, st>>>(ss, g, S, Y, dir, L.si, L.ci, L.vec4, part);
 }
 
 cudaError_t launch_lbfgs_direction(SiteState *ss, const float *g, float *dir,
-                                   const float *S_hist, const float *Y_hist, const Dims &d,
+                                   const float *S_hist, const float *Y_hist, const LbLayout &L,
                                    const SolveParams &p, double *part, cudaStream_t st)
 {
-    const int nch = lbfgs_chunks(d);
     switch (p.m) {
-    case 1: direction_m<1>(ss, g, dir, S_hist, Y_hist, d, part, nch, st); break;
-    case 2: direction_m<2>(ss, g, dir, S_hist, Y_hist, d, part, nch, st); break;
-    case 3: direction_m<3>(ss, g, dir, S_hist, Y_hist, d, part, nch, st); break;
-    case 4: direction_m<4>(ss, g, dir, S_hist, Y_hist, d, part, nch, st); break;
-    case 5: direction_m<5>(ss, g, dir, S_hist, Y_hist, d, part, nch, st); break;
-    case 6: direction_m<6>(ss, g, dir, S_hist, Y_hist, d, part, nch, st); break;
-    case 7: direction_m<7>(ss, g, dir, S_hist, Y_hist, d, part, nch, st); break;
-    case 8: direction_m<8>(ss, g, dir, S_hist, Y_hist, d, part, nch, st); break;
+    case 1: direction_m<1>(ss, g, dir, S_hist, Y_hist, L, part, st); break;
+    case 2: direction_m<2>(ss, g, dir, S_hist, Y_hist, L, part, st); break;
+    case 3: direction_m<3>(ss, g, dir, S_hist, Y_hist, L, part, st); break;
+    case 4: direction_m<4>(ss, g, dir, S_hist, Y_hist, L, part, st); break;
+    case 5: direction_m<5>(ss, g, dir, S_hist, Y_hist, L, part, st); break;
+    case 6: direction_m<6>(ss, g, dir, S_hist, Y_hist, L, part, st); break;
+    case 7: direction_m<7>(ss, g, dir, S_hist, Y_hist, L, part, st); break;
+    case 8: direction_m<8>(ss, g, dir, S_hist, Y_hist, L, part, st); break;
     default: return cudaErrorInvalidValue;
     }
-    k_dir_finish<<<d.N, 32, 0, st>>>(ss, part, nch);
+    k_dir_finish<<<L.nsites, 32, 0, st>>>(ss, part, L.si);
     count_launches(4);
     return cudaGetLastError();
 }
 
 cudaError_t launch_lbfgs_trial(SiteState *ss, const float *theta, const float *g, float *dir,
                                float *theta_t, __nv_bfloat16 *hi, __nv_bfloat16 *lo,
-                               const Dims &d, const SolveParams &p, double *part,
+                               const LbLayout &L, const SolveParams &p, double *part,
                                cudaStream_t st)
 {
     (void)p;
-    const int nch = lbfgs_chunks(d);
-    k_trial<<<vec_grid(d, nch), LB_THREADS, 0, st>>>(ss, theta, g, dir, theta_t, hi, lo, d, part,
-                                                      nch);
+    k_trial<<<L.nchunks, LB_THREADS, 0, st>>>(ss, theta, g, dir, theta_t, hi, lo, L.si, L.ci,
+                                               part);
     count_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_lbfgs_linesearch(SiteState *ss, const double *f_data, float *theta, float *g,
                                     const float *theta_t, const float *g_t, const float *dir,
-                                    float *S_hist, float *Y_hist, const Dims &d,
+                                    float *S_hist, float *Y_hist, const LbLayout &L,
                                     const SolveParams &p, double *part, int round,
                                     int *counters, cudaStream_t st)
 {
-    const int nch = lbfgs_chunks(d);
-    k_ls_dots<<<vec_grid(d, nch), LB_THREADS, 0, st>>>(ss, g_t, dir, d, part, nch);
-    k_ls_decide<<<d.N, 32, 0, st>>>(ss, f_data, part, nch, p, round, counters);
-    k_commit<<<vec_grid(d, nch), LB_THREADS, 0, st>>>(ss, theta, g, theta_t, g_t, S_hist, Y_hist,
-                                                       d, round);
+    k_ls_dots<<<L.nchunks, LB_THREADS, 0, st>>>(ss, g_t, dir, L.si, L.ci, part);
+    k_ls_decide<<<L.nsites, 32, 0, st>>>(ss, f_data, part, L.si, p, round, counters);
+    k_commit<<<L.nchunks, LB_THREADS, 0, st>>>(ss, theta, g, theta_t, g_t, S_hist, Y_hist, L.si,
+                                                L.ci, L.vec4, round);
     count_launches(3);
     return cudaGetLastError();
 }

@@ -245,13 +245,50 @@ __device__ __forceinline__ uint32_t swz(int row, int chunk16)
     return (uint32_t)(row * 128 + ((chunk16 ^ (row & 7)) << 4));
 }
 
+// Kernel parameters of one batched launch: the family descriptors and one
+// TMA map per family and operand (passed by value, read from param space).
+struct LogitsParams {
+    TcBatch b;
+    CUtensorMap hi[MAX_FAM], lo[MAX_FAM];
+};
+
+struct GradParams {
+    TcBatch b;
+    CUtensorMap dhi[MAX_FAM], dlo[MAX_FAM];
+};
+
+// family owning global tile `tile` (tile0 ascending)
+__device__ __forceinline__ int family_of(const TcBatch &b, int tile, bool grad)
+{
+    int f = 0;
+    for (int k = 1; k < b.nfam; ++k)
+        if ((grad ? b.f[k].tile0_grad : b.f[k].tile0_logits) <= tile) f = k;
+    return f;
+}
+
 // ---------------------------------------------------------------- logits
 __global__ void __launch_bounds__(192, 1)
-k_tc_logits(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo,
-            const int8_t *__restrict__ msa, const float *__restrict__ w, double inv_beff, Dims d,
-            int BP, __nv_bfloat16 *__restrict__ dt_hi, __nv_bfloat16 *__restrict__ dt_lo,
-            double *__restrict__ partial, int *__restrict__ err)
+k_tc_logits(const __grid_constant__ LogitsParams P, int *__restrict__ err)
 {
+    const int fi = family_of(P.b, blockIdx.x, false);
+    const FamDesc &F = P.b.f[fi];
+    const CUtensorMap &tm_hi = P.hi[fi];
+    const CUtensorMap &tm_lo = P.lo[fi];
+    const int8_t *__restrict__ msa = F.msa;
+    const float *__restrict__ w = F.w;
+    const double inv_beff = F.inv_beff;
+    const int BP = F.BP;
+    __nv_bfloat16 *__restrict__ dt_hi = F.dt_hi;
+    __nv_bfloat16 *__restrict__ dt_lo = F.dt_lo;
+    double *__restrict__ partial = F.partial;
+    Dims d;
+    d.B = F.B;
+    d.N = F.N;
+    d.KP = F.KP;
+    d.R = F.R;
+    d.K = F.N * Q + 1;
+    const int local = blockIdx.x - F.tile0_logits;
+    const int nbt = BP / TC_M;
     extern __shared__ uint8_t dsmem[];
     uint8_t *smem = align1024(dsmem);
     __shared__ __align__(8) uint64_t full_b[STAGES], full_a[STAGES], empty_[STAGES], acc_full;
@@ -260,7 +297,7 @@ k_tc_logits(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ C
     __shared__ double red[4][LG_SITES];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tb = blockIdx.x, tr = blockIdx.y;
+    const int tb = local % nbt, tr = local / nbt;
     const int b0 = tb * TC_M;
     const int r0 = tr * LG_SITES;
     const int row0 = r0 * QP;
@@ -458,10 +495,24 @@ k_tc_logits(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ C
 
 // ---------------------------------------------------------------- gradient
 __global__ void __launch_bounds__(192, 1)
-k_tc_grad(const __grid_constant__ CUtensorMap tm_dhi, const __grid_constant__ CUtensorMap tm_dlo,
-          const int8_t *__restrict__ msaT, const float *__restrict__ theta, Dims d, int BP,
-          float two_lh, float two_lj, float *__restrict__ G, int *__restrict__ err)
+k_tc_grad(const __grid_constant__ GradParams P, float two_lh, float two_lj, int *__restrict__ err)
 {
+    const int fi = family_of(P.b, blockIdx.x, true);
+    const FamDesc &F = P.b.f[fi];
+    const CUtensorMap &tm_dhi = P.dhi[fi];
+    const CUtensorMap &tm_dlo = P.dlo[fi];
+    const int8_t *__restrict__ msaT = F.msaT;
+    const float *__restrict__ theta = F.theta;
+    float *__restrict__ G = F.G;
+    const int BP = F.BP;
+    Dims d;
+    d.B = F.B;
+    d.N = F.N;
+    d.KP = F.KP;
+    d.R = F.R;
+    d.K = F.N * Q + 1;
+    const int local = blockIdx.x - F.tile0_grad;
+    const int nct = (d.KP + GR_N - 1) / GR_N;
     extern __shared__ uint8_t dsmem[];
     uint8_t *smem = align1024(dsmem);
     __shared__ __align__(8) uint64_t full_b[STAGES], full_a[STAGES], empty_[STAGES], acc_full;
@@ -469,8 +520,8 @@ k_tc_grad(const __grid_constant__ CUtensorMap tm_dhi, const __grid_constant__ CU
     __shared__ int abort_sh;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int c0 = blockIdx.x * GR_N;
-    const int rs0 = blockIdx.y * TC_M;
+    const int c0 = (local % nct) * GR_N;
+    const int rs0 = (local / nct) * TC_M;
     const int NK = BP / TC_BK;
     const int NQ = d.N * Q;
 
@@ -682,16 +733,28 @@ __global__ void k_split(const float *__restrict__ theta, size_t n,
 
 // msaT[i][b] = S[b][i] (b < B), 0x7F beyond B; row N is the constant-feature
 // row (0 for b < B, 0x7F beyond)
-__global__ void k_msa_transpose(const int8_t *__restrict__ msa, Dims d, int BP,
+__global__ void k_msa_transpose(const int8_t *__restrict__ msa, int B, int N, int BP,
                                 int8_t *__restrict__ msaT)
 {
     size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    size_t total = (size_t)(d.N + 1) * BP;
+    size_t total = (size_t)(N + 1) * BP;
     if (idx >= total) return;
     int i = (int)(idx / BP), b = (int)(idx % BP);
     int8_t v = 0x7F;
-    if (b < d.B) v = (i < d.N) ? msa[(size_t)b * d.N + i] : 0;
+    if (b < B) v = (i < N) ? msa[(size_t)b * N + i] : 0;
     msaT[idx] = v;
+}
+
+// f_data[r] = -(sum over sequence tiles of the partials) / B_eff, per family
+__global__ void k_tc_finish(const __grid_constant__ TcBatch b)
+{
+    const FamDesc &F = b.f[blockIdx.x];
+    const int nbt = F.BP / TC_M;
+    for (int r = threadIdx.x; r < F.N; r += blockDim.x) {
+        double t = 0.0;
+        for (int y = 0; y < nbt; ++y) t += F.partial[(size_t)y * F.N + r];
+        F.f_data[r] = -t / F.beff;
+    }
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
@@ -724,28 +787,27 @@ bool make_map(CUtensorMap *m, const void *base, uint64_t inner, uint64_t outer,
            CUDA_SUCCESS;
 }
 
-int padded_B(const Dims &d) { return (d.B + TC_M - 1) / TC_M * TC_M; }
-
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 }  // namespace
 
-cudaError_t launch_split_theta(const float *theta, const Dims &d, __nv_bfloat16 *hi,
+int tc_padded_B(int B) { return (B + TC_M - 1) / TC_M * TC_M; }
+
+cudaError_t launch_split_theta(const float *theta, size_t n, __nv_bfloat16 *hi,
                                __nv_bfloat16 *lo, cudaStream_t st)
 {
-    size_t n = d.theta_elems();
     k_split<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(theta, n, hi, lo);
     count_launches(1);
     return cudaGetLastError();
 }
 
-// scratch: D^T hi | D^T lo | partial | msaT
-size_t tc_scratch_bytes(const Dims &d)
+// one family's scratch: D^T hi | D^T lo | partial | msaT
+size_t tc_family_scratch_bytes(int B, int N)
 {
-    const size_t BP = padded_B(d);
+    const size_t BP = tc_padded_B(B), R = (size_t)N * QP;
     const size_t nbt = BP / TC_M;
-    return 2 * align256((size_t)d.R * BP * 2) + align256(nbt * d.N * sizeof(double)) +
-           align256((size_t)(d.N + 1) * BP);
+    return 2 * align256(R * BP * 2) + align256(nbt * N * sizeof(double)) +
+           align256((size_t)(N + 1) * BP);
 }
 
 int tc_supported()
@@ -757,11 +819,39 @@ int tc_supported()
     return (major == 10 && minor == 3 && encode_fn() != nullptr) ? 1 : 0;
 }
 
-cudaError_t launch_tc_eval(void *prof, const int8_t *msa, const float *w, double beff,
-                           const __nv_bfloat16 *th_hi, const __nv_bfloat16 *th_lo,
-                           const float *theta, const Dims &d, double lambda_h,
-                           double lambda_Jp, void *scratch, double *f_data, float *G, int *err,
-                           cudaStream_t st)
+cudaError_t launch_tc_prepare(TcBatch &b, void *const *scratch, cudaStream_t st)
+{
+    int tl = 0, tg = 0;
+    for (int i = 0; i < b.nfam; ++i) {
+        FamDesc &F = b.f[i];
+        F.BP = tc_padded_B(F.B);
+        F.R = F.N * QP;
+        F.KP = (F.N * Q + 1 + KALIGN - 1) / KALIGN * KALIGN;
+        const size_t nbt = F.BP / TC_M;
+        char *p = (char *)scratch[i];
+        F.dt_hi = (__nv_bfloat16 *)p;
+        p += align256((size_t)F.R * F.BP * 2);
+        F.dt_lo = (__nv_bfloat16 *)p;
+        p += align256((size_t)F.R * F.BP * 2);
+        F.partial = (double *)p;
+        p += align256(nbt * F.N * sizeof(double));
+        int8_t *msaT = (int8_t *)p;
+        F.msaT = msaT;
+        F.tile0_logits = tl;
+        F.tile0_grad = tg;
+        tl += (int)nbt * ((F.N + LG_SITES - 1) / LG_SITES);
+        tg += ((F.KP + GR_N - 1) / GR_N) * ((F.R + TC_M - 1) / TC_M);
+        const size_t nT = (size_t)(F.N + 1) * F.BP;
+        k_msa_transpose<<<(unsigned)((nT + 255) / 256), 256, 0, st>>>(F.msa, F.B, F.N, F.BP, msaT);
+        count_launches(1);
+    }
+    b.ntiles_logits = tl;
+    b.ntiles_grad = tg;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_eval(void *prof, const TcBatch &b, double lambda_h, double lambda_Jp,
+                           int *err, cudaStream_t st)
 {
     static bool attr = false;
     if (!attr) {
@@ -772,37 +862,26 @@ cudaError_t launch_tc_eval(void *prof, const int8_t *msa, const float *w, double
         if (e) return e;
         attr = true;
     }
-    const int BP = padded_B(d);
-    const int nbt = BP / TC_M;
-    char *p = (char *)scratch;
-    __nv_bfloat16 *dt_hi = (__nv_bfloat16 *)p;
-    p += align256((size_t)d.R * BP * 2);
-    __nv_bfloat16 *dt_lo = (__nv_bfloat16 *)p;
-    p += align256((size_t)d.R * BP * 2);
-    double *partial = (double *)p;
-    p += align256((size_t)nbt * d.N * sizeof(double));
-    int8_t *msaT = (int8_t *)p;
-
-    CUtensorMap m_hi, m_lo, m_dhi, m_dlo;
-    if (!make_map(&m_hi, th_hi, d.KP, d.R, TC_BK, LG_N) ||
-        !make_map(&m_lo, th_lo, d.KP, d.R, TC_BK, LG_N) ||
-        !make_map(&m_dhi, dt_hi, BP, d.R, TC_BK, TC_M) ||
-        !make_map(&m_dlo, dt_lo, BP, d.R, TC_BK, TC_M))
-        return cudaErrorInvalidValue;
-
-    size_t nT = (size_t)(d.N + 1) * BP;
-    k_msa_transpose<<<(unsigned)((nT + 255) / 256), 256, 0, st>>>(msa, d, BP, msaT);
+    if (b.nfam < 1 || b.nfam > MAX_FAM) return cudaErrorInvalidValue;
+    static LogitsParams lp;  // large parameter blocks: built on the host, passed by value
+    static GradParams gp;
+    lp.b = b;
+    gp.b = b;
+    for (int i = 0; i < b.nfam; ++i) {
+        const FamDesc &F = b.f[i];
+        if (!make_map(&lp.hi[i], F.th_hi, F.KP, F.R, TC_BK, LG_N) ||
+            !make_map(&lp.lo[i], F.th_lo, F.KP, F.R, TC_BK, LG_N) ||
+            !make_map(&gp.dhi[i], F.dt_hi, F.BP, F.R, TC_BK, TC_M) ||
+            !make_map(&gp.dlo[i], F.dt_lo, F.BP, F.R, TC_BK, TC_M))
+            return cudaErrorInvalidValue;
+    }
     void *t0 = prof ? prof_start(prof) : nullptr;
-    dim3 g1(nbt, (d.N + LG_SITES - 1) / LG_SITES);
-    k_tc_logits<<<g1, 192, TC_SMEM, st>>>(m_hi, m_lo, msa, w, 1.0 / beff, d, BP, dt_hi, dt_lo,
-                                          partial, err);
+    k_tc_logits<<<b.ntiles_logits, 192, TC_SMEM, st>>>(lp, err);
     if (prof) prof_stop(prof, "tc_logits", t0);
-    cudaError_t e = launch_finish_objective(partial, nbt, d, beff, nullptr, f_data, st);
-    if (e) return e;
+    k_tc_finish<<<b.nfam, 128, 0, st>>>(b);
     void *t1 = prof ? prof_start(prof) : nullptr;
-    dim3 g2((d.KP + GR_N - 1) / GR_N, (d.R + TC_M - 1) / TC_M);
-    k_tc_grad<<<g2, 192, TC_SMEM, st>>>(m_dhi, m_dlo, msaT, theta, d, BP, (float)(2.0 * lambda_h),
-                                        (float)(2.0 * lambda_Jp), G, err);
+    k_tc_grad<<<b.ntiles_grad, 192, TC_SMEM, st>>>(gp, (float)(2.0 * lambda_h),
+                                                   (float)(2.0 * lambda_Jp), err);
     if (prof) prof_stop(prof, "tc_grad", t1);
     count_launches(3);
     return cudaGetLastError();

@@ -1,6 +1,7 @@
 // plm_abi.cu -- the C ABI declared in include/plmdca.h: context and
 // workspace management, argument checks, host/device pointer staging, and
 // the orchestration of the kernels for each entry point.
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -242,46 +243,371 @@ plm_status check_msa(plm_ctx *ctx, const int8_t *msa_d, int B, int N)
     return PLM_OK;
 }
 
-// One objective+gradient evaluation of all sites at theta (internal layout).
-// f_data[r] = -(1/B_eff) sum_b w_b log P (no penalty); G includes 2 lambda theta.
-plm_status evaluate(plm_ctx *ctx, plm_precision prec, const int8_t *msa,
-                    const float *w, double beff, const Dims &d,
-                    const float *theta, const __nv_bfloat16 *hi,
-                    const __nv_bfloat16 *lo, double lambda_h, double lambda_Jp,
-                    double *f_data, float *G, int *tc_err)
+// ---------------------------------------------------------------------------
+// A problem = one or more families solved (or evaluated) together.  Every
+// solver vector is an arena holding the padded Theta blocks of the families
+// one after another; the sites of family f are sites site0_f .. site0_f+N_f-1.
+struct Fam {
+    const int8_t *msa = nullptr;  // device
+    Dims d;
+    size_t off = 0;   // arena offset (floats)
+    size_t woff = 0;  // offset in the concatenated weights
+    int site0 = 0;
+    double beff = 0.0;
+};
+
+struct Problem {
+    std::vector<Fam> fam;
+    size_t total = 0, wtotal = 0;
+    int nsites = 0, nchunks = 0;
+    int maxB = 0, maxN = 0;
+    size_t tc_scratch = 0;
+    LbLayout L{};
+    std::vector<TcBatch> tcb;  // the families in launches of at most MAX_FAM
+    bool tc_ready = false;
+};
+
+void layout_problem(Problem &P)
+{
+    size_t off = 0, woff = 0;
+    int site0 = 0;
+    P.tc_scratch = 0;
+    for (auto &F : P.fam) {
+        F.off = off;
+        F.woff = woff;
+        F.site0 = site0;
+        off += F.d.theta_elems();
+        woff += (size_t)F.d.B;
+        site0 += F.d.N;
+        P.maxB = std::max(P.maxB, F.d.B);
+        P.maxN = std::max(P.maxN, F.d.N);
+        P.tc_scratch += (tc_family_scratch_bytes(F.d.B, F.d.N) + 255) / 256 * 256;
+    }
+    P.total = off;
+    P.wtotal = woff;
+    P.nsites = site0;
+}
+
+// site and chunk tables of the batched L-BFGS
+plm_status build_lbfgs_tables(plm_ctx *ctx, Problem &P)
+{
+    std::vector<SiteInfo> si;
+    std::vector<ChunkInfo> ci;
+    for (size_t f = 0; f < P.fam.size(); ++f) {
+        const Fam &F = P.fam[f];
+        const int len4 = (int)(F.d.site_elems() / 4);
+        const int nch = (len4 + LB_CHUNK4 - 1) / LB_CHUNK4;
+        for (int r = 0; r < F.d.N; ++r) {
+            SiteInfo x;
+            x.off4 = (long long)((F.off + (size_t)r * F.d.site_elems()) / 4);
+            x.len4 = len4;
+            x.KP = F.d.KP;
+            x.NQ = F.d.N * Q;
+            x.chunk0 = (int)ci.size();
+            x.nchunks = nch;
+            x.family = (int)f;
+            x.r = r;
+            for (int c = 0; c < nch; ++c) {
+                ChunkInfo y;
+                y.site = (int)si.size();
+                y.e0 = c * LB_CHUNK4;
+                y.e1 = std::min(len4, (c + 1) * LB_CHUNK4);
+                ci.push_back(y);
+            }
+            si.push_back(x);
+        }
+    }
+    void *dsi, *dci;
+    CK(ws(ctx, "lb_site_info", si.size() * sizeof(SiteInfo), &dsi));
+    CK(ws(ctx, "lb_chunk_info", ci.size() * sizeof(ChunkInfo), &dci));
+    CK(cudaMemcpyAsync(dsi, si.data(), si.size() * sizeof(SiteInfo), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    CK(cudaMemcpyAsync(dci, ci.data(), ci.size() * sizeof(ChunkInfo), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    P.nchunks = (int)ci.size();
+    P.L.si = (const SiteInfo *)dsi;
+    P.L.ci = (const ChunkInfo *)dci;
+    P.L.nsites = P.nsites;
+    P.L.nchunks = P.nchunks;
+    P.L.vec4 = (long long)(P.total / 4);
+    return PLM_OK;
+}
+
+// tensor-core scratch, transposed MSAs and launch groups (once per problem)
+plm_status prepare_tc(plm_ctx *ctx, Problem &P, const float *w)
+{
+    void *base;
+    CK(ws(ctx, "tc_scratch", P.tc_scratch, &base));
+    P.tcb.clear();
+    size_t at = 0;
+    for (size_t f0 = 0; f0 < P.fam.size(); f0 += MAX_FAM) {
+        TcBatch b;
+        memset(&b, 0, sizeof b);
+        std::vector<void *> scr;
+        const size_t nf = std::min((size_t)MAX_FAM, P.fam.size() - f0);
+        b.nfam = (int)nf;
+        for (size_t i = 0; i < nf; ++i) {
+            const Fam &F = P.fam[f0 + i];
+            FamDesc &D = b.f[i];
+            D.msa = F.msa;
+            D.w = w + F.woff;
+            D.B = F.d.B;
+            D.N = F.d.N;
+            D.beff = F.beff;
+            D.inv_beff = 1.0 / F.beff;
+            scr.push_back((char *)base + at);
+            at += (tc_family_scratch_bytes(F.d.B, F.d.N) + 255) / 256 * 256;
+        }
+        CK(launch_tc_prepare(b, scr.data(), ctx->stream));
+        P.tcb.push_back(b);
+    }
+    P.tc_ready = true;
+    return PLM_OK;
+}
+
+// One objective+gradient evaluation of every site of the problem at theta
+// (arena).  f_data[site] = -(1/B_eff) sum_b w_b log P (no penalty); G (arena)
+// includes 2 lambda theta.
+plm_status evaluate(plm_ctx *ctx, plm_precision prec, Problem &P, const float *w,
+                    const float *theta, const __nv_bfloat16 *hi, const __nv_bfloat16 *lo,
+                    double lambda_h, double lambda_Jp, double *f_data, float *G, int *tc_err)
 {
     cudaStream_t st = ctx->stream;
     if (prec == PLM_FP32_EXACT) {
         void *L, *D, *part;
-        const int slices = softmax_slices(d);
-        CK(ws(ctx, "L", (size_t)d.B * d.R * sizeof(float), &L));
-        CK(ws(ctx, "D", (size_t)d.B * d.R * sizeof(float), &D));
-        CK(ws(ctx, "partial", (size_t)slices * d.N * sizeof(double), &part));
-        {
-            ProfScope ps(ctx, "logits_gather");
-            CK(launch_logits_gather(msa, theta, d, (float *)L, st));
+        size_t lmax = 0, pmax = 0;
+        for (auto &F : P.fam) {
+            lmax = std::max(lmax, (size_t)F.d.B * F.d.R);
+            pmax = std::max(pmax, (size_t)softmax_slices(F.d) * F.d.N);
         }
-        {
-            ProfScope ps(ctx, "softmax_resid");
-            CK(launch_softmax_resid(msa, w, beff, (float *)L, d, (double *)part, (float *)D, st));
-            CK(launch_finish_objective((double *)part, slices, d, beff, nullptr, f_data, st));
-        }
-        {
-            ProfScope ps(ctx, "grad_gather");
-            CK(launch_grad_gather(msa, (float *)D, theta, d, lambda_h, lambda_Jp, G, st));
+        CK(ws(ctx, "L", lmax * sizeof(float), &L));
+        CK(ws(ctx, "D", lmax * sizeof(float), &D));
+        CK(ws(ctx, "partial", pmax * sizeof(double), &part));
+        for (auto &F : P.fam) {
+            const Dims &d = F.d;
+            const int slices = softmax_slices(d);
+            const float *th = theta + F.off;
+            {
+                ProfScope ps(ctx, "logits_gather");
+                CK(launch_logits_gather(F.msa, th, d, (float *)L, st));
+            }
+            {
+                ProfScope ps(ctx, "softmax_resid");
+                CK(launch_softmax_resid(F.msa, w + F.woff, F.beff, (float *)L, d, (double *)part,
+                                        (float *)D, st));
+                CK(launch_finish_objective((double *)part, slices, d, F.beff, nullptr,
+                                           f_data + F.site0, st));
+            }
+            {
+                ProfScope ps(ctx, "grad_gather");
+                CK(launch_grad_gather(F.msa, (float *)D, th, d, lambda_h, lambda_Jp, G + F.off,
+                                      st));
+            }
         }
         return PLM_OK;
     }
     if (prec == PLM_SPLIT_BF16) {
         if (!tc_supported())
             return fail(ctx, PLM_ENOTIMPL, "split-bf16 tensor-core path needs an sm_103 GPU");
-        void *scratch;
-        CK(ws(ctx, "tc_scratch", tc_scratch_bytes(d), &scratch));
-        CK(launch_tc_eval(ctx->prof ? (void *)ctx : nullptr, msa, w, beff, hi, lo, theta, d,
-                          lambda_h, lambda_Jp, scratch, f_data, G, tc_err, st));
+        if (!P.tc_ready) {
+            plm_status s = prepare_tc(ctx, P, w);
+            if (s) return s;
+        }
+        size_t f0 = 0;
+        for (auto &b : P.tcb) {
+            for (int i = 0; i < b.nfam; ++i) {
+                const Fam &F = P.fam[f0 + i];
+                FamDesc &D = b.f[i];
+                D.th_hi = hi + F.off;
+                D.th_lo = lo + F.off;
+                D.theta = theta + F.off;
+                D.G = G + F.off;
+                D.f_data = f_data + F.site0;
+            }
+            CK(launch_tc_eval(ctx->prof ? (void *)ctx : nullptr, b, lambda_h, lambda_Jp, tc_err,
+                              st));
+            f0 += b.nfam;
+        }
         return PLM_OK;
     }
     return fail(ctx, PLM_ENOTIMPL, "precision mode %d is not built", (int)prec);
+}
+
+struct SolveOut {
+    float *h, *J;        // device (possibly staged)
+    plm_report *report;  // host, may be NULL
+};
+
+// Steps 1-3 for every family of the problem; outputs unpacked per family.
+plm_status solve_core(plm_ctx *ctx, Problem &P, const plm_opts &o, std::vector<SolveOut> &out,
+                      std::vector<plm_report> &reps)
+{
+    auto t_start = std::chrono::steady_clock::now();
+    cudaStream_t st = ctx->stream;
+    layout_problem(P);
+    const size_t nf = P.fam.size();
+
+    // step 2: reweighting, per family
+    void *scratch, *w, *beff_d, *flag;
+    CK(ws(ctx, "rw_scratch", reweight_scratch_bytes(P.maxB, P.maxN), &scratch));
+    CK(ws(ctx, "w", P.wtotal * sizeof(float), &w));
+    CK(ws(ctx, "beff", nf * sizeof(double), &beff_d));
+    CK(ws(ctx, "flag_rw", sizeof(int), &flag));
+    CK(cudaMemsetAsync(flag, 0, sizeof(int), st));
+    {
+        ProfScope ps(ctx, "reweight");
+        for (size_t f = 0; f < nf; ++f) {
+            const Fam &F = P.fam[f];
+            CK(launch_reweight(F.msa, F.d.B, F.d.N, identity_threshold(o.x, F.d.N), nullptr,
+                               (float *)w + F.woff, (double *)beff_d + f, scratch, (int *)flag,
+                               st));
+        }
+    }
+    std::vector<double> beffs(nf);
+    CK(cudaMemcpyAsync(ctx->host_counters + 9, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(beffs.data(), beff_d, nf * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (ctx->host_counters[9]) return fail(ctx, PLM_EINVAL, "msa has states outside 0..%d", Q - 1);
+    for (size_t f = 0; f < nf; ++f) P.fam[f].beff = beffs[f];
+
+    plm_status s = build_lbfgs_tables(ctx, P);
+    if (s) return s;
+    P.tc_ready = false;
+
+    // workspace of the solver
+    const size_t tb = P.total * sizeof(float);
+    void *theta, *theta_t, *g, *g_t, *dir, *Sh, *Yh, *sst, *fdat, *cnt, *part;
+    void *hi = nullptr, *lo = nullptr;
+    CK(ws(ctx, "theta", tb, &theta));
+    CK(ws(ctx, "theta_t", tb, &theta_t));
+    CK(ws(ctx, "g", tb, &g));
+    CK(ws(ctx, "G", tb, &g_t));
+    CK(ws(ctx, "dir", tb, &dir));
+    CK(ws(ctx, "S_hist", tb * o.lbfgs_m, &Sh));
+    CK(ws(ctx, "Y_hist", tb * o.lbfgs_m, &Yh));
+    CK(ws(ctx, "site_state", (size_t)P.nsites * sizeof(SiteState), &sst));
+    CK(ws(ctx, "fdata", (size_t)P.nsites * sizeof(double), &fdat));
+    CK(ws(ctx, "counters", 16 * sizeof(int), &cnt));
+    CK(ws(ctx, "lb_part", (size_t)P.nchunks * LB_PART * sizeof(double), &part));
+    if (o.prec == PLM_SPLIT_BF16) {
+        CK(ws(ctx, "theta_hi", P.total * 2, &hi));
+        CK(ws(ctx, "theta_lo", P.total * 2, &lo));
+    }
+    SolveParams p;
+    p.lambda_h = o.lambda_h;
+    p.lambda_Jp = 0.5 * o.lambda_J;  // step 1 of the rundown
+    p.gtol = o.gtol;
+    p.c1 = 1e-4;
+    p.c2 = 0.9;
+    p.noise = 1e-6;
+    p.m = o.lbfgs_m;
+    p.max_iter = o.max_iter;
+    p.max_ls = o.max_ls;
+
+    // origin start (Sec. 6)
+    CK(cudaMemsetAsync(theta, 0, tb, st));
+    CK(cudaMemsetAsync(theta_t, 0, tb, st));
+    CK(cudaMemsetAsync(dir, 0, tb, st));
+    if (hi) {
+        CK(cudaMemsetAsync(hi, 0, P.total * 2, st));
+        CK(cudaMemsetAsync(lo, 0, P.total * 2, st));
+    }
+    int evals = 0;
+    int *tc_err = (int *)cnt + 4;  // tensor-core timeout word, read back with the counters
+    CK(cudaMemsetAsync(cnt, 0, 16 * sizeof(int), st));
+    s = evaluate(ctx, o.prec, P, (const float *)w, (const float *)theta,
+                 (const __nv_bfloat16 *)hi, (const __nv_bfloat16 *)lo, p.lambda_h, p.lambda_Jp,
+                 (double *)fdat, (float *)g, tc_err);
+    if (s) return s;
+    evals++;
+    CK(launch_lbfgs_init((SiteState *)sst, (const double *)fdat, (const float *)g, P.L, p,
+                         (double *)part, st));
+
+    int *hc = ctx->host_counters;
+    int round = 0;
+    for (int it = 0; it < o.max_iter; ++it) {
+        CK(cudaMemsetAsync(cnt, 0, 2 * sizeof(int), st));
+        {
+            ProfScope ps(ctx, "lbfgs_direction");
+            CK(launch_lbfgs_direction((SiteState *)sst, (const float *)g, (float *)dir,
+                                      (const float *)Sh, (const float *)Yh, P.L, p,
+                                      (double *)part, st));
+        }
+        for (int ls = 0; ls < o.max_ls + 1; ++ls) {
+            ++round;
+            {
+                ProfScope ps(ctx, "lbfgs_trial");
+                CK(launch_lbfgs_trial((SiteState *)sst, (const float *)theta, (const float *)g,
+                                      (float *)dir, (float *)theta_t, (__nv_bfloat16 *)hi,
+                                      (__nv_bfloat16 *)lo, P.L, p, (double *)part, st));
+            }
+            s = evaluate(ctx, o.prec, P, (const float *)w, (const float *)theta_t,
+                         (const __nv_bfloat16 *)hi, (const __nv_bfloat16 *)lo, p.lambda_h,
+                         p.lambda_Jp, (double *)fdat, (float *)g_t, tc_err);
+            if (s) return s;
+            evals++;
+            CK(cudaMemsetAsync(cnt, 0, sizeof(int), st));
+            {
+                ProfScope ps(ctx, "lbfgs_linesearch");
+                CK(launch_lbfgs_linesearch((SiteState *)sst, (const double *)fdat,
+                                           (float *)theta, (float *)g, (const float *)theta_t,
+                                           (const float *)g_t, (const float *)dir, (float *)Sh,
+                                           (float *)Yh, P.L, p, (double *)part, round,
+                                           (int *)cnt, st));
+            }
+            CK(cudaMemcpyAsync(hc, cnt, 5 * sizeof(int), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            if (hc[4])
+                return fail(ctx, PLM_ETIMEOUT, "tensor-core pipeline wait timed out (code 0x%x)",
+                            hc[4]);
+            if (hc[0] == 0) break;
+        }
+        if (hc[1] == 0) break;  // no site left to iterate
+    }
+
+    for (size_t f = 0; f < nf; ++f)
+        CK(launch_unpack_theta((const float *)theta + P.fam[f].off, P.fam[f].d, out[f].h,
+                               out[f].J, st));
+    std::vector<SiteState> host(P.nsites);
+    CK(cudaMemcpyAsync(host.data(), sst, (size_t)P.nsites * sizeof(SiteState),
+                       cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const double secs =
+        std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    reps.assign(nf, plm_report{});
+    for (size_t f = 0; f < nf; ++f) {
+        plm_report &rep = reps[f];
+        memset(&rep, 0, sizeof rep);
+        rep.evals = evals;
+        rep.beff = P.fam[f].beff;
+        rep.seconds = secs;
+        for (int r = 0; r < P.fam[f].d.N; ++r) {
+            const SiteState &x = host[P.fam[f].site0 + r];
+            rep.iters = std::max(rep.iters, x.iters);
+            rep.f_total += x.f;
+            rep.gnorm_max = std::max(rep.gnorm_max, std::sqrt(x.gnorm2));
+            if (x.status == SITE_CONVERGED) rep.n_converged++;
+            else if (x.status == SITE_NOISE) rep.n_noise++;
+            else rep.n_failed++;
+        }
+    }
+    return PLM_OK;
+}
+
+plm_status check_opts(plm_ctx *ctx, const plm_opts &o)
+{
+    if (!(o.x >= 0.0 && o.x <= 1.0)) return fail(ctx, PLM_EINVAL, "x must lie in [0, 1]");
+    if (o.lambda_h < 0 || o.lambda_J < 0) return fail(ctx, PLM_EINVAL, "negative lambda");
+    if (!(o.lambda_h > 0 && o.lambda_J > 0))
+        return fail(ctx, PLM_EINVAL, "lambda_h and lambda_J must be > 0 (the l2 term makes "
+                                     "each site problem strongly convex)");
+    if (o.lbfgs_m < 1 || o.lbfgs_m > MAX_M)
+        return fail(ctx, PLM_EINVAL, "lbfgs_m must be 1..%d", MAX_M);
+    if (o.max_ls < 1) return fail(ctx, PLM_EINVAL, "max_ls must be >= 1");
+    if (!(o.gtol >= 0)) return fail(ctx, PLM_EINVAL, "gtol must be >= 0");
+    if (o.prec != PLM_FP32_EXACT && o.prec != PLM_SPLIT_BF16)
+        return fail(ctx, PLM_ENOTIMPL, "precision mode %d is not built", (int)o.prec);
+    return PLM_OK;
 }
 
 }  // namespace
@@ -459,6 +785,13 @@ plm_status plm_site_objective_grad(plm_ctx *ctx, const int8_t *msa,
     CK(stage_out(ctx, "out_f", f_out, (size_t)N * sizeof(double), &f_s));
     CK(stage_out(ctx, "out_gh", gh, NQ * sizeof(float), &gh_s));
     CK(stage_out(ctx, "out_gJ", gJ, NQ * NQ * sizeof(float), &gJ_s));
+    Problem P;
+    Fam F;
+    F.msa = (const int8_t *)msa_d;
+    F.d = d;
+    F.beff = beff;
+    P.fam.push_back(F);
+    layout_problem(P);
     void *theta, *G, *pen, *fdat, *hi = nullptr, *lo = nullptr;
     CK(ws(ctx, "theta", d.theta_elems() * sizeof(float), &theta));
     CK(ws(ctx, "G", d.theta_elems() * sizeof(float), &G));
@@ -470,17 +803,18 @@ plm_status plm_site_objective_grad(plm_ctx *ctx, const int8_t *msa,
     if (prec == PLM_SPLIT_BF16) {
         CK(ws(ctx, "theta_hi", d.theta_elems() * 2, &hi));
         CK(ws(ctx, "theta_lo", d.theta_elems() * 2, &lo));
-        CK(launch_split_theta((const float *)theta, d, (__nv_bfloat16 *)hi,
+        CK(launch_split_theta((const float *)theta, d.theta_elems(), (__nv_bfloat16 *)hi,
                               (__nv_bfloat16 *)lo, ctx->stream));
     }
     void *tcflag;
     CK(ws(ctx, "flag_tc", sizeof(int), &tcflag));
     CK(cudaMemsetAsync(tcflag, 0, sizeof(int), ctx->stream));
-    s = evaluate(ctx, prec, (const int8_t *)msa_d, (const float *)w_d, beff, d,
-                 (const float *)theta, (const __nv_bfloat16 *)hi, (const __nv_bfloat16 *)lo,
-                 lambda_h, lJp, (double *)fdat, (float *)G, (int *)tcflag);
+    s = evaluate(ctx, prec, P, (const float *)w_d, (const float *)theta,
+                 (const __nv_bfloat16 *)hi, (const __nv_bfloat16 *)lo, lambda_h, lJp,
+                 (double *)fdat, (float *)G, (int *)tcflag);
     if (s) return s;
-    // f = data + penalty
+    // f = data + penalty (the finishing kernel with one "slice" and B_eff = -1
+    // computes -(-fdata) + pen)
     void *fsum;
     CK(ws(ctx, "fsum", (size_t)N * sizeof(double), &fsum));
     CK(launch_finish_objective((const double *)fdat, 1, d, -1.0, (const double *)pen,
@@ -507,174 +841,70 @@ plm_status plm_solve(plm_ctx *ctx, const int8_t *msa, int B, int N, int q,
                      const plm_opts *opts, float *h_out, float *J_out,
                      plm_report *report)
 {
-    auto t_start = std::chrono::steady_clock::now();
-    plm_status s = check_common(ctx, B, N, q);
-    if (s) return s;
-    if (!msa) return fail(ctx, PLM_EINVAL, "msa is NULL");
+    plm_family fam;
+    fam.msa = msa;
+    fam.B = B;
+    fam.N = N;
+    fam.h_out = h_out;
+    fam.J_out = J_out;
+    return plm_solve_batch(ctx, &fam, 1, q, opts, report);
+}
+
+plm_status plm_solve_batch(plm_ctx *ctx, const plm_family *fams, int nfam, int q,
+                           const plm_opts *opts, plm_report *reports)
+{
+    if (!ctx) return PLM_EINVAL;
+    if (!fams || nfam < 1) return fail(ctx, PLM_EINVAL, "need at least one family");
+    for (int f = 0; f < nfam; ++f) {
+        plm_status s = check_common(ctx, fams[f].B, fams[f].N, q);
+        if (s) return s;
+        if (!fams[f].msa) return fail(ctx, PLM_EINVAL, "family %d: msa is NULL", f);
+    }
     plm_opts o;
     if (opts) o = *opts;
     else plm_default_opts(&o);
-    if (!(o.x >= 0.0 && o.x <= 1.0)) return fail(ctx, PLM_EINVAL, "x must lie in [0, 1]");
-    if (o.lambda_h < 0 || o.lambda_J < 0) return fail(ctx, PLM_EINVAL, "negative lambda");
-    if (!(o.lambda_h > 0 && o.lambda_J > 0))
-        return fail(ctx, PLM_EINVAL, "lambda_h and lambda_J must be > 0 (the l2 term makes "
-                                     "each site problem strongly convex)");
-    if (o.lbfgs_m < 1 || o.lbfgs_m > MAX_M) return fail(ctx, PLM_EINVAL, "lbfgs_m must be 1..%d", MAX_M);
-    if (o.max_ls < 1) return fail(ctx, PLM_EINVAL, "max_ls must be >= 1");
-    if (!(o.gtol >= 0)) return fail(ctx, PLM_EINVAL, "gtol must be >= 0");
-    if (o.prec != PLM_FP32_EXACT && o.prec != PLM_SPLIT_BF16)
-        return fail(ctx, PLM_ENOTIMPL, "precision mode %d is not built", (int)o.prec);
-    CK(cudaSetDevice(ctx->device));
-    cudaStream_t st = ctx->stream;
-    const Dims d = make_dims(B, N);
-    const size_t NQ = (size_t)N * Q;
-
-    const void *msa_d;
-    CK(stage_in(ctx, "in_msa", msa, (size_t)B * N, &msa_d));
-    const int8_t *S = (const int8_t *)msa_d;
-    Staged h_s, J_s;
-    CK(stage_out(ctx, "out_h", h_out, NQ * sizeof(float), &h_s));
-    CK(stage_out(ctx, "out_J", J_out, NQ * NQ * sizeof(float), &J_s));
-
-    // step 2: reweighting
-    void *scratch, *w, *beff_d, *flag;
-    CK(ws(ctx, "rw_scratch", reweight_scratch_bytes(B, N), &scratch));
-    CK(ws(ctx, "w", (size_t)B * sizeof(float), &w));
-    CK(ws(ctx, "beff", sizeof(double), &beff_d));
-    CK(ws(ctx, "flag_rw", sizeof(int), &flag));
-    CK(cudaMemsetAsync(flag, 0, sizeof(int), st));
-    {
-        ProfScope ps(ctx, "reweight");
-        CK(launch_reweight(S, B, N, identity_threshold(o.x, N), nullptr, (float *)w,
-                           (double *)beff_d, scratch, (int *)flag, st));
-    }
-    CK(cudaMemcpyAsync(ctx->host_scalars, beff_d, sizeof(double), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(ctx->host_counters + 9, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    if (ctx->host_counters[9]) return fail(ctx, PLM_EINVAL, "msa has states outside 0..%d", Q - 1);
-    const double beff = ctx->host_scalars[0];
-
-    // workspace of the solver
-    const size_t tb = d.theta_elems() * sizeof(float);
-    void *theta, *theta_t, *g, *g_t, *dir, *Sh, *Yh, *sst, *fdat, *cnt;
-    void *hi = nullptr, *lo = nullptr;
-    CK(ws(ctx, "theta", tb, &theta));
-    CK(ws(ctx, "theta_t", tb, &theta_t));
-    CK(ws(ctx, "g", tb, &g));
-    CK(ws(ctx, "G", tb, &g_t));
-    CK(ws(ctx, "dir", tb, &dir));
-    CK(ws(ctx, "S_hist", tb * o.lbfgs_m, &Sh));
-    CK(ws(ctx, "Y_hist", tb * o.lbfgs_m, &Yh));
-    CK(ws(ctx, "site_state", (size_t)N * sizeof(SiteState), &sst));
-    CK(ws(ctx, "fdata", (size_t)N * sizeof(double), &fdat));
-    CK(ws(ctx, "counters", 16 * sizeof(int), &cnt));
-    if (o.prec == PLM_SPLIT_BF16) {
-        CK(ws(ctx, "theta_hi", d.theta_elems() * 2, &hi));
-        CK(ws(ctx, "theta_lo", d.theta_elems() * 2, &lo));
-    }
-    SolveParams p;
-    p.lambda_h = o.lambda_h;
-    p.lambda_Jp = 0.5 * o.lambda_J;  // step 1 of the rundown
-    p.gtol = o.gtol;
-    p.c1 = 1e-4;
-    p.c2 = 0.9;
-    p.noise = 1e-6;
-    p.m = o.lbfgs_m;
-    p.max_iter = o.max_iter;
-    p.max_ls = o.max_ls;
-
-    // origin start (Sec. 6)
-    CK(cudaMemsetAsync(theta, 0, tb, st));
-    CK(cudaMemsetAsync(theta_t, 0, tb, st));
-    CK(cudaMemsetAsync(dir, 0, tb, st));
-    if (hi) {
-        CK(cudaMemsetAsync(hi, 0, d.theta_elems() * 2, st));
-        CK(cudaMemsetAsync(lo, 0, d.theta_elems() * 2, st));
-    }
-    int evals = 0;
-    int *tc_err = (int *)cnt + 4;  // tensor-core timeout word, read back with the counters
-    void *part;
-    CK(ws(ctx, "lb_part", (size_t)N * lbfgs_chunks(d) * LB_PART * sizeof(double), &part));
-    CK(cudaMemsetAsync(cnt, 0, 16 * sizeof(int), st));
-    s = evaluate(ctx, o.prec, S, (const float *)w, beff, d, (const float *)theta,
-                 (const __nv_bfloat16 *)hi, (const __nv_bfloat16 *)lo, p.lambda_h,
-                 p.lambda_Jp, (double *)fdat, (float *)g, tc_err);
+    plm_status s = check_opts(ctx, o);
     if (s) return s;
-    evals++;
-    CK(launch_lbfgs_init((SiteState *)sst, (const double *)fdat, (const float *)g, d, p,
-                         (double *)part, st));
-
-    int *hc = ctx->host_counters;
-    int round = 0;
-    for (int it = 0; it < o.max_iter; ++it) {
-        CK(cudaMemsetAsync(cnt, 0, 2 * sizeof(int), st));
-        {
-            ProfScope ps(ctx, "lbfgs_direction");
-            CK(launch_lbfgs_direction((SiteState *)sst, (const float *)g, (float *)dir,
-                                      (const float *)Sh, (const float *)Yh, d, p,
-                                      (double *)part, st));
-        }
-        for (int ls = 0; ls < o.max_ls + 1; ++ls) {
-            ++round;
-            {
-                ProfScope ps(ctx, "lbfgs_trial");
-                CK(launch_lbfgs_trial((SiteState *)sst, (const float *)theta, (const float *)g,
-                                      (float *)dir, (float *)theta_t, (__nv_bfloat16 *)hi,
-                                      (__nv_bfloat16 *)lo, d, p, (double *)part, st));
-            }
-            s = evaluate(ctx, o.prec, S, (const float *)w, beff, d, (const float *)theta_t,
-                         (const __nv_bfloat16 *)hi, (const __nv_bfloat16 *)lo, p.lambda_h,
-                         p.lambda_Jp, (double *)fdat, (float *)g_t, tc_err);
-            if (s) return s;
-            evals++;
-            CK(cudaMemsetAsync(cnt, 0, sizeof(int), st));
-            {
-                ProfScope ps(ctx, "lbfgs_linesearch");
-                CK(launch_lbfgs_linesearch((SiteState *)sst, (const double *)fdat,
-                                           (float *)theta, (float *)g, (const float *)theta_t,
-                                           (const float *)g_t, (const float *)dir, (float *)Sh,
-                                           (float *)Yh, d, p, (double *)part, round, (int *)cnt,
-                                           st));
-            }
-            CK(cudaMemcpyAsync(hc, cnt, 5 * sizeof(int), cudaMemcpyDeviceToHost, st));
-            CK(cudaStreamSynchronize(st));
-            if (hc[4])
-                return fail(ctx, PLM_ETIMEOUT, "tensor-core pipeline wait timed out (code 0x%x)",
-                            hc[4]);
-            if (hc[0] == 0) break;
-        }
-        if (hc[1] == 0) break;  // no site left to iterate
+    CK(cudaSetDevice(ctx->device));
+    Problem P;
+    std::vector<SolveOut> out(nfam);
+    std::vector<Staged> hs(nfam), Js(nfam);
+    char name[64];
+    for (int f = 0; f < nfam; ++f) {
+        const int B = fams[f].B, N = fams[f].N;
+        const size_t NQ = (size_t)N * Q;
+        const void *msa_d;
+        snprintf(name, sizeof name, "in_msa_%d", f);
+        CK(stage_in(ctx, name, fams[f].msa, (size_t)B * N, &msa_d));
+        snprintf(name, sizeof name, "out_h_%d", f);
+        CK(stage_out(ctx, name, fams[f].h_out, NQ * sizeof(float), &hs[f]));
+        snprintf(name, sizeof name, "out_J_%d", f);
+        CK(stage_out(ctx, name, fams[f].J_out, NQ * NQ * sizeof(float), &Js[f]));
+        Fam F;
+        F.msa = (const int8_t *)msa_d;
+        F.d = make_dims(B, N);
+        P.fam.push_back(F);
+        out[f].h = (float *)hs[f].dev;
+        out[f].J = (float *)Js[f].dev;
     }
-
-    CK(launch_unpack_theta((const float *)theta, d, (float *)h_s.dev, (float *)J_s.dev, st));
-    CK(copy_back(ctx, h_s));
-    CK(copy_back(ctx, J_s));
-    std::vector<SiteState> host(N);
-    CK(cudaMemcpyAsync(host.data(), sst, (size_t)N * sizeof(SiteState), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    plm_report rep;
-    memset(&rep, 0, sizeof rep);
-    rep.evals = evals;
-    rep.beff = beff;
-    bool all_conv = true;
-    for (int r = 0; r < N; ++r) {
-        const SiteState &x = host[r];
-        rep.iters = x.iters > rep.iters ? x.iters : rep.iters;
-        rep.f_total += x.f;
-        double gn = std::sqrt(x.gnorm2);
-        if (gn > rep.gnorm_max) rep.gnorm_max = gn;
-        if (x.status == SITE_CONVERGED) rep.n_converged++;
-        else {
-            all_conv = false;
-            if (x.status == SITE_NOISE) rep.n_noise++;
-            else rep.n_failed++;
-        }
+    std::vector<plm_report> reps;
+    s = solve_core(ctx, P, o, out, reps);
+    if (s) return s;
+    for (int f = 0; f < nfam; ++f) {
+        CK(copy_back(ctx, hs[f]));
+        CK(copy_back(ctx, Js[f]));
     }
-    rep.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
-    if (report) *report = rep;
-    if (!all_conv)
+    CK(cudaStreamSynchronize(ctx->stream));
+    int notconv = 0, noise = 0, total = 0;
+    for (int f = 0; f < nfam; ++f) {
+        if (reports) reports[f] = reps[f];
+        notconv += reps[f].n_noise + reps[f].n_failed;
+        noise += reps[f].n_noise;
+        total += fams[f].N;
+    }
+    if (notconv)
         return fail(ctx, PLM_ENOTCONV, "%d of %d sites stopped before gtol (%d at the noise floor)",
-                    rep.n_noise + rep.n_failed, N, rep.n_noise);
+                    notconv, total, noise);
     return PLM_OK;
 }
 

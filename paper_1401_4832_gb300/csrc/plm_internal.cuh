@@ -137,25 +137,51 @@ cudaError_t launch_grad_gather(const int8_t *msa, const float *D,
                                cudaStream_t st);
 
 // ---- L-BFGS (k_lbfgs.cu) ----
-// Every vector kernel runs on a (chunk, site) grid: the site's segment of
-// QP*KP floats is cut into lbfgs_chunks(d) chunks; partial FP64 sums go to
-// part[(site * nchunks + chunk) * LB_PART + k] and are reduced per site in
-// a fixed order by the one-warp-per-site scalar kernels.
-int lbfgs_chunks(const Dims &d);
+// All vectors of the solver (theta, g, d, S, Y ...) are arenas holding the
+// padded Theta blocks of every family one after another.  A site is a row
+// block of one family; its segment is described by SiteInfo, cut into
+// chunks of at most LB_CHUNK4 float4 (ChunkInfo).  Vector kernels run one
+// CTA per chunk and write FP64 partial sums to part[chunk * LB_PART + k];
+// one-warp-per-site kernels reduce a site's chunks in a fixed order.
+constexpr int LB_CHUNK4 = 2048;
+
+struct SiteInfo {
+    long long off4;  // float4 offset of the segment in every arena vector
+    int len4;        // float4 count of the segment (QP * KP / 4)
+    int KP;          // padded columns of the family
+    int NQ;          // N_f * Q: the field column
+    int chunk0;      // first chunk of the site
+    int nchunks;
+    int family;
+    int r;           // site index inside its family
+};
+
+struct ChunkInfo {
+    int site;
+    int e0, e1;  // float4 range inside the site segment
+};
+
+struct LbLayout {
+    const SiteInfo *si;
+    const ChunkInfo *ci;
+    int nsites, nchunks;
+    long long vec4;  // float4 stride between history slots (arena size / 4)
+};
+
 cudaError_t launch_lbfgs_init(SiteState *ss, const double *f, const float *g,
-                              const Dims &d, const SolveParams &p, double *part,
+                              const LbLayout &L, const SolveParams &p, double *part,
                               cudaStream_t st);
 // direction d = -H g (compact representation) and line-search set-up
 cudaError_t launch_lbfgs_direction(SiteState *ss, const float *g, float *dir,
                                    const float *S_hist, const float *Y_hist,
-                                   const Dims &d, const SolveParams &p,
+                                   const LbLayout &L, const SolveParams &p,
                                    double *part, cudaStream_t st);
 cudaError_t launch_lbfgs_trial(SiteState *ss, const float *theta,
                                const float *g, float *dir, float *theta_t,
                                __nv_bfloat16 *hi, __nv_bfloat16 *lo,
-                               const Dims &d, const SolveParams &p, double *part,
+                               const LbLayout &L, const SolveParams &p, double *part,
                                cudaStream_t st);
-// consumes f_data[r] (data part of the objective at theta_t) and g_t; the
+// consumes f_data[site] (data part of the objective at theta_t) and g_t; the
 // decision is taken per site; accepted steps are committed in the same call
 // (S, Y, theta, g updated).  counters[0] += #sites still searching,
 // counters[1] += #sites that became ready for a new direction.
@@ -163,7 +189,7 @@ cudaError_t launch_lbfgs_linesearch(SiteState *ss, const double *f_data,
                                     float *theta, float *g,
                                     const float *theta_t, const float *g_t,
                                     const float *dir, float *S_hist,
-                                    float *Y_hist, const Dims &d,
+                                    float *Y_hist, const LbLayout &L,
                                     const SolveParams &p, double *part,
                                     int round, int *counters, cudaStream_t st);
 
@@ -179,20 +205,47 @@ cudaError_t launch_topL(const double *score, int N, int L, int min_sep,
                         int32_t *ij, void *scratch, cudaStream_t st);
 
 // ---- tcgen05 split-BF16 path (k_tc.cu) ----
+// A batch of families evaluated by one launch of each kernel: the tiles of
+// every family form one grid.  Each family's arrays are sub-ranges of the
+// solver arenas.
+constexpr int MAX_FAM = 64;  // families per launch
+
+struct FamDesc {
+    const __nv_bfloat16 *th_hi, *th_lo;  // [R][KP] split theta (the logits' B operand)
+    const int8_t *msa;        // [B][N]
+    const int8_t *msaT;       // [N+1][BP] transposed, padded (built by launch_tc_prepare)
+    const float *w;           // [B]
+    const float *theta;       // [R][KP] fp32 (penalty term of the gradient)
+    float *G;                 // [R][KP] gradient out
+    __nv_bfloat16 *dt_hi, *dt_lo;  // [R][BP] residual, transposed
+    double *partial;          // [BP/128][N] objective partials
+    double *f_data;           // [N] objective out (data term)
+    double inv_beff, beff;
+    int B, N, KP, BP, R;
+    int tile0_logits, tile0_grad;  // first tile of the family in each grid
+    int pad_;
+};
+
+struct TcBatch {
+    int nfam;
+    int ntiles_logits, ntiles_grad;
+    FamDesc f[MAX_FAM];
+};
+
 // split theta (fp32) into bf16 hi + lo: hi = RN(x), lo = RN(x - hi)
-cudaError_t launch_split_theta(const float *theta, const Dims &d,
-                               __nv_bfloat16 *hi, __nv_bfloat16 *lo,
-                               cudaStream_t st);
-size_t tc_scratch_bytes(const Dims &d);
+cudaError_t launch_split_theta(const float *theta, size_t n, __nv_bfloat16 *hi,
+                               __nv_bfloat16 *lo, cudaStream_t st);
 int tc_supported();
-// logits GEMM with fused log-softmax epilogue: writes objective partials
-// [n_btiles][N] and the residual D^T (split bf16) [R][BP]
+// bytes of residual / partial / transposed-MSA scratch of one family
+size_t tc_family_scratch_bytes(int B, int N);
+int tc_padded_B(int B);
+// fills the scratch pointers, tile offsets and msaT of every family
+// (launches the transposes); scratch[f] points at tc_family_scratch_bytes
+cudaError_t launch_tc_prepare(TcBatch &b, void *const *scratch, cudaStream_t st);
+// one evaluation of every family of the batch at its split theta (th_hi/lo):
+// f_data (data term) and G (with 2 lambda theta) per family
 // prof: opaque context pointer for per-kernel event timing (NULL = off)
-cudaError_t launch_tc_eval(void *prof, const int8_t *msa, const float *w, double beff,
-                           const __nv_bfloat16 *th_hi,
-                           const __nv_bfloat16 *th_lo, const float *theta,
-                           const Dims &d, double lambda_h, double lambda_Jp,
-                           void *scratch, double *f_data, float *G,
+cudaError_t launch_tc_eval(void *prof, const TcBatch &b, double lambda_h, double lambda_Jp,
                            int *err_flag, cudaStream_t st);
 
 }  // namespace plm
