@@ -421,8 +421,10 @@ __device__ double safe_interp(double lo, double flo, double dlo, double hi, doub
 enum { LS_CONTINUE = 0, LS_ACCEPT = 1, LS_FAIL = 2 };
 
 __global__ void k_ls_decide(SiteState *ss, const double *__restrict__ f_data, const double *part,
-                            const SiteInfo *si, SolveParams p, int round, int *counters)
+                            const SiteInfo *si, SolveParams p, const int *round_ptr,
+                            int *counters)
 {
+    const int round = *round_ptr;
     const int r = blockIdx.x;
     SiteState &s = ss[r];
     if (s.status != SITE_SEARCHING) return;
@@ -499,8 +501,9 @@ __global__ void __launch_bounds__(LB_THREADS)
 k_commit(const SiteState *ss, float *__restrict__ theta, float *__restrict__ g,
          const float *__restrict__ theta_t, const float *__restrict__ g_t,
          float *__restrict__ S, float *__restrict__ Y, const SiteInfo *si, const ChunkInfo *ci,
-         long long vec4, int round)
+         long long vec4, const int *round_ptr)
 {
+    const int round = *round_ptr;
     const Chunk ch = chunk_of(si, ci);
     const SiteState &s = ss[ch.site];
     if (s.commit_round != round) return;
@@ -575,14 +578,29 @@ cudaError_t launch_lbfgs_trial(SiteState *ss, const float *theta, const float *g
 cudaError_t launch_lbfgs_linesearch(SiteState *ss, const double *f_data, float *theta, float *g,
                                     const float *theta_t, const float *g_t, const float *dir,
                                     float *S_hist, float *Y_hist, const LbLayout &L,
-                                    const SolveParams &p, double *part, int round,
+                                    const SolveParams &p, double *part, const int *round_ptr,
                                     int *counters, cudaStream_t st)
 {
     k_ls_dots<<<L.nchunks, LB_THREADS, 0, st>>>(ss, g_t, dir, L.si, L.ci, part);
-    k_ls_decide<<<L.nsites, 32, 0, st>>>(ss, f_data, part, L.si, p, round, counters);
+    k_ls_decide<<<L.nsites, 32, 0, st>>>(ss, f_data, part, L.si, p, round_ptr, counters);
     k_commit<<<L.nchunks, LB_THREADS, 0, st>>>(ss, theta, g, theta_t, g_t, S_hist, Y_hist, L.si,
-                                                L.ci, L.vec4, round);
+                                                L.ci, L.vec4, round_ptr);
     count_launches(3);
+    return cudaGetLastError();
+}
+
+namespace {
+__global__ void k_round_inc(int *round_ptr, int *counters)
+{
+    *round_ptr += 1;
+    counters[0] = 0;  // sites still searching after this round
+}
+}  // namespace
+
+cudaError_t launch_round_begin(int *round_ptr, int *counters, cudaStream_t st)
+{
+    k_round_inc<<<1, 1, 0, st>>>(round_ptr, counters);
+    count_launches(1);
     return cudaGetLastError();
 }
 

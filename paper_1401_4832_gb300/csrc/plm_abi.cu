@@ -524,38 +524,74 @@ plm_status solve_core(plm_ctx *ctx, Problem &P, const plm_opts &o, std::vector<S
                          (double *)part, st));
 
     int *hc = ctx->host_counters;
-    int round = 0;
-    for (int it = 0; it < o.max_iter; ++it) {
+    int *round_ptr = (int *)cnt + 8;  // device round counter (commit matching)
+    // the per-iteration launches: eagerly, or replayed from two CUDA graphs
+    auto direction_step = [&]() -> plm_status {
         CK(cudaMemsetAsync(cnt, 0, 2 * sizeof(int), st));
+        ProfScope ps(ctx, "lbfgs_direction");
+        CK(launch_lbfgs_direction((SiteState *)sst, (const float *)g, (float *)dir,
+                                  (const float *)Sh, (const float *)Yh, P.L, p, (double *)part,
+                                  st));
+        return PLM_OK;
+    };
+    auto round_step = [&]() -> plm_status {
+        CK(launch_round_begin(round_ptr, (int *)cnt, st));
         {
-            ProfScope ps(ctx, "lbfgs_direction");
-            CK(launch_lbfgs_direction((SiteState *)sst, (const float *)g, (float *)dir,
-                                      (const float *)Sh, (const float *)Yh, P.L, p,
-                                      (double *)part, st));
+            ProfScope ps(ctx, "lbfgs_trial");
+            CK(launch_lbfgs_trial((SiteState *)sst, (const float *)theta, (const float *)g,
+                                  (float *)dir, (float *)theta_t, (__nv_bfloat16 *)hi,
+                                  (__nv_bfloat16 *)lo, P.L, p, (double *)part, st));
+        }
+        plm_status s2 = evaluate(ctx, o.prec, P, (const float *)w, (const float *)theta_t,
+                                 (const __nv_bfloat16 *)hi, (const __nv_bfloat16 *)lo, p.lambda_h,
+                                 p.lambda_Jp, (double *)fdat, (float *)g_t, tc_err);
+        if (s2) return s2;
+        {
+            ProfScope ps(ctx, "lbfgs_linesearch");
+            CK(launch_lbfgs_linesearch((SiteState *)sst, (const double *)fdat, (float *)theta,
+                                       (float *)g, (const float *)theta_t, (const float *)g_t,
+                                       (const float *)dir, (float *)Sh, (float *)Yh, P.L, p,
+                                       (double *)part, round_ptr, (int *)cnt, st));
+        }
+        CK(cudaMemcpyAsync(hc, cnt, 5 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        return PLM_OK;
+    };
+    cudaGraphExec_t g_dir = nullptr, g_round = nullptr;
+    const bool use_graph = o.use_graph && st != nullptr && !ctx->prof;
+    if (use_graph) {
+        cudaGraph_t gr;
+        for (int k = 0; k < 2; ++k) {
+            CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            plm_status s2 = k == 0 ? direction_step() : round_step();
+            cudaError_t e = cudaStreamEndCapture(st, &gr);
+            if (s2) return s2;
+            if (e) return cuda_fail(ctx, e, "cudaStreamEndCapture");
+            e = cudaGraphInstantiate(k == 0 ? &g_dir : &g_round, gr, 0);
+            cudaGraphDestroy(gr);
+            if (e) return cuda_fail(ctx, e, "cudaGraphInstantiate");
+        }
+    }
+    struct GraphGuard {
+        cudaGraphExec_t a, b;
+        ~GraphGuard()
+        {
+            if (a) cudaGraphExecDestroy(a);
+            if (b) cudaGraphExecDestroy(b);
+        }
+    } guard{g_dir, g_round};
+    for (int it = 0; it < o.max_iter; ++it) {
+        if (use_graph) CK(cudaGraphLaunch(g_dir, st));
+        else {
+            s = direction_step();
+            if (s) return s;
         }
         for (int ls = 0; ls < o.max_ls + 1; ++ls) {
-            ++round;
-            {
-                ProfScope ps(ctx, "lbfgs_trial");
-                CK(launch_lbfgs_trial((SiteState *)sst, (const float *)theta, (const float *)g,
-                                      (float *)dir, (float *)theta_t, (__nv_bfloat16 *)hi,
-                                      (__nv_bfloat16 *)lo, P.L, p, (double *)part, st));
+            if (use_graph) CK(cudaGraphLaunch(g_round, st));
+            else {
+                s = round_step();
+                if (s) return s;
             }
-            s = evaluate(ctx, o.prec, P, (const float *)w, (const float *)theta_t,
-                         (const __nv_bfloat16 *)hi, (const __nv_bfloat16 *)lo, p.lambda_h,
-                         p.lambda_Jp, (double *)fdat, (float *)g_t, tc_err);
-            if (s) return s;
             evals++;
-            CK(cudaMemsetAsync(cnt, 0, sizeof(int), st));
-            {
-                ProfScope ps(ctx, "lbfgs_linesearch");
-                CK(launch_lbfgs_linesearch((SiteState *)sst, (const double *)fdat,
-                                           (float *)theta, (float *)g, (const float *)theta_t,
-                                           (const float *)g_t, (const float *)dir, (float *)Sh,
-                                           (float *)Yh, P.L, p, (double *)part, round,
-                                           (int *)cnt, st));
-            }
-            CK(cudaMemcpyAsync(hc, cnt, 5 * sizeof(int), cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
             if (hc[4])
                 return fail(ctx, PLM_ETIMEOUT, "tensor-core pipeline wait timed out (code 0x%x)",

@@ -191,7 +191,9 @@ cudaError_t launch_lbfgs_linesearch(SiteState *ss, const double *f_data,
                                     const float *dir, float *S_hist,
                                     float *Y_hist, const LbLayout &L,
                                     const SolveParams &p, double *part,
-                                    int round, int *counters, cudaStream_t st);
+                                    const int *round_ptr, int *counters, cudaStream_t st);
+// start of a line-search round: ++*round_ptr, counters[0] = 0
+cudaError_t launch_round_begin(int *round_ptr, int *counters, cudaStream_t st);
 
 // ---- scores (k_scores.cu) ----
 cudaError_t launch_fn(const float *J, int N, int combine, double *fn,

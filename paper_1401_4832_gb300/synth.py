@@ -283,7 +283,7 @@ def scale_family(seed: int = 0, sweeps: int = 100, **kw) -> Family:
                   name="scale N=500 B=50000", **kw)
 
 
-def batch_families(count: int = 64, sweeps: int = 200, **kw) -> list[Family]:
+def batch_families(count: int = 64, sweeps: int = 100, **kw) -> list[Family]:
     """``count`` families, family f seeded with f: N ~ U{50..300},
     B = round(exp(U(ln 500, ln 20000))), ceil(1.5 N) chain pairs, 15 % gaps."""
     fams = []
