@@ -42,6 +42,9 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32-cmp", action="store_true",
                     help="skip timing the plain FP32 path beside the split-bf16 one")
+    ap.add_argument("--workload", default="family", choices=["family", "batch", "scale"],
+                    help="family: the benchmark line; batch (64 families) and scale "
+                         "(N=500, B=50000): separate measurements")
     ap.add_argument("--cpu-sites", type=int, default=0,
                     help="sites per CPU-oracle sample (0 = one per host core, at most 16)")
     return ap.parse_args()
@@ -163,8 +166,71 @@ def run_reference(args, rank):
     }), flush=True)
 
 
+def run_batch(args):
+    """64 families (N ~ U{50..300}, B log-uniform in [500, 20000]) in one
+    batched solve vs the same families solved one after another."""
+    import torch
+    from paper_1401_4832_gb300 import api, synth
+    fams = synth.batch_families()
+    stream = torch.cuda.Stream()
+    ctx = api.Context(0, stream)
+    msas = [torch.from_numpy(f.msa).cuda() for f in fams]
+    out = {}
+    with torch.cuda.stream(stream):
+        for mode in ("batched", "one_by_one"):
+            times = []
+            for k in range(args.warmup + args.steps):
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                if mode == "batched":
+                    res = api.plm_solve_batch(ctx, msas, gtol=args.gtol)
+                else:
+                    res = [api.plm_solve(ctx, m, gtol=args.gtol) for m in msas]
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if k >= args.warmup:
+                    times.append(e0.elapsed_time(e1) / 1000.0)
+            out[mode] = {"s": statistics.mean(times),
+                         "sites_not_converged": sum(r[2]["n_noise"] + r[2]["n_failed"] for r in res)}
+    print(json.dumps({"workload": "batch: 64 synthetic families, N~U{50..300}, B log-uniform [500,20000]",
+                      "families": len(fams), "sum_N": sum(f.N for f in fams),
+                      "sum_BN": sum(f.B * f.N for f in fams), "results": out,
+                      "batched_speedup": out["one_by_one"]["s"] / out["batched"]["s"]}), flush=True)
+
+
+def run_scale(args):
+    """N=500, B=50000: evaluations per second of both precisions."""
+    import torch
+    from paper_1401_4832_gb300 import api, synth
+    fam = synth.scale_family()
+    S = torch.from_numpy(fam.msa).cuda()
+    ctx = api.Context(0)
+    m, w, beff = api.msa_reweight(ctx, S)
+    N = fam.N
+    h = torch.zeros((N, 21), device="cuda")
+    J = torch.zeros((N, 21, N, 21), device="cuda")
+    out = {}
+    for prec in ("split_bf16", "fp32"):
+        for _ in range(2):
+            api.plm_site_objective_grad(ctx, S, w, beff, h, J, prec=prec)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            api.plm_site_objective_grad(ctx, S, w, beff, h, J, prec=prec)
+        torch.cuda.synchronize()
+        out[prec] = {"s_per_eval": (time.perf_counter() - t0) / args.steps}
+    print(json.dumps({"workload": "scale: N=500 B=50000 q=21 (750 chain contacts, 20% gaps)",
+                      "results": out}), flush=True)
+
+
 def main():
     args = parse_args()
+    if args.workload == "batch":
+        return run_batch(args)
+    if args.workload == "scale":
+        return run_scale(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

@@ -73,8 +73,12 @@ typedef struct {
     int max_iter;      /* iteration cap per site */
     int max_ls;        /* trial steps per line search before a site fails */
     plm_precision prec;
-    int use_graph;     /* 1: capture the per-iteration launches in a CUDA graph */
-    int reserved[7];
+    int use_graph;     /* 1: replay the per-iteration launches from CUDA graphs
+                          (needs a non-legacy stream) */
+    int autotune;      /* 1: time the candidate tensor-core tile shapes once per
+                          problem shape (cached for the process) and use the
+                          fastest; 0: fixed shapes */
+    int reserved[6];
 } plm_opts;
 
 typedef struct {
@@ -93,7 +97,7 @@ typedef struct {
 
 /* Fills opts with the paper's recommended inputs (x = 0.8, lambda_h =
  * lambda_J = 0.01, Sec. 3.5) and gtol = 1e-4, m = 5, max_iter = 1000,
- * max_ls = 20, PLM_SPLIT_BF16, use_graph = 1. */
+ * max_ls = 20, PLM_SPLIT_BF16, use_graph = 1, autotune = 1. */
 void plm_default_opts(plm_opts *opts);
 
 /* Creates a context on CUDA device `device` that orders its work on

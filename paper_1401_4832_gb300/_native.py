@@ -33,7 +33,8 @@ class plm_opts(ctypes.Structure):
                 ("lambda_J", ctypes.c_double), ("gtol", ctypes.c_double),
                 ("lbfgs_m", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("max_ls", ctypes.c_int), ("prec", ctypes.c_int),
-                ("use_graph", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+                ("use_graph", ctypes.c_int), ("autotune", ctypes.c_int),
+                ("reserved", ctypes.c_int * 6)]
 
 
 class plm_report(ctypes.Structure):

@@ -34,8 +34,15 @@ constexpr size_t LG_SMEM = (size_t)LG_IC * Q * LG_STRIDE * sizeof(float) +
 
 __global__ void __launch_bounds__(256)
 k_logits_gather(const int8_t *__restrict__ msa, const float *__restrict__ theta,
-                Dims d, float *__restrict__ L)
+                Dims d, float *__restrict__ L, const uint8_t *__restrict__ active)
 {
+    if (active) {  // skip row tiles whose sites need no evaluation
+        bool any = false;
+        const int rs0 = blockIdx.x * LG_ROWS;
+        for (int r = rs0 / QP; r <= (rs0 + LG_ROWS - 1) / QP && r < d.N; ++r)
+            any |= active[r] != 0;
+        if (!any) return;
+    }
     extern __shared__ float smem[];
     float *ths = smem;                                           // [IC*Q][129]
     int8_t *ss = (int8_t *)(smem + LG_IC * Q * LG_STRIDE);       // [BT][IC]
@@ -103,15 +110,17 @@ constexpr int SM_WARPS = 8;
 __global__ void __launch_bounds__(256)
 k_softmax_resid(const int8_t *__restrict__ msa, const float *__restrict__ w,
                 double beff, const float *__restrict__ L, Dims d,
-                double *__restrict__ partial, float *__restrict__ D)
+                double *__restrict__ partial, float *__restrict__ D,
+                const uint8_t *__restrict__ active)
 {
     __shared__ double red[SM_WARPS][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int r = blockIdx.x * 32 + lane;
+    const bool live = r < d.N && (!active || active[r]);
     const int nslices = gridDim.y * SM_WARPS;
     const int slice = blockIdx.y * SM_WARPS + warp;
     double obj = 0.0;
-    if (r < d.N) {
+    if (live) {
         for (int b = slice; b < d.B; b += nslices) {
             const float *lr = L + (size_t)b * d.R + (size_t)r * QP;
             float l[Q];
@@ -177,8 +186,15 @@ constexpr int GG_BT = 64;    // sequences per staged tile
 __global__ void __launch_bounds__(256)
 k_grad_gather(const int8_t *__restrict__ msa, const float *__restrict__ D,
               const float *__restrict__ theta, Dims d, double lambda_h,
-              double lambda_Jp, float *__restrict__ G)
+              double lambda_Jp, float *__restrict__ G, const uint8_t *__restrict__ active)
 {
+    if (active) {
+        bool any = false;
+        const int rs0 = blockIdx.x * GG_ROWS;
+        for (int r = rs0 / QP; r <= (rs0 + GG_ROWS - 1) / QP && r < d.N; ++r)
+            any |= active[r] != 0;
+        if (!any) return;
+    }
     __shared__ float ds[GG_BT][GG_ROWS];
     __shared__ int8_t ss[GG_BT][GG_IC];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -257,7 +273,8 @@ k_grad_gather(const int8_t *__restrict__ msa, const float *__restrict__ D,
 }  // namespace
 
 cudaError_t launch_logits_gather(const int8_t *msa, const float *theta,
-                                 const Dims &d, float *L, cudaStream_t st)
+                                 const Dims &d, float *L, const uint8_t *active,
+                                 cudaStream_t st)
 {
     static bool attr_set = false;
     if (!attr_set) {
@@ -267,7 +284,7 @@ cudaError_t launch_logits_gather(const int8_t *msa, const float *theta,
         attr_set = true;
     }
     dim3 grid((d.R + LG_ROWS - 1) / LG_ROWS, (d.B + LG_BT - 1) / LG_BT);
-    k_logits_gather<<<grid, 256, LG_SMEM, st>>>(msa, theta, d, L);
+    k_logits_gather<<<grid, 256, LG_SMEM, st>>>(msa, theta, d, L, active);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -285,10 +302,11 @@ int softmax_slices(const Dims &d)
 
 cudaError_t launch_softmax_resid(const int8_t *msa, const float *w,
                                  double beff, const float *L, const Dims &d,
-                                 double *partial, float *D, cudaStream_t st)
+                                 double *partial, float *D, const uint8_t *active,
+                                 cudaStream_t st)
 {
     dim3 grid((d.N + 31) / 32, softmax_slices(d));
-    k_softmax_resid<<<grid, 32 * SM_WARPS, 0, st>>>(msa, w, beff, L, d, partial, D);
+    k_softmax_resid<<<grid, 32 * SM_WARPS, 0, st>>>(msa, w, beff, L, d, partial, D, active);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -306,10 +324,10 @@ cudaError_t launch_finish_objective(const double *partial, int slices,
 cudaError_t launch_grad_gather(const int8_t *msa, const float *D,
                                const float *theta, const Dims &d,
                                double lambda_h, double lambda_Jp, float *G,
-                               cudaStream_t st)
+                               const uint8_t *active, cudaStream_t st)
 {
     dim3 grid((d.R + GG_ROWS - 1) / GG_ROWS, (d.N + GG_IC - 1) / GG_IC);
-    k_grad_gather<<<grid, 256, 0, st>>>(msa, D, theta, d, lambda_h, lambda_Jp, G);
+    k_grad_gather<<<grid, 256, 0, st>>>(msa, D, theta, d, lambda_h, lambda_Jp, G, active);
     count_launches(1);
     return cudaGetLastError();
 }

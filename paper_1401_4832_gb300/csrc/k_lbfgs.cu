@@ -597,6 +597,21 @@ __global__ void k_round_inc(int *round_ptr, int *counters)
 }
 }  // namespace
 
+namespace {
+__global__ void k_active(const SiteState *ss, int nsites, uint8_t *active)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < nsites) active[r] = ss[r].status == SITE_SEARCHING ? 1 : 0;
+}
+}  // namespace
+
+cudaError_t launch_active_flags(const SiteState *ss, int nsites, uint8_t *active, cudaStream_t st)
+{
+    k_active<<<(nsites + 255) / 256, 256, 0, st>>>(ss, nsites, active);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_round_begin(int *round_ptr, int *counters, cudaStream_t st)
 {
     k_round_inc<<<1, 1, 0, st>>>(round_ptr, counters);

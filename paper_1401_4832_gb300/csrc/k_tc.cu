@@ -40,18 +40,13 @@ namespace {
 
 constexpr int TC_M = 128;
 constexpr int TC_BK = 64;                  // K per stage: 64 bf16 = 128 bytes
-constexpr int STAGES = 3;
-constexpr int LG_SITES = 8;                // sites per logits tile
-constexpr int LG_N = LG_SITES * QP;        // 192 accumulator columns
-constexpr int GR_N = 256;                  // gradient tile columns
+constexpr int MAX_STAGES = 4;
+constexpr int MAX_LG_SITES = 10;           // sites per logits tile: 2..10, even
 constexpr int TMEM_COLS = 256;
 constexpr int LG_A_BYTES = TC_M * TC_BK * 2;          // 16 KB
-constexpr int LG_B_BYTES = LG_N * TC_BK * 2;          // 24 KB
-constexpr int LG_STAGE = LG_A_BYTES + 2 * LG_B_BYTES;  // 64 KB
 constexpr int GR_A_BYTES = TC_M * TC_BK * 2;          // 16 KB
-constexpr int GR_B_BYTES = GR_N * TC_BK * 2;          // 32 KB
-constexpr int GR_STAGE = 2 * GR_A_BYTES + GR_B_BYTES;  // 64 KB
-constexpr int TC_SMEM = STAGES * 65536 + 1024;         // + alignment slack
+constexpr int SMEM_BUDGET = 224 * 1024;  // pipeline bytes; + 1 KB alignment slack and the static
+                                         // shared memory stay under the 227 KB per block
 constexpr long long WAIT_CYCLES = 4000000000LL;        // ~2 s at 2 GHz
 
 enum { ERR_TIMEOUT_TMA = 1 << 4, ERR_TIMEOUT_MMA = 1 << 5, ERR_TIMEOUT_PROD = 1 << 6,
@@ -249,11 +244,13 @@ __device__ __forceinline__ uint32_t swz(int row, int chunk16)
 // TMA map per family and operand (passed by value, read from param space).
 struct LogitsParams {
     TcBatch b;
+    int sites, ncols, stages, stage_bytes;  // tile: `sites` sites = ncols accumulator columns
     CUtensorMap hi[MAX_FAM], lo[MAX_FAM];
 };
 
 struct GradParams {
     TcBatch b;
+    int ncols, stages, stage_bytes;  // tile: 128 rows x ncols columns
     CUtensorMap dhi[MAX_FAM], dlo[MAX_FAM];
 };
 
@@ -289,23 +286,30 @@ k_tc_logits(const __grid_constant__ LogitsParams P, int *__restrict__ err)
     d.K = F.N * Q + 1;
     const int local = blockIdx.x - F.tile0_logits;
     const int nbt = BP / TC_M;
+    const int LGS = P.sites, LGN = P.ncols, NST = P.stages, LGSTAGE = P.stage_bytes;
+    const int LGB = LGN * TC_BK * 2;
     extern __shared__ uint8_t dsmem[];
     uint8_t *smem = align1024(dsmem);
-    __shared__ __align__(8) uint64_t full_b[STAGES], full_a[STAGES], empty_[STAGES], acc_full;
+    __shared__ __align__(8) uint64_t full_b[MAX_STAGES], full_a[MAX_STAGES], empty_[MAX_STAGES], acc_full;
     __shared__ uint32_t tmem_sh;
     __shared__ int abort_sh;
-    __shared__ double red[4][LG_SITES];
+    __shared__ double red[4][MAX_LG_SITES];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tb = local % nbt, tr = local / nbt;
     const int b0 = tb * TC_M;
-    const int r0 = tr * LG_SITES;
+    const int r0 = tr * LGS;
+    if (F.active) {  // skip the tile when none of its sites needs this evaluation
+        bool any = false;
+        for (int j = 0; j < LGS && r0 + j < F.N; ++j) any |= F.active[r0 + j] != 0;
+        if (!any) return;
+    }
     const int row0 = r0 * QP;
     const int NK = d.KP / TC_BK;
     const int NQ = d.N * Q;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) {
+        for (int s = 0; s < NST; ++s) {
             mbar_init(&full_b[s], 1);
             mbar_init(&full_a[s], 128);
             mbar_init(&empty_[s], 1);
@@ -327,31 +331,31 @@ k_tc_logits(const __grid_constant__ LogitsParams P, int *__restrict__ err)
         if (lane == 0) {
             int issued = 0;
             for (int kc = 0; kc < NK; ++kc) {
-                const int s = kc % STAGES, n = kc / STAGES;
+                const int s = kc % NST, n = kc / NST;
                 if (n > 0 && !mbar_wait(&empty_[s], (n - 1) & 1, &abort_sh, err, ERR_TIMEOUT_TMA))
                     break;
-                uint8_t *st = smem + s * LG_STAGE;
-                mbar_expect_tx(&full_b[s], 2 * LG_B_BYTES);
+                uint8_t *st = smem + s * LGSTAGE;
+                mbar_expect_tx(&full_b[s], 2 * LGB);
                 tma_load_2d(st + LG_A_BYTES, &tm_hi, &full_b[s], kc * TC_BK, row0);
-                tma_load_2d(st + LG_A_BYTES + LG_B_BYTES, &tm_lo, &full_b[s], kc * TC_BK, row0);
+                tma_load_2d(st + LG_A_BYTES + LGB, &tm_lo, &full_b[s], kc * TC_BK, row0);
                 issued = kc + 1;
             }
             // let the copies still in flight land before the CTA can exit
-            for (int kc = issued - STAGES < 0 ? 0 : issued - STAGES; kc < issued; ++kc)
-                mbar_drain(&full_b[kc % STAGES], (kc / STAGES) & 1);
+            for (int kc = issued - NST < 0 ? 0 : issued - NST; kc < issued; ++kc)
+                mbar_drain(&full_b[kc % NST], (kc / NST) & 1);
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            const uint32_t idesc = idesc_bf16(TC_M, LG_N);
+            const uint32_t idesc = idesc_bf16(TC_M, LGN);
             for (int kc = 0; kc < NK; ++kc) {
-                const int s = kc % STAGES, n = kc / STAGES;
+                const int s = kc % NST, n = kc / NST;
                 if (!mbar_wait(&full_b[s], n & 1, &abort_sh, err, ERR_TIMEOUT_MMA)) break;
                 if (!mbar_wait(&full_a[s], n & 1, &abort_sh, err, ERR_TIMEOUT_MMA)) break;
                 tc_fence_after();
-                uint8_t *st = smem + s * LG_STAGE;
+                uint8_t *st = smem + s * LGSTAGE;
                 const uint32_t a = smem_u32(st);
                 const uint32_t bh = smem_u32(st + LG_A_BYTES);
-                const uint32_t bl = smem_u32(st + LG_A_BYTES + LG_B_BYTES);
+                const uint32_t bl = smem_u32(st + LG_A_BYTES + LGB);
 #pragma unroll
                 for (int k = 0; k < TC_BK / 16; ++k)
                     mma_bf16(tmem, sdesc(a + 32 * k), sdesc(bh + 32 * k), idesc,
@@ -382,11 +386,11 @@ k_tc_logits(const __grid_constant__ LogitsParams P, int *__restrict__ err)
         int cur5[5], nxt5[5];
         fetch(0, cur5);
         for (int kc = 0; kc < NK; ++kc) {
-            const int s = kc % STAGES, n = kc / STAGES;
+            const int s = kc % NST, n = kc / NST;
             fetch(kc + 1 < NK ? kc + 1 : kc, nxt5);
             if (n > 0 && !mbar_wait(&empty_[s], (n - 1) & 1, &abort_sh, err, ERR_TIMEOUT_PROD))
                 break;
-            uint8_t *rowp = smem + s * LG_STAGE + p * 128;
+            uint8_t *rowp = smem + s * LGSTAGE + p * 128;
             const uint4 z = make_uint4(0, 0, 0, 0);
             // rotate the chunk order by row so a warp's stores spread over the banks
 #pragma unroll
@@ -421,13 +425,13 @@ k_tc_logits(const __grid_constant__ LogitsParams P, int *__restrict__ err)
         const bool ev = eb < d.B;
         const bool ok = mbar_wait(&acc_full, 0, &abort_sh, err, ERR_TIMEOUT_EPI);
         tc_fence_after();
-        __nv_bfloat16 *st_hi = (__nv_bfloat16 *)smem;            // [LG_N][128]
-        __nv_bfloat16 *st_lo = st_hi + LG_N * TC_M;              // [LG_N][128]
+        __nv_bfloat16 *st_hi = (__nv_bfloat16 *)smem;            // [LGN][128]
+        __nv_bfloat16 *st_lo = st_hi + LGN * TC_M;              // [LGN][128]
         const float wb = ev ? w[eb] : 0.0f;
         const float scale = (float)((double)wb * inv_beff);
         const uint32_t tl = tmem + ((uint32_t)(q4 * 32) << 16);
 #pragma unroll 1
-        for (int jp = 0; jp < LG_SITES / 2; ++jp) {
+        for (int jp = 0; jp < LGS / 2; ++jp) {
             float v[48];
             tmem_ld16(tl + jp * 48, v);
             tmem_ld16(tl + jp * 48 + 16, v + 16);
@@ -468,13 +472,13 @@ k_tc_logits(const __grid_constant__ LogitsParams P, int *__restrict__ err)
         }
         epi_bar();
         const int t = threadIdx.x - 64;
-        if (t < LG_SITES && r0 + t < d.N)
+        if (t < LGS && r0 + t < d.N)
             partial[(size_t)tb * d.N + r0 + t] = ((red[0][t] + red[1][t]) + red[2][t]) + red[3][t];
         // copy-out: row (r,s) of the tile = 128 sequences = 256 bytes = 16 x 16 B
-        const int nrows = min(LG_N, d.R - row0);
-        for (int e = t; e < 2 * LG_N * 16; e += 128) {
-            const int half = e / (LG_N * 16);
-            const int rem = e % (LG_N * 16);
+        const int nrows = min(LGN, d.R - row0);
+        for (int e = t; e < 2 * LGN * 16; e += 128) {
+            const int half = e / (LGN * 16);
+            const int rem = e % (LGN * 16);
             const int row = rem / 16, c16 = rem % 16;
             if (row >= nrows) continue;
             const __nv_bfloat16 *src = (half ? st_lo : st_hi) + row * TC_M + c16 * 8;
@@ -512,21 +516,28 @@ k_tc_grad(const __grid_constant__ GradParams P, float two_lh, float two_lj, int 
     d.R = F.R;
     d.K = F.N * Q + 1;
     const int local = blockIdx.x - F.tile0_grad;
-    const int nct = (d.KP + GR_N - 1) / GR_N;
+    const int GRN = P.ncols, NST = P.stages, GRSTAGE = P.stage_bytes;
+    const int nct = (d.KP + GRN - 1) / GRN;
     extern __shared__ uint8_t dsmem[];
     uint8_t *smem = align1024(dsmem);
-    __shared__ __align__(8) uint64_t full_b[STAGES], full_a[STAGES], empty_[STAGES], acc_full;
+    __shared__ __align__(8) uint64_t full_b[MAX_STAGES], full_a[MAX_STAGES], empty_[MAX_STAGES], acc_full;
     __shared__ uint32_t tmem_sh;
     __shared__ int abort_sh;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int c0 = (local % nct) * GR_N;
+    const int c0 = (local % nct) * GRN;
     const int rs0 = (local / nct) * TC_M;
+    if (F.active) {
+        bool any = false;
+        for (int r = rs0 / QP; r <= (rs0 + TC_M - 1) / QP && r < F.N; ++r)
+            any |= F.active[r] != 0;
+        if (!any) return;
+    }
     const int NK = BP / TC_BK;
     const int NQ = d.N * Q;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) {
+        for (int s = 0; s < NST; ++s) {
             mbar_init(&full_b[s], 1);
             mbar_init(&full_a[s], 128);
             mbar_init(&empty_[s], 1);
@@ -548,27 +559,27 @@ k_tc_grad(const __grid_constant__ GradParams P, float two_lh, float two_lj, int 
         if (lane == 0) {
             int issued = 0;
             for (int kc = 0; kc < NK; ++kc) {
-                const int s = kc % STAGES, n = kc / STAGES;
+                const int s = kc % NST, n = kc / NST;
                 if (n > 0 && !mbar_wait(&empty_[s], (n - 1) & 1, &abort_sh, err, ERR_TIMEOUT_TMA))
                     break;
-                uint8_t *st = smem + s * GR_STAGE;
+                uint8_t *st = smem + s * GRSTAGE;
                 mbar_expect_tx(&full_b[s], 2 * GR_A_BYTES);
                 tma_load_2d(st, &tm_dhi, &full_b[s], kc * TC_BK, rs0);
                 tma_load_2d(st + GR_A_BYTES, &tm_dlo, &full_b[s], kc * TC_BK, rs0);
                 issued = kc + 1;
             }
-            for (int kc = issued - STAGES < 0 ? 0 : issued - STAGES; kc < issued; ++kc)
-                mbar_drain(&full_b[kc % STAGES], (kc / STAGES) & 1);
+            for (int kc = issued - NST < 0 ? 0 : issued - NST; kc < issued; ++kc)
+                mbar_drain(&full_b[kc % NST], (kc / NST) & 1);
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            const uint32_t idesc = idesc_bf16(TC_M, GR_N);
+            const uint32_t idesc = idesc_bf16(TC_M, GRN);
             for (int kc = 0; kc < NK; ++kc) {
-                const int s = kc % STAGES, n = kc / STAGES;
+                const int s = kc % NST, n = kc / NST;
                 if (!mbar_wait(&full_b[s], n & 1, &abort_sh, err, ERR_TIMEOUT_MMA)) break;
                 if (!mbar_wait(&full_a[s], n & 1, &abort_sh, err, ERR_TIMEOUT_MMA)) break;
                 tc_fence_after();
-                uint8_t *st = smem + s * GR_STAGE;
+                uint8_t *st = smem + s * GRSTAGE;
                 const uint32_t ah = smem_u32(st);
                 const uint32_t al = smem_u32(st + GR_A_BYTES);
                 const uint32_t bx = smem_u32(st + 2 * GR_A_BYTES);
@@ -612,7 +623,7 @@ k_tc_grad(const __grid_constant__ GradParams P, float two_lh, float two_lj, int 
             for (int q = 0; q < 4; ++q)
                 cur[u][q] = __ldg((const uint4 *)(msaT + (size_t)src_i[u] * BP) + q);
         for (int kc = 0; kc < NK; ++kc) {
-            const int s = kc % STAGES, n = kc / STAGES;
+            const int s = kc % NST, n = kc / NST;
             const int kn = kc + 1 < NK ? kc + 1 : kc;
 #pragma unroll
             for (int u = 0; u < 2; ++u)
@@ -622,10 +633,11 @@ k_tc_grad(const __grid_constant__ GradParams P, float two_lh, float two_lj, int 
                         __ldg((const uint4 *)(msaT + (size_t)src_i[u] * BP + kn * TC_BK) + q);
             if (n > 0 && !mbar_wait(&empty_[s], (n - 1) & 1, &abort_sh, err, ERR_TIMEOUT_PROD))
                 break;
-            uint8_t *bt = smem + s * GR_STAGE + 2 * GR_A_BYTES;
+            uint8_t *bt = smem + s * GRSTAGE + 2 * GR_A_BYTES;
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
                 const int row = p + 128 * u;
+                if (row >= GRN) continue;
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {  // 16 sequences per word group
                     const uint4 x = cur[u][q];
@@ -656,11 +668,11 @@ k_tc_grad(const __grid_constant__ GradParams P, float two_lh, float two_lj, int 
         const int trow = q4 * 32 + lane;
         const bool ok = mbar_wait(&acc_full, 0, &abort_sh, err, ERR_TIMEOUT_EPI);
         tc_fence_after();
-        constexpr int GS = GR_N + 4;
+        const int GS = GRN + 4;
         float *acc_s = (float *)smem;  // [128][GS]
         const uint32_t tl = tmem + ((uint32_t)(q4 * 32) << 16);
 #pragma unroll 1
-        for (int cc = 0; cc < GR_N / 16; ++cc) {
+        for (int cc = 0; cc < GRN / 16; ++cc) {
             float v[16];
             tmem_ld16(tl + cc * 16, v);
             tmem_wait_ld();
@@ -672,15 +684,15 @@ k_tc_grad(const __grid_constant__ GradParams P, float two_lh, float two_lj, int 
         epi_bar();
         const int t = threadIdx.x - 64;
         constexpr int UNR = 8;
-        for (int e0 = t; e0 < TC_M * (GR_N / 4); e0 += 128 * UNR) {
+        for (int e0 = t; e0 < TC_M * (GRN / 4); e0 += 128 * UNR) {
             float4 th[UNR];
             bool live[UNR];
 #pragma unroll
             for (int k = 0; k < UNR; ++k) {  // issue all loads first
                 const int e = e0 + 128 * k;
-                const int rr = e / (GR_N / 4), c4 = e % (GR_N / 4);
+                const int rr = e / (GRN / 4), c4 = e % (GRN / 4);
                 const int row = rs0 + rr, cb = c0 + 4 * c4;
-                live[k] = ok && e < TC_M * (GR_N / 4) && row < d.R && cb < d.KP;
+                live[k] = ok && e < TC_M * (GRN / 4) && row < d.R && cb < d.KP;
                 th[k] = live[k] ? *(const float4 *)(theta + (size_t)row * d.KP + cb)
                                 : make_float4(0.f, 0.f, 0.f, 0.f);
             }
@@ -688,7 +700,7 @@ k_tc_grad(const __grid_constant__ GradParams P, float two_lh, float two_lj, int 
             for (int k = 0; k < UNR; ++k) {
                 if (!live[k]) continue;
                 const int e = e0 + 128 * k;
-                const int rr = e / (GR_N / 4), c4 = e % (GR_N / 4);
+                const int rr = e / (GRN / 4), c4 = e % (GRN / 4);
                 const int row = rs0 + rr, cb = c0 + 4 * c4;
                 const int r = row / QP, sstate = row % QP;
                 const float4 a = *(const float4 *)(acc_s + rr * GS + 4 * c4);
@@ -837,53 +849,87 @@ cudaError_t launch_tc_prepare(TcBatch &b, void *const *scratch, cudaStream_t st)
         p += align256(nbt * F.N * sizeof(double));
         int8_t *msaT = (int8_t *)p;
         F.msaT = msaT;
-        F.tile0_logits = tl;
-        F.tile0_grad = tg;
-        tl += (int)nbt * ((F.N + LG_SITES - 1) / LG_SITES);
-        tg += ((F.KP + GR_N - 1) / GR_N) * ((F.R + TC_M - 1) / TC_M);
         const size_t nT = (size_t)(F.N + 1) * F.BP;
         k_msa_transpose<<<(unsigned)((nT + 255) / 256), 256, 0, st>>>(F.msa, F.B, F.N, F.BP, msaT);
         count_launches(1);
     }
-    b.ntiles_logits = tl;
-    b.ntiles_grad = tg;
+    (void)tl;
+    (void)tg;
     return cudaGetLastError();
 }
 
-cudaError_t launch_tc_eval(void *prof, const TcBatch &b, double lambda_h, double lambda_Jp,
-                           int *err, cudaStream_t st)
+int tc_stages(int stage_bytes)
+{
+    int n = SMEM_BUDGET / stage_bytes;
+    return n > MAX_STAGES ? MAX_STAGES : n;
+}
+
+bool tc_config_valid(const TcConfig &c)
+{
+    return c.lg_sites >= 2 && c.lg_sites <= MAX_LG_SITES && c.lg_sites % 2 == 0 &&
+           c.gr_ncols >= 32 && c.gr_ncols <= 256 && c.gr_ncols % 32 == 0;
+}
+
+cudaError_t launch_tc_eval(void *prof, const TcBatch &b_in, const TcConfig &cfg, double lambda_h,
+                           double lambda_Jp, int *err, cudaStream_t st, int which)
 {
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k_tc_logits,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             SMEM_BUDGET + 1024);
         if (e) return e;
-        e = cudaFuncSetAttribute(k_tc_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+        e = cudaFuncSetAttribute(k_tc_grad, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 SMEM_BUDGET + 1024);
         if (e) return e;
         attr = true;
     }
-    if (b.nfam < 1 || b.nfam > MAX_FAM) return cudaErrorInvalidValue;
+    if (b_in.nfam < 1 || b_in.nfam > MAX_FAM || !tc_config_valid(cfg))
+        return cudaErrorInvalidValue;
     static LogitsParams lp;  // large parameter blocks: built on the host, passed by value
     static GradParams gp;
-    lp.b = b;
-    gp.b = b;
-    for (int i = 0; i < b.nfam; ++i) {
-        const FamDesc &F = b.f[i];
-        if (!make_map(&lp.hi[i], F.th_hi, F.KP, F.R, TC_BK, LG_N) ||
-            !make_map(&lp.lo[i], F.th_lo, F.KP, F.R, TC_BK, LG_N) ||
+    lp.b = b_in;
+    const int lg_ncols = cfg.lg_sites * QP;
+    int tl = 0, tg = 0;
+    for (int i = 0; i < lp.b.nfam; ++i) {
+        FamDesc &F = lp.b.f[i];
+        F.tile0_logits = tl;
+        F.tile0_grad = tg;
+        tl += (F.BP / TC_M) * ((F.N + cfg.lg_sites - 1) / cfg.lg_sites);
+        tg += ((F.KP + cfg.gr_ncols - 1) / cfg.gr_ncols) * ((F.R + TC_M - 1) / TC_M);
+    }
+    lp.b.ntiles_logits = tl;
+    lp.b.ntiles_grad = tg;
+    gp.b = lp.b;
+    lp.sites = cfg.lg_sites;
+    lp.ncols = lg_ncols;
+    lp.stage_bytes = LG_A_BYTES + 2 * lg_ncols * TC_BK * 2;
+    lp.stages = tc_stages(lp.stage_bytes);
+    gp.ncols = cfg.gr_ncols;
+    gp.stage_bytes = 2 * GR_A_BYTES + cfg.gr_ncols * TC_BK * 2;
+    gp.stages = tc_stages(gp.stage_bytes);
+    for (int i = 0; i < lp.b.nfam; ++i) {
+        const FamDesc &F = lp.b.f[i];
+        if (!make_map(&lp.hi[i], F.th_hi, F.KP, F.R, TC_BK, lg_ncols) ||
+            !make_map(&lp.lo[i], F.th_lo, F.KP, F.R, TC_BK, lg_ncols) ||
             !make_map(&gp.dhi[i], F.dt_hi, F.BP, F.R, TC_BK, TC_M) ||
             !make_map(&gp.dlo[i], F.dt_lo, F.BP, F.R, TC_BK, TC_M))
             return cudaErrorInvalidValue;
     }
-    void *t0 = prof ? prof_start(prof) : nullptr;
-    k_tc_logits<<<b.ntiles_logits, 192, TC_SMEM, st>>>(lp, err);
-    if (prof) prof_stop(prof, "tc_logits", t0);
-    k_tc_finish<<<b.nfam, 128, 0, st>>>(b);
-    void *t1 = prof ? prof_start(prof) : nullptr;
-    k_tc_grad<<<b.ntiles_grad, 192, TC_SMEM, st>>>(gp, (float)(2.0 * lambda_h),
-                                                   (float)(2.0 * lambda_Jp), err);
-    if (prof) prof_stop(prof, "tc_grad", t1);
-    count_launches(3);
+    if (which & 1) {
+        void *t0 = prof ? prof_start(prof) : nullptr;
+        k_tc_logits<<<tl, 192, lp.stages * lp.stage_bytes + 1024, st>>>(lp, err);
+        if (prof) prof_stop(prof, "tc_logits", t0);
+        k_tc_finish<<<lp.b.nfam, 128, 0, st>>>(lp.b);
+        count_launches(2);
+    }
+    if (which & 2) {
+        void *t1 = prof ? prof_start(prof) : nullptr;
+        k_tc_grad<<<tg, 192, gp.stages * gp.stage_bytes + 1024, st>>>(
+            gp, (float)(2.0 * lambda_h), (float)(2.0 * lambda_Jp), err);
+        if (prof) prof_stop(prof, "tc_grad", t1);
+        count_launches(1);
+    }
     return cudaGetLastError();
 }
 

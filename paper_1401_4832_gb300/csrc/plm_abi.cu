@@ -7,8 +7,10 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -265,6 +267,9 @@ struct Problem {
     LbLayout L{};
     std::vector<TcBatch> tcb;  // the families in launches of at most MAX_FAM
     bool tc_ready = false;
+    TcConfig tc_cfg;
+    bool tc_tuned = false;
+    bool autotune = true;
 };
 
 void layout_problem(Problem &P)
@@ -365,12 +370,96 @@ plm_status prepare_tc(plm_ctx *ctx, Problem &P, const float *w)
     return PLM_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Autotuner of the tensor-core tile shapes.  For a problem signature (the
+// (N, B) of its families) every candidate shape of the logits kernel (sites
+// per tile) and of the gradient kernel (columns per tile) is timed with CUDA
+// events on the context's stream -- one warm-up launch, then the best of two
+// -- and the fastest of each is kept.  The choice is cached per signature for
+// the life of the process.  Wave quantisation on 152 SMs is what mostly
+// decides it (e.g. 230 vs 276 gradient tiles).
+std::mutex g_tune_mutex;
+std::map<std::string, TcConfig> g_tune_cache;
+
+std::string problem_signature(const Problem &P)
+{
+    std::string sig;
+    char buf[48];
+    for (auto &F : P.fam) {
+        snprintf(buf, sizeof buf, "%d:%d;", F.d.N, F.d.B);
+        sig += buf;
+    }
+    return sig;
+}
+
+plm_status autotune_tc(plm_ctx *ctx, Problem &P, int *tc_err)
+{
+    const std::string sig = problem_signature(P);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto it = g_tune_cache.find(sig);
+        if (it != g_tune_cache.end()) {
+            P.tc_cfg = it->second;
+            P.tc_tuned = true;
+            return PLM_OK;
+        }
+    }
+    cudaStream_t st = ctx->stream;
+    cudaEvent_t e0 = take_event(ctx), e1 = take_event(ctx);
+    auto time_it = [&](const TcConfig &c, int which, float *best) -> plm_status {
+        *best = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+            CK(cudaEventRecord(e0, st));
+            for (auto &b : P.tcb) CK(launch_tc_eval(nullptr, b, c, 0.0, 0.0, tc_err, st, which));
+            CK(cudaEventRecord(e1, st));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.0f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (rep > 0 && ms < *best) *best = ms;
+        }
+        return PLM_OK;
+    };
+    TcConfig best;
+    float tbest = 1e30f;
+    for (int sites : {4, 6, 8, 10}) {
+        TcConfig c = best;
+        c.lg_sites = sites;
+        float t;
+        plm_status s = time_it(c, 1, &t);
+        if (s) return s;
+        if (t < tbest) {
+            tbest = t;
+            best.lg_sites = sites;
+        }
+    }
+    tbest = 1e30f;
+    for (int cols : {128, 160, 192, 224, 256}) {
+        TcConfig c = best;
+        c.gr_ncols = cols;
+        float t;
+        plm_status s = time_it(c, 2, &t);
+        if (s) return s;
+        if (t < tbest) {
+            tbest = t;
+            best.gr_ncols = cols;
+        }
+    }
+    ctx->event_pool.push_back(e0);
+    ctx->event_pool.push_back(e1);
+    P.tc_cfg = best;
+    P.tc_tuned = true;
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune_cache[sig] = best;
+    return PLM_OK;
+}
+
 // One objective+gradient evaluation of every site of the problem at theta
 // (arena).  f_data[site] = -(1/B_eff) sum_b w_b log P (no penalty); G (arena)
 // includes 2 lambda theta.
 plm_status evaluate(plm_ctx *ctx, plm_precision prec, Problem &P, const float *w,
                     const float *theta, const __nv_bfloat16 *hi, const __nv_bfloat16 *lo,
-                    double lambda_h, double lambda_Jp, double *f_data, float *G, int *tc_err)
+                    double lambda_h, double lambda_Jp, double *f_data, float *G, int *tc_err,
+                    const uint8_t *active = nullptr)
 {
     cudaStream_t st = ctx->stream;
     if (prec == PLM_FP32_EXACT) {
@@ -389,19 +478,20 @@ plm_status evaluate(plm_ctx *ctx, plm_precision prec, Problem &P, const float *w
             const float *th = theta + F.off;
             {
                 ProfScope ps(ctx, "logits_gather");
-                CK(launch_logits_gather(F.msa, th, d, (float *)L, st));
+                CK(launch_logits_gather(F.msa, th, d, (float *)L,
+                                        active ? active + F.site0 : nullptr, st));
             }
             {
                 ProfScope ps(ctx, "softmax_resid");
                 CK(launch_softmax_resid(F.msa, w + F.woff, F.beff, (float *)L, d, (double *)part,
-                                        (float *)D, st));
+                                        (float *)D, active ? active + F.site0 : nullptr, st));
                 CK(launch_finish_objective((double *)part, slices, d, F.beff, nullptr,
                                            f_data + F.site0, st));
             }
             {
                 ProfScope ps(ctx, "grad_gather");
                 CK(launch_grad_gather(F.msa, (float *)D, th, d, lambda_h, lambda_Jp, G + F.off,
-                                      st));
+                                      active ? active + F.site0 : nullptr, st));
             }
         }
         return PLM_OK;
@@ -423,11 +513,29 @@ plm_status evaluate(plm_ctx *ctx, plm_precision prec, Problem &P, const float *w
                 D.theta = theta + F.off;
                 D.G = G + F.off;
                 D.f_data = f_data + F.site0;
+                D.active = active ? active + F.site0 : nullptr;
             }
-            CK(launch_tc_eval(ctx->prof ? (void *)ctx : nullptr, b, lambda_h, lambda_Jp, tc_err,
-                              st));
             f0 += b.nfam;
         }
+        if (!P.tc_tuned) {
+            // PLMDCA_TC_TILES="sites,cols" forces a tile shape (tests, experiments)
+            const char *force = getenv("PLMDCA_TC_TILES");
+            TcConfig fc;
+            if (force && sscanf(force, "%d,%d", &fc.lg_sites, &fc.gr_ncols) == 2 &&
+                tc_config_valid(fc)) {
+                P.tc_cfg = fc;
+                P.tc_tuned = true;
+            } else if (P.autotune) {
+                plm_status s = autotune_tc(ctx, P, tc_err);
+                if (s) return s;
+            } else {
+                P.tc_cfg = TcConfig();
+                P.tc_tuned = true;
+            }
+        }
+        for (auto &b : P.tcb)
+            CK(launch_tc_eval(ctx->prof ? (void *)ctx : nullptr, b, P.tc_cfg, lambda_h, lambda_Jp,
+                              tc_err, st));
         return PLM_OK;
     }
     return fail(ctx, PLM_ENOTIMPL, "precision mode %d is not built", (int)prec);
@@ -489,6 +597,8 @@ plm_status solve_core(plm_ctx *ctx, Problem &P, const plm_opts &o, std::vector<S
     CK(ws(ctx, "fdata", (size_t)P.nsites * sizeof(double), &fdat));
     CK(ws(ctx, "counters", 16 * sizeof(int), &cnt));
     CK(ws(ctx, "lb_part", (size_t)P.nchunks * LB_PART * sizeof(double), &part));
+    void *active;
+    CK(ws(ctx, "active", (size_t)P.nsites, &active));
     if (o.prec == PLM_SPLIT_BF16) {
         CK(ws(ctx, "theta_hi", P.total * 2, &hi));
         CK(ws(ctx, "theta_lo", P.total * 2, &lo));
@@ -542,9 +652,11 @@ plm_status solve_core(plm_ctx *ctx, Problem &P, const plm_opts &o, std::vector<S
                                   (float *)dir, (float *)theta_t, (__nv_bfloat16 *)hi,
                                   (__nv_bfloat16 *)lo, P.L, p, (double *)part, st));
         }
+        CK(launch_active_flags((const SiteState *)sst, P.nsites, (uint8_t *)active, st));
         plm_status s2 = evaluate(ctx, o.prec, P, (const float *)w, (const float *)theta_t,
                                  (const __nv_bfloat16 *)hi, (const __nv_bfloat16 *)lo, p.lambda_h,
-                                 p.lambda_Jp, (double *)fdat, (float *)g_t, tc_err);
+                                 p.lambda_Jp, (double *)fdat, (float *)g_t, tc_err,
+                                 (const uint8_t *)active);
         if (s2) return s2;
         {
             ProfScope ps(ctx, "lbfgs_linesearch");
@@ -663,6 +775,7 @@ void plm_default_opts(plm_opts *o)
     o->max_ls = 20;
     o->prec = PLM_SPLIT_BF16;
     o->use_graph = 1;
+    o->autotune = 1;
 }
 
 plm_status plm_create(plm_ctx **out, int device, void *cuda_stream)
@@ -920,6 +1033,7 @@ plm_status plm_solve_batch(plm_ctx *ctx, const plm_family *fams, int nfam, int q
         F.msa = (const int8_t *)msa_d;
         F.d = make_dims(B, N);
         P.fam.push_back(F);
+        P.autotune = o.autotune != 0;
         out[f].h = (float *)hs[f].dev;
         out[f].J = (float *)Js[f].dev;
     }

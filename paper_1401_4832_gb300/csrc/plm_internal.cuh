@@ -118,14 +118,18 @@ cudaError_t launch_penalty(const float *theta, const Dims &d, double lambda_h,
                            double lambda_Jp, double *pen, cudaStream_t st);
 
 // ---- FP32 gather path (k_gather.cu) ----
+// `active` (per site, may be NULL = all): row tiles without an active site
+// are skipped (their outputs are left as they were)
 cudaError_t launch_logits_gather(const int8_t *msa, const float *theta,
-                                 const Dims &d, float *L, cudaStream_t st);
+                                 const Dims &d, float *L, const uint8_t *active,
+                                 cudaStream_t st);
 // per-(slice, site) FP64 partial sums of w_b (L[b][r][S_br] - lse); residual
 // D[b][(r,s)] = (w_b / B_eff)(P - Y) in FP32
 int softmax_slices(const Dims &d);
 cudaError_t launch_softmax_resid(const int8_t *msa, const float *w,
                                  double beff, const float *L, const Dims &d,
-                                 double *partial, float *D, cudaStream_t st);
+                                 double *partial, float *D, const uint8_t *active,
+                                 cudaStream_t st);
 // f[r] = -(sum partial)/B_eff + pen[r]  (pen may be NULL)
 cudaError_t launch_finish_objective(const double *partial, int slices,
                                     const Dims &d, double beff,
@@ -134,7 +138,7 @@ cudaError_t launch_finish_objective(const double *partial, int slices,
 cudaError_t launch_grad_gather(const int8_t *msa, const float *D,
                                const float *theta, const Dims &d,
                                double lambda_h, double lambda_Jp, float *G,
-                               cudaStream_t st);
+                               const uint8_t *active, cudaStream_t st);
 
 // ---- L-BFGS (k_lbfgs.cu) ----
 // All vectors of the solver (theta, g, d, S, Y ...) are arenas holding the
@@ -194,6 +198,10 @@ cudaError_t launch_lbfgs_linesearch(SiteState *ss, const double *f_data,
                                     const int *round_ptr, int *counters, cudaStream_t st);
 // start of a line-search round: ++*round_ptr, counters[0] = 0
 cudaError_t launch_round_begin(int *round_ptr, int *counters, cudaStream_t st);
+// active[site] = 1 if the site is in a line search (its trial point needs an
+// evaluation), else 0; the evaluation kernels skip tiles without active sites
+cudaError_t launch_active_flags(const SiteState *ss, int nsites, uint8_t *active,
+                                cudaStream_t st);
 
 // ---- scores (k_scores.cu) ----
 cudaError_t launch_fn(const float *J, int N, int combine, double *fn,
@@ -222,6 +230,7 @@ struct FamDesc {
     __nv_bfloat16 *dt_hi, *dt_lo;  // [R][BP] residual, transposed
     double *partial;          // [BP/128][N] objective partials
     double *f_data;           // [N] objective out (data term)
+    const uint8_t *active;    // [N] sites to evaluate (NULL = all)
     double inv_beff, beff;
     int B, N, KP, BP, R;
     int tile0_logits, tile0_grad;  // first tile of the family in each grid
@@ -244,10 +253,19 @@ int tc_padded_B(int B);
 // fills the scratch pointers, tile offsets and msaT of every family
 // (launches the transposes); scratch[f] points at tc_family_scratch_bytes
 cudaError_t launch_tc_prepare(TcBatch &b, void *const *scratch, cudaStream_t st);
+// tile shapes: logits tiles of `lg_sites` sites (24 columns each, even,
+// 2..10) x 128 sequences; gradient tiles of 128 rows x `gr_ncols` columns
+// (multiple of 32, <= 256)
+struct TcConfig {
+    int lg_sites = 8;
+    int gr_ncols = 256;
+};
+bool tc_config_valid(const TcConfig &c);
 // one evaluation of every family of the batch at its split theta (th_hi/lo):
-// f_data (data term) and G (with 2 lambda theta) per family
+// f_data (data term) and G (with 2 lambda theta) per family.  which: 1 =
+// logits + objective only, 2 = gradient only, 3 = both.
 // prof: opaque context pointer for per-kernel event timing (NULL = off)
-cudaError_t launch_tc_eval(void *prof, const TcBatch &b, double lambda_h, double lambda_Jp,
-                           int *err_flag, cudaStream_t st);
+cudaError_t launch_tc_eval(void *prof, const TcBatch &b, const TcConfig &cfg, double lambda_h,
+                           double lambda_Jp, int *err_flag, cudaStream_t st, int which = 3);
 
 }  // namespace plm
