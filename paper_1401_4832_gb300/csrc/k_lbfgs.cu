@@ -19,10 +19,14 @@
 // H0 = gamma I, gamma = s'y / y'y of the newest pair:
 //     H g = gamma g + S p - gamma Y R^{-1} u,
 //     u = S'g, v = Y'g, p = R^{-T} ((D + gamma Y'Y) R^{-1} u - gamma v),
-// R the upper triangle of S'Y (age order), D its diagonal.  One streaming
-// pass forms S'g, Y'g and the dot products of the newest y with every
-// stored pair (which keep S'Y and Y'Y current), a second pass forms d.
-// The result equals the two-loop recursion's.
+// R the upper triangle of S'Y (age order), D its diagonal.  u and v are
+// kept current incrementally: when the accepted step adds the pair
+// (s_n, y_n) and moves g to g + y_n, u_j += s_j'y_n and v_j += y_j'y_n for
+// the older pairs, and u_n = s_n'g_new, v_n = y_n'g_old + y_n'y_n for the new
+// one (the commit pass forms s_n'g_new and y_n'g_old from values it already
+// holds).  So one streaming pass forms S'y_n and Y'y_n (which also keep S'Y
+// and Y'Y current) and a second pass forms d.  The result equals the
+// two-loop recursion's.
 //
 // Step: strong-Wolfe search (c1, c2) in the style of Nocedal & Wright
 // Alg. 3.5/3.6, driven by the directional derivative: the objective is
@@ -134,103 +138,124 @@ __device__ __forceinline__ bool slot_valid(int j, int head, int hist, int M)
     return ((head - 1 - j + 2 * M) % M) < hist;  // distance from the newest slot
 }
 
-// pass 1: S'g, Y'g, S'y_new, Y'y_new
+// pass 1: S'y_n and Y'y_n for the newest pair n
 template <int M>
 __global__ void __launch_bounds__(LB_THREADS)
-k_dir_dots(const SiteState *ss, const float *__restrict__ g, const float *__restrict__ S,
-           const float *__restrict__ Y, const SiteInfo *si, const ChunkInfo *ci, long long vec4,
-           double *part)
+k_dir_dots(const SiteState *ss, const float *__restrict__ S, const float *__restrict__ Y,
+           const SiteInfo *si, const ChunkInfo *ci, long long vec4, double *part)
 {
     const Chunk ch = chunk_of(si, ci);
     const SiteState &s = ss[ch.site];
     if (s.status != SITE_READY || s.hist == 0) return;
     const int hist = s.hist, head = s.head;
     const int newest = (head - 1 + M) % M;
-    const float4 *g4 = (const float4 *)g + ch.base4;
     const float4 *S4 = (const float4 *)S + ch.base4;
     const float4 *Y4 = (const float4 *)Y + ch.base4;
     bool valid[M];
 #pragma unroll
     for (int j = 0; j < M; ++j) valid[j] = slot_valid(j, head, hist, M);
-    DF acc[4 * M];
+    DF acc[2 * M];
     for (size_t e = ch.e0 + threadIdx.x; e < ch.e1; e += LB_THREADS) {
-        const float4 gv = g4[e];
         const float4 yn = Y4[(size_t)newest * vec4 + e];
 #pragma unroll
         for (int j = 0; j < M; ++j) {
             if (!valid[j]) continue;
             const float4 sv = S4[(size_t)j * vec4 + e];
-            const float4 yv = Y4[(size_t)j * vec4 + e];
-            df_dot4(acc[j], sv, gv);
-            df_dot4(acc[M + j], yv, gv);
-            df_dot4(acc[2 * M + j], sv, yn);
-            df_dot4(acc[3 * M + j], yv, yn);
+            const float4 yv = (j == newest) ? yn : Y4[(size_t)j * vec4 + e];
+            df_dot4(acc[j], sv, yn);
+            df_dot4(acc[M + j], yv, yn);
         }
     }
-    double v[4 * M];
+    double v[2 * M];
 #pragma unroll
-    for (int k = 0; k < 4 * M; ++k) v[k] = df_value(acc[k]);
-    block_write<4 * M>(v, part_rec(part));
+    for (int k = 0; k < 2 * M; ++k) v[k] = df_value(acc[k]);
+    block_write<2 * M>(v, part_rec(part));
 }
 
-// the small FP64 algebra of the compact form, one warp per site
+// the small FP64 algebra of the compact form, one warp per site (the site's
+// matrices are staged in shared memory)
 template <int M>
 __global__ void k_dir_solve(SiteState *ss, const double *part, const SiteInfo *si)
 {
     const int r = blockIdx.x;
     SiteState &s = ss[r];
     if (s.status != SITE_READY) return;
-    __shared__ double tot[4 * M];
-    if (s.hist > 0) {
-        for (int k = 0; k < 4 * M; ++k) {
-            double t = chunk_sum(part, si[r], k);
-            if (threadIdx.x == 0) tot[k] = t;
+    __shared__ double tot[2 * M + 2];
+    __shared__ double SY[M][M], YY[M][M];
+    const int hist = s.hist, head = s.head;
+    const int lane = threadIdx.x;
+    if (hist > 0) {
+        for (int k = 0; k < 2 * M; ++k) {
+            const double t = chunk_sum(part, si[r], k);
+            if (lane == 0) tot[k] = t;
+        }
+        const double sg = chunk_sum(part, si[r], LB_SLOT_SG);
+        const double yg = chunk_sum(part, si[r], LB_SLOT_YG);
+        if (lane == 0) {
+            tot[2 * M] = sg;
+            tot[2 * M + 1] = yg;
+        }
+        for (int k = lane; k < M * M; k += 32) {
+            SY[k / M][k % M] = s.SY[k / M][k % M];
+            YY[k / M][k % M] = s.YY[k / M][k % M];
         }
     }
     __syncwarp();
-    if (threadIdx.x != 0) return;
+    if (lane != 0) return;
     for (int j = 0; j < MAX_M; ++j) s.cs[j] = s.cy[j] = 0.0;
     s.cg = 1.0;
-    int hist = s.hist, head = s.head;
     if (hist == 0) return;
     const int n = (head - 1 + M) % M;
+    // new column of S'Y and row/column of Y'Y; u, v moved to g_new
     for (int j = 0; j < M; ++j) {
         if (!slot_valid(j, head, hist, M)) continue;
-        s.SY[j][n] = tot[2 * M + j];
-        s.YY[j][n] = tot[3 * M + j];
-        s.YY[n][j] = tot[3 * M + j];
+        SY[j][n] = tot[j];
+        YY[j][n] = tot[M + j];
+        YY[n][j] = tot[M + j];
+        if (j != n) {
+            s.u[j] += tot[j];
+            s.v[j] += tot[M + j];
+        }
     }
-    if (!(s.SY[n][n] > 0.0) || !(s.YY[n][n] > 0.0)) {
+    s.u[n] = tot[2 * M];
+    s.v[n] = tot[2 * M + 1] + YY[n][n];
+    for (int j = 0; j < M; ++j) {
+        if (!slot_valid(j, head, hist, M)) continue;
+        s.SY[j][n] = SY[j][n];
+        s.YY[j][n] = YY[j][n];
+        s.YY[n][j] = YY[n][j];
+    }
+    if (!(SY[n][n] > 0.0) || !(YY[n][n] > 0.0)) {
         // newest pair violates the curvature condition: restart from -g
         s.hist = 0;
         s.head = 0;
         return;
     }
-    const double gamma = s.SY[n][n] / s.YY[n][n];
+    const double gamma = SY[n][n] / YY[n][n];
     int idx[M];
     double u[M], v[M], t1[M], t2[M], pp[M];
     for (int a = 0; a < hist; ++a) {
         idx[a] = (head - hist + a + 2 * M) % M;  // oldest first
-        u[a] = tot[idx[a]];
-        v[a] = tot[M + idx[a]];
+        u[a] = s.u[idx[a]];
+        v[a] = s.v[idx[a]];
     }
     // t1 = R^{-1} u, R[a][b] = s_a . y_b (a <= b in age order)
     for (int a = hist - 1; a >= 0; --a) {
         double x = u[a];
-        for (int b = a + 1; b < hist; ++b) x -= s.SY[idx[a]][idx[b]] * t1[b];
-        t1[a] = x / s.SY[idx[a]][idx[a]];
+        for (int b = a + 1; b < hist; ++b) x -= SY[idx[a]][idx[b]] * t1[b];
+        t1[a] = x / SY[idx[a]][idx[a]];
     }
     // t2 = (D + gamma Y'Y) t1 - gamma v
     for (int a = 0; a < hist; ++a) {
-        double x = s.SY[idx[a]][idx[a]] * t1[a] - gamma * v[a];
-        for (int b = 0; b < hist; ++b) x += gamma * s.YY[idx[a]][idx[b]] * t1[b];
+        double x = SY[idx[a]][idx[a]] * t1[a] - gamma * v[a];
+        for (int b = 0; b < hist; ++b) x += gamma * YY[idx[a]][idx[b]] * t1[b];
         t2[a] = x;
     }
     // p = R^{-T} t2
     for (int a = 0; a < hist; ++a) {
         double x = t2[a];
-        for (int b = 0; b < a; ++b) x -= s.SY[idx[b]][idx[a]] * pp[b];
-        pp[a] = x / s.SY[idx[a]][idx[a]];
+        for (int b = 0; b < a; ++b) x -= SY[idx[b]][idx[a]] * pp[b];
+        pp[a] = x / SY[idx[a]][idx[a]];
     }
     s.gamma = gamma;
     s.cg = gamma;
@@ -265,22 +290,41 @@ k_dir_apply(const SiteState *ss, const float *__restrict__ g, const float *__res
         cy[j] = (float)s.cy[j];
     }
     DF acc;
-    for (size_t e = ch.e0 + threadIdx.x; e < ch.e1; e += LB_THREADS) {
+    // two elements per pass keep twice the loads in flight
+    for (size_t e = ch.e0 + threadIdx.x; e < ch.e1; e += 2 * LB_THREADS) {
+        const size_t e2 = e + LB_THREADS;
+        const bool two = e2 < ch.e1;
         const float4 gv = g4[e];
+        const float4 gw = two ? g4[e2] : make_float4(0.f, 0.f, 0.f, 0.f);
         float4 a = make_float4(cg * gv.x, cg * gv.y, cg * gv.z, cg * gv.w);
+        float4 b = make_float4(cg * gw.x, cg * gw.y, cg * gw.z, cg * gw.w);
 #pragma unroll
         for (int j = 0; j < M; ++j) {
             if (!valid[j]) continue;
             const float4 sv = S4[(size_t)j * vec4 + e];
             const float4 yv = Y4[(size_t)j * vec4 + e];
+            float4 sw = make_float4(0.f, 0.f, 0.f, 0.f), yw = sw;
+            if (two) {
+                sw = S4[(size_t)j * vec4 + e2];
+                yw = Y4[(size_t)j * vec4 + e2];
+            }
             a.x += cs[j] * sv.x + cy[j] * yv.x;
             a.y += cs[j] * sv.y + cy[j] * yv.y;
             a.z += cs[j] * sv.z + cy[j] * yv.z;
             a.w += cs[j] * sv.w + cy[j] * yv.w;
+            b.x += cs[j] * sw.x + cy[j] * yw.x;
+            b.y += cs[j] * sw.y + cy[j] * yw.y;
+            b.z += cs[j] * sw.z + cy[j] * yw.z;
+            b.w += cs[j] * sw.w + cy[j] * yw.w;
         }
         const float4 dv = make_float4(-a.x, -a.y, -a.z, -a.w);
         d4[e] = dv;
         df_dot4(acc, gv, dv);
+        if (two) {
+            const float4 dw = make_float4(-b.x, -b.y, -b.z, -b.w);
+            d4[e2] = dw;
+            df_dot4(acc, gw, dw);
+        }
     }
     double v[1] = {df_value(acc)};
     block_write<1>(v, part_rec(part));
@@ -501,7 +545,7 @@ __global__ void __launch_bounds__(LB_THREADS)
 k_commit(const SiteState *ss, float *__restrict__ theta, float *__restrict__ g,
          const float *__restrict__ theta_t, const float *__restrict__ g_t,
          float *__restrict__ S, float *__restrict__ Y, const SiteInfo *si, const ChunkInfo *ci,
-         long long vec4, const int *round_ptr)
+         long long vec4, const int *round_ptr, double *part)
 {
     const int round = *round_ptr;
     const Chunk ch = chunk_of(si, ci);
@@ -514,13 +558,20 @@ k_commit(const SiteState *ss, float *__restrict__ theta, float *__restrict__ g,
     const float4 *gt4 = (const float4 *)g_t + ch.base4;
     float4 *s4 = (float4 *)S + slot * vec4 + ch.base4;
     float4 *y4 = (float4 *)Y + slot * vec4 + ch.base4;
+    DF sg, yg;
     for (size_t e = ch.e0 + threadIdx.x; e < ch.e1; e += LB_THREADS) {
         const float4 tn = tt4[e], to = th4[e], gn = gt4[e], go = g4[e];
-        s4[e] = make_float4(tn.x - to.x, tn.y - to.y, tn.z - to.z, tn.w - to.w);
-        y4[e] = make_float4(gn.x - go.x, gn.y - go.y, gn.z - go.z, gn.w - go.w);
+        const float4 sv = make_float4(tn.x - to.x, tn.y - to.y, tn.z - to.z, tn.w - to.w);
+        const float4 yv = make_float4(gn.x - go.x, gn.y - go.y, gn.z - go.z, gn.w - go.w);
+        s4[e] = sv;
+        y4[e] = yv;
         th4[e] = tn;
         g4[e] = gn;
+        df_dot4(sg, sv, gn);  // s_n . g_new
+        df_dot4(yg, yv, go);  // y_n . g_old
     }
+    double v[2] = {df_value(sg), df_value(yg)};
+    block_write<2>(v, part_rec(part) + LB_SLOT_SG);
 }
 
 }  // namespace
@@ -538,7 +589,7 @@ template <int M>
 static void direction_m(SiteState *ss, const float *g, float *dir, const float *S,
                         const float *Y, const LbLayout &L, double *part, cudaStream_t st)
 {
-    k_dir_dots<M><<<L.nchunks, LB_THREADS, 0, st>>>(ss, g, S, Y, L.si, L.ci, L.vec4, part);
+    k_dir_dots<M><<<L.nchunks, LB_THREADS, 0, st>>>(ss, S, Y, L.si, L.ci, L.vec4, part);
     k_dir_solve<M><<<L.nsites, 32, 0, st>>>(ss, part, L.si);
     k_dir_apply<M><<<L.nchunks, LB_THREADS, 0, st>>>(ss, g, S, Y, dir, L.si, L.ci, L.vec4, part);
 }
@@ -584,7 +635,7 @@ cudaError_t launch_lbfgs_linesearch(SiteState *ss, const double *f_data, float *
     k_ls_dots<<<L.nchunks, LB_THREADS, 0, st>>>(ss, g_t, dir, L.si, L.ci, part);
     k_ls_decide<<<L.nsites, 32, 0, st>>>(ss, f_data, part, L.si, p, round_ptr, counters);
     k_commit<<<L.nchunks, LB_THREADS, 0, st>>>(ss, theta, g, theta_t, g_t, S_hist, Y_hist, L.si,
-                                                L.ci, L.vec4, round_ptr);
+                                                L.ci, L.vec4, round_ptr, part);
     count_launches(3);
     return cudaGetLastError();
 }

@@ -63,6 +63,9 @@ enum SiteStatus : int {
 
 constexpr int MAX_M = 8;             // largest L-BFGS memory
 constexpr int LB_PART = 4 * MAX_M;   // doubles per (site, chunk) partial record
+// partial-record slots written by the commit of an accepted step and read by
+// the next direction step of that site: s_new . g_new, y_new . g_old
+constexpr int LB_SLOT_SG = LB_PART - 2, LB_SLOT_YG = LB_PART - 1;
 
 struct SiteState {
     double f;        // objective at theta
@@ -77,6 +80,7 @@ struct SiteState {
     double YY[MAX_M][MAX_M];  // y_i . y_j by ring slot
     double cg;                 // direction: d = -(cg g + sum cs_j s_j + sum cy_j y_j)
     double cs[MAX_M], cy[MAX_M];
+    double u[MAX_M], v[MAX_M];  // s_j . g and y_j . g at the current g, by ring slot
     int status;
     int phase;       // 0: bracketing, 1: zoom
     int trials;
