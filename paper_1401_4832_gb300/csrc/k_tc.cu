@@ -28,6 +28,8 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
+
 #include "plm_device.cuh"
 #include "plm_internal.cuh"
 
@@ -263,63 +265,70 @@ __device__ __forceinline__ int family_of(const TcBatch &b, int tile, bool grad)
     return f;
 }
 
+__device__ __forceinline__ void epi_bar2()
+{
+    asm volatile("bar.sync 2, 128;" ::: "memory");
+}
+
+// tile t of the logits grid: family, sequence tile, site tile
+__device__ __forceinline__ void lg_tile(const LogitsParams &P, int t, int &fi, int &tb, int &tr)
+{
+    fi = family_of(P.b, t, false);
+    const FamDesc &F = P.b.f[fi];
+    const int local = t - F.tile0_logits;
+    const int nbt = F.BP / TC_M;
+    tb = local % nbt;
+    tr = local / nbt;
+}
+
+// does the tile hold a site that needs this evaluation?
+__device__ __forceinline__ bool sites_active(const FamDesc &F, int r_lo, int r_hi)
+{
+    if (!F.active) return true;
+    for (int r = r_lo; r <= r_hi && r < F.N; ++r)
+        if (F.active[r]) return true;
+    return false;
+}
+
 // ---------------------------------------------------------------- logits
-__global__ void __launch_bounds__(192, 1)
+// Persistent: one CTA per SM walks the tile list (stride gridDim.x).  Warp
+// 0: TMA for Theta hi/lo; warp 1: TMEM (2 x 256 columns) and MMA issue;
+// warps 2-5: one-hot producers; warps 6-9: epilogue.  The accumulator is
+// double-buffered, so a tile's epilogue overlaps the next tile's main loop.
+__global__ void __launch_bounds__(320, 1)
 k_tc_logits(const __grid_constant__ LogitsParams P, int *__restrict__ err)
 {
-    const int fi = family_of(P.b, blockIdx.x, false);
-    const FamDesc &F = P.b.f[fi];
-    const CUtensorMap &tm_hi = P.hi[fi];
-    const CUtensorMap &tm_lo = P.lo[fi];
-    const int8_t *__restrict__ msa = F.msa;
-    const float *__restrict__ w = F.w;
-    const double inv_beff = F.inv_beff;
-    const int BP = F.BP;
-    __nv_bfloat16 *__restrict__ dt_hi = F.dt_hi;
-    __nv_bfloat16 *__restrict__ dt_lo = F.dt_lo;
-    double *__restrict__ partial = F.partial;
-    Dims d;
-    d.B = F.B;
-    d.N = F.N;
-    d.KP = F.KP;
-    d.R = F.R;
-    d.K = F.N * Q + 1;
-    const int local = blockIdx.x - F.tile0_logits;
-    const int nbt = BP / TC_M;
-    const int LGS = P.sites, LGN = P.ncols, NST = P.stages, LGSTAGE = P.stage_bytes;
-    const int LGB = LGN * TC_BK * 2;
     extern __shared__ uint8_t dsmem[];
     uint8_t *smem = align1024(dsmem);
-    __shared__ __align__(8) uint64_t full_b[MAX_STAGES], full_a[MAX_STAGES], empty_[MAX_STAGES], acc_full;
+    const int LGS = P.sites, NST = P.stages, LGSTAGE = P.stage_bytes;
+    const int LGB = P.ncols * TC_BK * 2;
+    // epilogue slab: the residual rows of two sites, [48][128] bf16, hi then lo
+    __nv_bfloat16 *slab_hi = (__nv_bfloat16 *)(smem + NST * LGSTAGE);
+    __nv_bfloat16 *slab_lo = slab_hi + 2 * QP * TC_M;
+    __shared__ __align__(8) uint64_t full_b[MAX_STAGES], full_a[MAX_STAGES], empty_[MAX_STAGES];
+    __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2], mma_done;
     __shared__ uint32_t tmem_sh;
     __shared__ int abort_sh;
     __shared__ double red[4][MAX_LG_SITES];
-
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tb = local % nbt, tr = local / nbt;
-    const int b0 = tb * TC_M;
-    const int r0 = tr * LGS;
-    if (F.active) {  // skip the tile when none of its sites needs this evaluation
-        bool any = false;
-        for (int j = 0; j < LGS && r0 + j < F.N; ++j) any |= F.active[r0 + j] != 0;
-        if (!any) return;
-    }
-    const int row0 = r0 * QP;
-    const int NK = d.KP / TC_BK;
-    const int NQ = d.N * Q;
+    const int ntiles = P.b.ntiles_logits;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < NST; ++s) {
+        for (int s = 0; s < MAX_STAGES; ++s) {
             mbar_init(&full_b[s], 1);
             mbar_init(&full_a[s], 128);
             mbar_init(&empty_[s], 1);
         }
-        mbar_init(&acc_full, 1);
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&acc_full[a], 1);
+            mbar_init(&acc_empty[a], 128);
+        }
+        mbar_init(&mma_done, 1);
         abort_sh = 0;
         fence_mbar_init();
     }
     if (warp == 1) {
-        tmem_alloc(&tmem_sh, TMEM_COLS);
+        tmem_alloc(&tmem_sh, 2 * TMEM_COLS);
         tmem_relinquish();
     }
     tc_fence_before();
@@ -329,175 +338,244 @@ k_tc_logits(const __grid_constant__ LogitsParams P, int *__restrict__ err)
 
     if (warp == 0) {
         if (lane == 0) {
-            int issued = 0;
-            for (int kc = 0; kc < NK; ++kc) {
-                const int s = kc % NST, n = kc / NST;
-                if (n > 0 && !mbar_wait(&empty_[s], (n - 1) & 1, &abort_sh, err, ERR_TIMEOUT_TMA))
-                    break;
-                uint8_t *st = smem + s * LGSTAGE;
-                mbar_expect_tx(&full_b[s], 2 * LGB);
-                tma_load_2d(st + LG_A_BYTES, &tm_hi, &full_b[s], kc * TC_BK, row0);
-                tma_load_2d(st + LG_A_BYTES + LGB, &tm_lo, &full_b[s], kc * TC_BK, row0);
-                issued = kc + 1;
+            long long kit = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                int fi, tb, tr;
+                lg_tile(P, t, fi, tb, tr);
+                const FamDesc &F = P.b.f[fi];
+                if (!sites_active(F, tr * LGS, tr * LGS + LGS - 1)) continue;
+                const int row0 = tr * LGS * QP, NK = F.KP / TC_BK;
+                for (int kc = 0; kc < NK; ++kc, ++kit) {
+                    const int s = (int)(kit % NST);
+                    const long long n = kit / NST;
+                    if (n > 0 &&
+                        !mbar_wait(&empty_[s], (uint32_t)((n - 1) & 1), &abort_sh, err, ERR_TIMEOUT_TMA)) {
+                        ok = false;
+                        break;
+                    }
+                    uint8_t *st = smem + s * LGSTAGE;
+                    mbar_expect_tx(&full_b[s], 2 * LGB);
+                    tma_load_2d(st + LG_A_BYTES, &P.hi[fi], &full_b[s], kc * TC_BK, row0);
+                    tma_load_2d(st + LG_A_BYTES + LGB, &P.lo[fi], &full_b[s], kc * TC_BK, row0);
+                }
             }
             // let the copies still in flight land before the CTA can exit
-            for (int kc = issued - NST < 0 ? 0 : issued - NST; kc < issued; ++kc)
-                mbar_drain(&full_b[kc % NST], (kc / NST) & 1);
+            for (long long k = kit - NST < 0 ? 0 : kit - NST; k < kit; ++k)
+                mbar_drain(&full_b[k % NST], (uint32_t)((k / NST) & 1));
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            const uint32_t idesc = idesc_bf16(TC_M, LGN);
-            for (int kc = 0; kc < NK; ++kc) {
-                const int s = kc % NST, n = kc / NST;
-                if (!mbar_wait(&full_b[s], n & 1, &abort_sh, err, ERR_TIMEOUT_MMA)) break;
-                if (!mbar_wait(&full_a[s], n & 1, &abort_sh, err, ERR_TIMEOUT_MMA)) break;
+            const uint32_t idesc = idesc_bf16(TC_M, P.ncols);
+            long long kit = 0;
+            int ti = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                int fi, tb, tr;
+                lg_tile(P, t, fi, tb, tr);
+                const FamDesc &F = P.b.f[fi];
+                if (!sites_active(F, tr * LGS, tr * LGS + LGS - 1)) continue;
+                const int a = ti & 1, use = ti >> 1;
+                if (use > 0 &&
+                    !mbar_wait(&acc_empty[a], (uint32_t)((use - 1) & 1), &abort_sh, err, ERR_TIMEOUT_MMA))
+                    break;
                 tc_fence_after();
-                uint8_t *st = smem + s * LGSTAGE;
-                const uint32_t a = smem_u32(st);
-                const uint32_t bh = smem_u32(st + LG_A_BYTES);
-                const uint32_t bl = smem_u32(st + LG_A_BYTES + LGB);
+                const uint32_t dt = tmem + a * TMEM_COLS;
+                const int NK = F.KP / TC_BK;
+                for (int kc = 0; kc < NK; ++kc, ++kit) {
+                    const int s = (int)(kit % NST);
+                    const uint32_t ph = (uint32_t)((kit / NST) & 1);
+                    if (!mbar_wait(&full_b[s], ph, &abort_sh, err, ERR_TIMEOUT_MMA) ||
+                        !mbar_wait(&full_a[s], ph, &abort_sh, err, ERR_TIMEOUT_MMA)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    uint8_t *st = smem + s * LGSTAGE;
+                    const uint32_t aa = smem_u32(st);
+                    const uint32_t bh = smem_u32(st + LG_A_BYTES);
+                    const uint32_t bl = smem_u32(st + LG_A_BYTES + LGB);
 #pragma unroll
-                for (int k = 0; k < TC_BK / 16; ++k)
-                    mma_bf16(tmem, sdesc(a + 32 * k), sdesc(bh + 32 * k), idesc,
-                             (kc > 0 || k > 0) ? 1u : 0u);
+                    for (int k = 0; k < TC_BK / 16; ++k)
+                        mma_bf16(dt, sdesc(aa + 32 * k), sdesc(bh + 32 * k), idesc,
+                                 (kc > 0 || k > 0) ? 1u : 0u);
 #pragma unroll
-                for (int k = 0; k < TC_BK / 16; ++k)
-                    mma_bf16(tmem, sdesc(a + 32 * k), sdesc(bl + 32 * k), idesc, 1u);
-                mma_commit(&empty_[s]);
+                    for (int k = 0; k < TC_BK / 16; ++k)
+                        mma_bf16(dt, sdesc(aa + 32 * k), sdesc(bl + 32 * k), idesc, 1u);
+                    mma_commit(&empty_[s]);
+                }
+                if (!ok) break;
+                mma_commit(&acc_full[a]);
+                ++ti;
             }
-            mma_commit(&acc_full);  // arrives when every MMA above has completed
+            mma_commit(&mma_done);  // arrives when every MMA issued above has completed
         }
-    } else {
-        // ---- one-hot producer: thread p writes row p of X (sequence b0 + p)
+    } else if (warp < 6) {
+        // ---- one-hot producers: thread p writes row p of X for each tile
         const int p = threadIdx.x - 64;
-        const int b = b0 + p;
-        const bool valid = b < d.B;
-        const int8_t *srow = msa + (size_t)(valid ? b : 0) * d.N;
-        // states of the (at most 5) positions a chunk of 64 columns touches,
-        // fetched one chunk ahead
-        auto fetch = [&](int kc, int (&st5)[5]) {
-            const int i_lo = (kc * TC_BK) / Q;
-#pragma unroll
-            for (int u = 0; u < 5; ++u) {
-                const int i = i_lo + u;
-                st5[u] = (valid && i < d.N) ? (int)srow[i] : 0;
-            }
-        };
-        int cur5[5], nxt5[5];
-        fetch(0, cur5);
-        for (int kc = 0; kc < NK; ++kc) {
-            const int s = kc % NST, n = kc / NST;
-            fetch(kc + 1 < NK ? kc + 1 : kc, nxt5);
-            if (n > 0 && !mbar_wait(&empty_[s], (n - 1) & 1, &abort_sh, err, ERR_TIMEOUT_PROD))
-                break;
-            uint8_t *rowp = smem + s * LGSTAGE + p * 128;
-            const uint4 z = make_uint4(0, 0, 0, 0);
-            // rotate the chunk order by row so a warp's stores spread over the banks
-#pragma unroll
-            for (int j = 0; j < 8; ++j) *(uint4 *)(rowp + ((j + p) & 7) * 16) = z;
-            if (valid) {
-                const int c0 = kc * TC_BK;
-                const int i_lo = c0 / Q;
+        long long kit = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            int fi, tb, tr;
+            lg_tile(P, t, fi, tb, tr);
+            const FamDesc &F = P.b.f[fi];
+            if (!sites_active(F, tr * LGS, tr * LGS + LGS - 1)) continue;
+            const int b = tb * TC_M + p;
+            const bool valid = b < F.B;
+            const int8_t *srow = F.msa + (size_t)(valid ? b : 0) * F.N;
+            const int NK = F.KP / TC_BK, NQ = F.N * Q, N = F.N;
+            // states of the (at most 5) positions a chunk of 64 columns
+            // touches, fetched one chunk ahead
+            auto fetch = [&](int kc, int (&st5)[5]) {
+                const int i_lo = (kc * TC_BK) / Q;
 #pragma unroll
                 for (int u = 0; u < 5; ++u) {
                     const int i = i_lo + u;
-                    const int pos = i * Q + cur5[u] - c0;
-                    if (i < d.N && pos >= 0 && pos < TC_BK)
-                        *(uint16_t *)(rowp + ((((pos >> 3) ^ (p & 7)) << 4) | ((pos & 7) << 1))) =
+                    st5[u] = (valid && i < N) ? (int)srow[i] : 0;
+                }
+            };
+            int cur5[5], nxt5[5];
+            fetch(0, cur5);
+            for (int kc = 0; kc < NK; ++kc, ++kit) {
+                const int s = (int)(kit % NST);
+                const long long n = kit / NST;
+                fetch(kc + 1 < NK ? kc + 1 : kc, nxt5);
+                if (n > 0 &&
+                    !mbar_wait(&empty_[s], (uint32_t)((n - 1) & 1), &abort_sh, err, ERR_TIMEOUT_PROD)) {
+                    ok = false;
+                    break;
+                }
+                uint8_t *rowp = smem + s * LGSTAGE + p * 128;
+                const uint4 z = make_uint4(0, 0, 0, 0);
+                // rotate the chunk order by row so a warp's stores spread over the banks
+#pragma unroll
+                for (int j = 0; j < 8; ++j) *(uint4 *)(rowp + ((j + p) & 7) * 16) = z;
+                if (valid) {
+                    const int c0 = kc * TC_BK;
+                    const int i_lo = c0 / Q;
+#pragma unroll
+                    for (int u = 0; u < 5; ++u) {
+                        const int i = i_lo + u;
+                        const int pos = i * Q + cur5[u] - c0;
+                        if (i < N && pos >= 0 && pos < TC_BK)
+                            *(uint16_t *)(rowp + ((((pos >> 3) ^ (p & 7)) << 4) | ((pos & 7) << 1))) =
+                                0x3F80;
+                    }
+                    const int pf = NQ - c0;  // the field column: feature 1
+                    if (pf >= 0 && pf < TC_BK)
+                        *(uint16_t *)(rowp + ((((pf >> 3) ^ (p & 7)) << 4) | ((pf & 7) << 1))) =
                             0x3F80;
                 }
-                const int pf = NQ - c0;  // the field column: feature 1
-                if (pf >= 0 && pf < TC_BK)
-                    *(uint16_t *)(rowp + ((((pf >> 3) ^ (p & 7)) << 4) | ((pf & 7) << 1))) = 0x3F80;
-            }
-            fence_proxy_async();
-            mbar_arrive(&full_a[s]);
+                fence_proxy_async();
+                mbar_arrive(&full_a[s]);
 #pragma unroll
-            for (int u = 0; u < 5; ++u) cur5[u] = nxt5[u];
+                for (int u = 0; u < 5; ++u) cur5[u] = nxt5[u];
+            }
         }
-
-        // ---- epilogue: one sequence per thread, its TMEM lane.  The residual
-        // tile is staged in the (now idle) pipeline buffers as D^T rows of
-        // 128 sequences, then written out with 16-byte stores.
+    } else {
+        // ---- epilogue: one sequence per thread (its TMEM lane).  Residual
+        // rows of two sites at a time are staged in the slab and written out
+        // with 16-byte stores.
         const int q4 = warp & 3;
         const int er = q4 * 32 + lane;
-        const int eb = b0 + er;
-        const bool ev = eb < d.B;
-        const bool ok = mbar_wait(&acc_full, 0, &abort_sh, err, ERR_TIMEOUT_EPI);
-        tc_fence_after();
-        __nv_bfloat16 *st_hi = (__nv_bfloat16 *)smem;            // [LGN][128]
-        __nv_bfloat16 *st_lo = st_hi + LGN * TC_M;              // [LGN][128]
-        const float wb = ev ? w[eb] : 0.0f;
-        const float scale = (float)((double)wb * inv_beff);
-        const uint32_t tl = tmem + ((uint32_t)(q4 * 32) << 16);
+        const int t128 = threadIdx.x - 192;
+        int ti = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            int fi, tb, tr;
+            lg_tile(P, t, fi, tb, tr);
+            const FamDesc &F = P.b.f[fi];
+            const int r0 = tr * LGS;
+            if (!sites_active(F, r0, r0 + LGS - 1)) continue;
+            const int a = ti & 1, use = ti >> 1;
+            const bool ok = mbar_wait(&acc_full[a], (uint32_t)(use & 1), &abort_sh, err, ERR_TIMEOUT_EPI);
+            tc_fence_after();
+            const int b0 = tb * TC_M, row0 = r0 * QP, BP = F.BP;
+            const int eb = b0 + er;
+            const bool ev = eb < F.B;
+            const float wb = ev ? F.w[eb] : 0.0f;
+            const float scale = (float)((double)wb * F.inv_beff);
+            const uint32_t tl = tmem + a * TMEM_COLS + ((uint32_t)(q4 * 32) << 16);
 #pragma unroll 1
-        for (int jp = 0; jp < LGS / 2; ++jp) {
-            float v[48];
-            tmem_ld16(tl + jp * 48, v);
-            tmem_ld16(tl + jp * 48 + 16, v + 16);
-            tmem_ld16(tl + jp * 48 + 32, v + 32);
-            tmem_wait_ld();
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int j = 2 * jp + h;
-                const int r = r0 + j;
-                const float *l = v + 24 * h;
-                double contrib = 0.0;
-                float mx = l[0];
-#pragma unroll
-                for (int s2 = 1; s2 < Q; ++s2) mx = fmaxf(mx, l[s2]);
-                float z = 0.0f;
-#pragma unroll
-                for (int s2 = 0; s2 < Q; ++s2) z += __expf(l[s2] - mx);
-                const float lse = mx + __logf(z);
-                const int sr = (ev && r < d.N) ? msa[(size_t)eb * d.N + r] : -1;
-                float lsr = 0.0f;
-#pragma unroll
-                for (int s2 = 0; s2 < Q; ++s2)
-                    if (s2 == sr) lsr = l[s2];
-                if (ev && r < d.N && ok) contrib = (double)wb * (double)(lsr - lse);
-#pragma unroll
-                for (int s2 = 0; s2 < QP; ++s2) {
-                    float dv = 0.0f;
-                    if (s2 < Q && ev && r < d.N)
-                        dv = scale * (__expf(l[s2] - lse) - (s2 == sr ? 1.0f : 0.0f));
-                    const __nv_bfloat16 hi = __float2bfloat16_rn(dv);
-                    st_hi[(j * QP + s2) * TC_M + er] = hi;
-                    st_lo[(j * QP + s2) * TC_M + er] =
-                        __float2bfloat16_rn(dv - __bfloat162float(hi));
+            for (int jp = 0; jp < LGS / 2; ++jp) {
+                float v[48];
+                tmem_ld16(tl + jp * 48, v);
+                tmem_ld16(tl + jp * 48 + 16, v + 16);
+                tmem_ld16(tl + jp * 48 + 32, v + 32);
+                tmem_wait_ld();
+                if (jp == LGS / 2 - 1) {
+                    // all tensor-memory reads of this tile are done: release it
+                    tc_fence_before();
+                    mbar_arrive(&acc_empty[a]);
                 }
-                contrib = warp_sum_d(contrib);
-                if (lane == 0) red[q4][j] = contrib;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int j = 2 * jp + h;
+                    const int r = r0 + j;
+                    const float *l = v + 24 * h;
+                    float mx = l[0];
+#pragma unroll
+                    for (int s2 = 1; s2 < Q; ++s2) mx = fmaxf(mx, l[s2]);
+                    float z = 0.0f;
+#pragma unroll
+                    for (int s2 = 0; s2 < Q; ++s2) z += __expf(l[s2] - mx);
+                    const float lse = mx + __logf(z);
+                    const int sr = (ev && r < F.N) ? F.msa[(size_t)eb * F.N + r] : -1;
+                    float lsr = 0.0f;
+#pragma unroll
+                    for (int s2 = 0; s2 < Q; ++s2)
+                        if (s2 == sr) lsr = l[s2];
+                    double contrib = 0.0;
+                    if (ev && r < F.N && ok) contrib = (double)wb * (double)(lsr - lse);
+#pragma unroll
+                    for (int s2 = 0; s2 < QP; ++s2) {
+                        float dv = 0.0f;
+                        if (s2 < Q && ev && r < F.N)
+                            dv = scale * (__expf(l[s2] - lse) - (s2 == sr ? 1.0f : 0.0f));
+                        const __nv_bfloat16 hi = __float2bfloat16_rn(dv);
+                        slab_hi[(h * QP + s2) * TC_M + er] = hi;
+                        slab_lo[(h * QP + s2) * TC_M + er] =
+                            __float2bfloat16_rn(dv - __bfloat162float(hi));
+                    }
+                    contrib = warp_sum_d(contrib);
+                    if (lane == 0) red[q4][j] = contrib;
+                }
+                epi_bar2();
+                // copy-out: 2 sites x 24 rows x 128 sequences, hi and lo
+                const int nrows = min(2 * QP, F.R - (row0 + jp * 2 * QP));
+                for (int e = t128; e < 2 * 2 * QP * 16; e += 128) {
+                    const int half = e / (2 * QP * 16);
+                    const int rem = e % (2 * QP * 16);
+                    const int row = rem / 16, c16 = rem % 16;
+                    if (!ok || row >= nrows) continue;
+                    const __nv_bfloat16 *src = (half ? slab_lo : slab_hi) + row * TC_M + c16 * 8;
+                    __nv_bfloat16 *dst = (half ? F.dt_lo : F.dt_hi) +
+                                         (size_t)(row0 + jp * 2 * QP + row) * BP + b0 + c16 * 8;
+                    *(uint4 *)dst = *(const uint4 *)src;
+                }
+                epi_bar2();
             }
-        }
-        epi_bar();
-        const int t = threadIdx.x - 64;
-        if (t < LGS && r0 + t < d.N)
-            partial[(size_t)tb * d.N + r0 + t] = ((red[0][t] + red[1][t]) + red[2][t]) + red[3][t];
-        // copy-out: row (r,s) of the tile = 128 sequences = 256 bytes = 16 x 16 B
-        const int nrows = min(LGN, d.R - row0);
-        for (int e = t; e < 2 * LGN * 16; e += 128) {
-            const int half = e / (LGN * 16);
-            const int rem = e % (LGN * 16);
-            const int row = rem / 16, c16 = rem % 16;
-            if (row >= nrows) continue;
-            const __nv_bfloat16 *src = (half ? st_lo : st_hi) + row * TC_M + c16 * 8;
-            __nv_bfloat16 *dst = (half ? dt_lo : dt_hi) + (size_t)(row0 + row) * BP + b0 + c16 * 8;
-            *(uint4 *)dst = *(const uint4 *)src;
+            if (t128 < LGS && r0 + t128 < F.N && ok)
+                F.partial[(size_t)tb * F.N + r0 + t128] =
+                    ((red[0][t128] + red[1][t128]) + red[2][t128]) + red[3][t128];
+            epi_bar2();
+            ++ti;
         }
     }
     tc_fence_before();
     __syncthreads();
     if (warp == 1) {
         // every MMA must be complete before the tensor memory is released
-        if (lane == 0) mbar_drain(&acc_full, 0);
+        if (lane == 0) mbar_drain(&mma_done, 0);
         __syncwarp();
         tc_fence_after();
-        tmem_dealloc(tmem, TMEM_COLS);
+        tmem_dealloc(tmem, 2 * TMEM_COLS);
     }
 }
 
 // ---------------------------------------------------------------- gradient
+// One 128 x ncols tile per CTA (measured faster here than a persistent
+// variant: with ~1.5 tiles per SM there is little epilogue to overlap, and
+// the whole-tile shared-memory staging of the epilogue writes G coalesced).
 __global__ void __launch_bounds__(192, 1)
 k_tc_grad(const __grid_constant__ GradParams P, float two_lh, float two_lj, int *__restrict__ err)
 {
@@ -858,10 +936,24 @@ cudaError_t launch_tc_prepare(TcBatch &b, void *const *scratch, cudaStream_t st)
     return cudaGetLastError();
 }
 
-int tc_stages(int stage_bytes)
+constexpr int LG_SLAB = 2 * 2 * QP * TC_M * 2;  // two sites of residual rows, hi + lo
+
+int tc_stages(int stage_bytes, int slab_bytes)
 {
-    int n = SMEM_BUDGET / stage_bytes;
+    int n = (SMEM_BUDGET - slab_bytes) / stage_bytes;
     return n > MAX_STAGES ? MAX_STAGES : n;
+}
+
+int num_sms()
+{
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
 }
 
 bool tc_config_valid(const TcConfig &c)
@@ -904,10 +996,10 @@ cudaError_t launch_tc_eval(void *prof, const TcBatch &b_in, const TcConfig &cfg,
     lp.sites = cfg.lg_sites;
     lp.ncols = lg_ncols;
     lp.stage_bytes = LG_A_BYTES + 2 * lg_ncols * TC_BK * 2;
-    lp.stages = tc_stages(lp.stage_bytes);
+    lp.stages = tc_stages(lp.stage_bytes, LG_SLAB);
     gp.ncols = cfg.gr_ncols;
     gp.stage_bytes = 2 * GR_A_BYTES + cfg.gr_ncols * TC_BK * 2;
-    gp.stages = tc_stages(gp.stage_bytes);
+    gp.stages = tc_stages(gp.stage_bytes, 0);
     for (int i = 0; i < lp.b.nfam; ++i) {
         const FamDesc &F = lp.b.f[i];
         if (!make_map(&lp.hi[i], F.th_hi, F.KP, F.R, TC_BK, lg_ncols) ||
@@ -918,15 +1010,18 @@ cudaError_t launch_tc_eval(void *prof, const TcBatch &b_in, const TcConfig &cfg,
     }
     if (which & 1) {
         void *t0 = prof ? prof_start(prof) : nullptr;
-        k_tc_logits<<<tl, 192, lp.stages * lp.stage_bytes + 1024, st>>>(lp, err);
+        const int grid = std::min(tl, num_sms());
+        if (grid > 0)
+            k_tc_logits<<<grid, 320, lp.stages * lp.stage_bytes + LG_SLAB + 1024, st>>>(lp, err);
         if (prof) prof_stop(prof, "tc_logits", t0);
         k_tc_finish<<<lp.b.nfam, 128, 0, st>>>(lp.b);
         count_launches(2);
     }
     if (which & 2) {
         void *t1 = prof ? prof_start(prof) : nullptr;
-        k_tc_grad<<<tg, 192, gp.stages * gp.stage_bytes + 1024, st>>>(
-            gp, (float)(2.0 * lambda_h), (float)(2.0 * lambda_Jp), err);
+        if (tg > 0)
+            k_tc_grad<<<tg, 192, gp.stages * gp.stage_bytes + 1024, st>>>(
+                gp, (float)(2.0 * lambda_h), (float)(2.0 * lambda_Jp), err);
         if (prof) prof_stop(prof, "tc_grad", t1);
         count_launches(1);
     }
