@@ -350,28 +350,26 @@ def main():
     d2h = (N * 21 + (N * 21) ** 2) * 4 + 2 * N * N * 8 + N * 2 * 4
 
     # per-kernel device times of one profiled solve (events on the library stream)
+    import ctypes
+    lib.plm_profile_report.argtypes = [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_int]
     lib.plm_profile(ctx.handle, 1)
     with torch.cuda.stream(stream):
         flush.zero_()
         rep_p, _ = step()
-    import ctypes
-    buf = ctypes.create_string_buffer(1 << 16)
-    lib.plm_profile_report.argtypes = [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_int]
-    lib.plm_profile_report(ctx.handle, buf, len(buf))
+    kern = read_profile(lib, ctx)
     lib.plm_profile(ctx.handle, 0)
-    kern = {}
-    for ln in buf.value.decode().splitlines():
-        name, cnt, ms = ln.split()
-        kern[name] = (int(cnt), float(ms))
+    # the tensor-core kernels on full evaluations (every tile live; inside the
+    # solve, tiles whose sites all stopped searching are skipped)
+    tc_full = tc_full_evals(api, lib, ctx, stream, msa, flush, prec, reps=10)
+    per_kernel = kernel_rooflines(kern, tc_full, B, N, pk, pk_kind)
     dom = max(kern, key=lambda k: kern[k][1]) if kern else None
     roof = None
     if dom:
-        cnt, ms = kern[dom]
-        avg_s = ms / 1000.0 / cnt
-        roof = roofline_entry(dom, avg_s, B, N, pk, pk_kind)
+        roof = dict(per_kernel.get(dom) or {"bound": None, "achieved": None, "peak": None,
+                                            "unit": None, "frac": None, "traffic": None})
         roof["kernel"] = dom
-        roof["launches_profiled"] = cnt
-        roof["share_of_profiled"] = ms / sum(v[1] for v in kern.values())
+        roof["launches_profiled"] = kern[dom][0]
+        roof["share_of_profiled"] = kern[dom][1] / sum(v[1] for v in kern.values())
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -405,6 +403,7 @@ def main():
             "gpu_launches": launches,
             "roofline": roof,
             "kernels_profiled_ms": {k: v[1] for k, v in kern.items()},
+            "kernel_rooflines": per_kernel,
             "cpu_baseline": cpu,
             "wall_s_timed_region": t_wall,
         }
@@ -414,31 +413,80 @@ def main():
         dist.destroy_process_group()
 
 
-def roofline_entry(kernel, avg_s, B, N, pk, pk_kind):
-    """Algorithmic work of one launch of the dominant kernel / its duration."""
+def read_profile(lib, ctx):
+    """{kernel: (launches, total ms, algorithmic bytes)} from the context's
+    profile record."""
+    import ctypes
+    buf = ctypes.create_string_buffer(1 << 16)
+    lib.plm_profile_report(ctx.handle, buf, len(buf))
+    out = {}
+    for ln in buf.value.decode().splitlines():
+        name, cnt, ms, by = ln.split()
+        out[name] = (int(cnt), float(ms), float(by))
+    return out
+
+
+def tc_full_evals(api, lib, ctx, stream, msa, flush, prec, reps=10):
+    """Per-launch device time of the evaluation kernels on full evaluations
+    (all sites, a random theta), L2 flushed before each."""
+    import numpy as np
+    import torch
+    B, N = msa.shape
+    m, w, beff = api.msa_reweight(ctx, msa)
+    rng = np.random.default_rng(0)
+    h = torch.from_numpy(rng.normal(0, 0.05, (N, 21)).astype(np.float32)).to(msa.device)
+    J = rng.normal(0, 0.05, (N, 21, N, 21)).astype(np.float32)
+    for r in range(N):
+        J[r, :, r, :] = 0
+    J = torch.from_numpy(J).to(msa.device)
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            api.plm_site_objective_grad(ctx, msa, w, beff, h, J, prec=prec)
+        lib.plm_profile(ctx.handle, 1)
+        for _ in range(reps):
+            flush.zero_()
+            api.plm_site_objective_grad(ctx, msa, w, beff, h, J, prec=prec)
+        kern = read_profile(lib, ctx)
+        lib.plm_profile(ctx.handle, 0)
+    return {k: v[1] / 1000.0 / v[0] for k, v in kern.items()}
+
+
+def kernel_rooflines(kern, tc_full, B, N, pk, pk_kind):
+    """Roofline entry of every profiled kernel: HBM-bound passes from their
+    algorithmic bytes over the profiled solve, tensor-core kernels from the
+    dense-equivalent flops of one full evaluation."""
     q = 21
-    if kernel in ("logits_gather", "grad_gather"):
-        # one FP32 add per gathered coupling: B * N * (N-1) * q couplings + B*N*q fields
-        adds = B * N * N * q
-        sm_mhz = pk.get("sm_max_mhz", 2070.0)
-        peak = 152 * 128 * sm_mhz * 1e6 / 1e12  # FP32 lanes x clock, T adds/s
-        ach = adds / avg_s / 1e12
-        return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Tadd/s",
-                "frac": ach / peak, "traffic": None,
-                "peak_note": f"152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (derived)"}
-    if kernel in ("tc_logits", "tc_grad"):
-        KP = (N * q + 1 + 63) // 64 * 64
-        R = N * 24
-        BP = (B + 127) // 128 * 128
-        flops = 2 * 2 * BP * R * KP  # split: two bf16 products into one accumulator
-        peak = pk.get("bf16_tflops_sustained", 1700.0)
-        ach = flops / avg_s / 1e12
-        return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": None,
-                "peak_note": f"bf16 dense sustained, {pk_kind}"}
-    # L-BFGS / other streaming kernels: HBM bound
-    return {"bound": "hbm", "achieved": None, "peak": pk.get("hbm_gbs"), "unit": "GB/s",
-            "frac": None, "traffic": None}
+    out = {}
+    hbm = pk.get("hbm_gbs", 6800.0)
+    for name, (cnt, ms, by) in kern.items():
+        if by > 0:
+            ach = by / (ms / 1000.0) / 1e9
+            out[name] = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                         "frac": ach / hbm, "traffic": None,
+                         "bytes_per_launch": by / cnt,
+                         "peak_note": f"HBM copy bandwidth, {pk_kind}"}
+    for name, avg_s in tc_full.items():
+        if name in ("tc_logits", "tc_grad"):
+            # the one-hot contraction as a dense GEMM (unpadded): B x Nq x (Nq + 1)
+            # multiply-adds, two bf16 products (hi, lo) each
+            flops = 2 * 2 * B * (N * q) * (N * q + 1)
+            peak = pk.get("bf16_tflops_sustained", 1700.0)
+            ach = flops / avg_s / 1e12
+            out[name] = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                         "frac": ach / peak, "traffic": None, "flops_per_launch": flops,
+                         "launch_us_full_eval": avg_s * 1e6,
+                         "peak_note": f"bf16 dense sustained, {pk_kind}; timed on full "
+                                      "evaluations, L2 flushed before each"}
+        elif name in ("logits_gather", "grad_gather"):
+            adds = B * N * N * q
+            sm_mhz = pk.get("sm_max_mhz", 2070.0)
+            peak = 152 * 128 * sm_mhz * 1e6 / 1e12
+            ach = adds / avg_s / 1e12
+            out[name] = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Tadd/s",
+                         "frac": ach / peak, "traffic": None,
+                         "launch_us_full_eval": avg_s * 1e6,
+                         "peak_note": f"152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (derived)"}
+    return out
 
 
 if __name__ == "__main__":

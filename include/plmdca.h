@@ -224,8 +224,11 @@ plm_status msa_reweight_static(const int8_t *msa, int B, int N, int q, double x,
  * plm_profile: with enable = 1 the context brackets each hot kernel with
  * CUDA events on its stream (a small timing overhead); enable = 0 stops and
  * clears the record.  plm_profile_report writes one line per kernel,
- * "name launches total_ms\n", into buf (NUL-terminated, truncated to len);
- * it synchronises the stream and returns the number of bytes needed. */
+ * "name launches total_ms bytes\n", into buf (NUL-terminated, truncated to
+ * len); bytes is the algorithmic HBM traffic of the streaming passes of the
+ * L-BFGS (each live site's elements once per vector read or written; 0 for
+ * kernels not counted); it synchronises the stream and returns the number
+ * of bytes needed. */
 long long plm_kernel_launches(void);
 plm_status plm_profile(plm_ctx *ctx, int enable);
 int plm_profile_report(plm_ctx *ctx, char *buf, int len);

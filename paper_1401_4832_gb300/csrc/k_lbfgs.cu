@@ -586,31 +586,56 @@ cudaError_t launch_lbfgs_init(SiteState *ss, const double *f, const float *g, co
 }
 
 template <int M>
-static void direction_m(SiteState *ss, const float *g, float *dir, const float *S,
-                        const float *Y, const LbLayout &L, double *part, cudaStream_t st)
+static void dir_dots_m(SiteState *ss, const float *S, const float *Y, const LbLayout &L,
+                       double *part, cudaStream_t st)
 {
     k_dir_dots<M><<<L.nchunks, LB_THREADS, 0, st>>>(ss, S, Y, L.si, L.ci, L.vec4, part);
     k_dir_solve<M><<<L.nsites, 32, 0, st>>>(ss, part, L.si);
+}
+
+template <int M>
+static void dir_apply_m(SiteState *ss, const float *g, float *dir, const float *S,
+                        const float *Y, const LbLayout &L, double *part, cudaStream_t st)
+{
     k_dir_apply<M><<<L.nchunks, LB_THREADS, 0, st>>>(ss, g, S, Y, dir, L.si, L.ci, L.vec4, part);
 }
 
-cudaError_t launch_lbfgs_direction(SiteState *ss, const float *g, float *dir,
+cudaError_t launch_lbfgs_dir_dots(SiteState *ss, const float *S_hist, const float *Y_hist,
+                                  const LbLayout &L, const SolveParams &p, double *part,
+                                  cudaStream_t st)
+{
+    switch (p.m) {
+    case 1: dir_dots_m<1>(ss, S_hist, Y_hist, L, part, st); break;
+    case 2: dir_dots_m<2>(ss, S_hist, Y_hist, L, part, st); break;
+    case 3: dir_dots_m<3>(ss, S_hist, Y_hist, L, part, st); break;
+    case 4: dir_dots_m<4>(ss, S_hist, Y_hist, L, part, st); break;
+    case 5: dir_dots_m<5>(ss, S_hist, Y_hist, L, part, st); break;
+    case 6: dir_dots_m<6>(ss, S_hist, Y_hist, L, part, st); break;
+    case 7: dir_dots_m<7>(ss, S_hist, Y_hist, L, part, st); break;
+    case 8: dir_dots_m<8>(ss, S_hist, Y_hist, L, part, st); break;
+    default: return cudaErrorInvalidValue;
+    }
+    count_launches(2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lbfgs_dir_apply(SiteState *ss, const float *g, float *dir,
                                    const float *S_hist, const float *Y_hist, const LbLayout &L,
                                    const SolveParams &p, double *part, cudaStream_t st)
 {
     switch (p.m) {
-    case 1: direction_m<1>(ss, g, dir, S_hist, Y_hist, L, part, st); break;
-    case 2: direction_m<2>(ss, g, dir, S_hist, Y_hist, L, part, st); break;
-    case 3: direction_m<3>(ss, g, dir, S_hist, Y_hist, L, part, st); break;
-    case 4: direction_m<4>(ss, g, dir, S_hist, Y_hist, L, part, st); break;
-    case 5: direction_m<5>(ss, g, dir, S_hist, Y_hist, L, part, st); break;
-    case 6: direction_m<6>(ss, g, dir, S_hist, Y_hist, L, part, st); break;
-    case 7: direction_m<7>(ss, g, dir, S_hist, Y_hist, L, part, st); break;
-    case 8: direction_m<8>(ss, g, dir, S_hist, Y_hist, L, part, st); break;
+    case 1: dir_apply_m<1>(ss, g, dir, S_hist, Y_hist, L, part, st); break;
+    case 2: dir_apply_m<2>(ss, g, dir, S_hist, Y_hist, L, part, st); break;
+    case 3: dir_apply_m<3>(ss, g, dir, S_hist, Y_hist, L, part, st); break;
+    case 4: dir_apply_m<4>(ss, g, dir, S_hist, Y_hist, L, part, st); break;
+    case 5: dir_apply_m<5>(ss, g, dir, S_hist, Y_hist, L, part, st); break;
+    case 6: dir_apply_m<6>(ss, g, dir, S_hist, Y_hist, L, part, st); break;
+    case 7: dir_apply_m<7>(ss, g, dir, S_hist, Y_hist, L, part, st); break;
+    case 8: dir_apply_m<8>(ss, g, dir, S_hist, Y_hist, L, part, st); break;
     default: return cudaErrorInvalidValue;
     }
     k_dir_finish<<<L.nsites, 32, 0, st>>>(ss, part, L.si);
-    count_launches(4);
+    count_launches(2);
     return cudaGetLastError();
 }
 
@@ -626,17 +651,25 @@ cudaError_t launch_lbfgs_trial(SiteState *ss, const float *theta, const float *g
     return cudaGetLastError();
 }
 
-cudaError_t launch_lbfgs_linesearch(SiteState *ss, const double *f_data, float *theta, float *g,
-                                    const float *theta_t, const float *g_t, const float *dir,
-                                    float *S_hist, float *Y_hist, const LbLayout &L,
-                                    const SolveParams &p, double *part, const int *round_ptr,
-                                    int *counters, cudaStream_t st)
+cudaError_t launch_lbfgs_linesearch(SiteState *ss, const double *f_data, const float *g_t,
+                                    const float *dir, const LbLayout &L, const SolveParams &p,
+                                    double *part, const int *round_ptr, int *counters,
+                                    cudaStream_t st)
 {
     k_ls_dots<<<L.nchunks, LB_THREADS, 0, st>>>(ss, g_t, dir, L.si, L.ci, part);
     k_ls_decide<<<L.nsites, 32, 0, st>>>(ss, f_data, part, L.si, p, round_ptr, counters);
+    count_launches(2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lbfgs_commit(const SiteState *ss, float *theta, float *g,
+                                const float *theta_t, const float *g_t, float *S_hist,
+                                float *Y_hist, const LbLayout &L, double *part,
+                                const int *round_ptr, cudaStream_t st)
+{
     k_commit<<<L.nchunks, LB_THREADS, 0, st>>>(ss, theta, g, theta_t, g_t, S_hist, Y_hist, L.si,
                                                 L.ci, L.vec4, round_ptr, part);
-    count_launches(3);
+    count_launches(1);
     return cudaGetLastError();
 }
 
@@ -645,6 +678,7 @@ __global__ void k_round_inc(int *round_ptr, int *counters)
 {
     *round_ptr += 1;
     counters[0] = 0;  // sites still searching after this round
+    counters[1] = 0;  // sites that accept a step in this round and iterate on
 }
 }  // namespace
 

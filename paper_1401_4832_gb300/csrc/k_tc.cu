@@ -911,7 +911,6 @@ int tc_supported()
 
 cudaError_t launch_tc_prepare(TcBatch &b, void *const *scratch, cudaStream_t st)
 {
-    int tl = 0, tg = 0;
     for (int i = 0; i < b.nfam; ++i) {
         FamDesc &F = b.f[i];
         F.BP = tc_padded_B(F.B);
@@ -931,8 +930,6 @@ cudaError_t launch_tc_prepare(TcBatch &b, void *const *scratch, cudaStream_t st)
         k_msa_transpose<<<(unsigned)((nT + 255) / 256), 256, 0, st>>>(F.msa, F.B, F.N, F.BP, msaT);
         count_launches(1);
     }
-    (void)tl;
-    (void)tg;
     return cudaGetLastError();
 }
 

@@ -27,6 +27,7 @@ struct DevBuf {
 struct ProfRecord {
     const char *name;
     cudaEvent_t a, b;
+    double bytes;  // algorithmic bytes the bracketed kernels move (0: not counted)
 };
 
 struct plm_ctx {
@@ -64,8 +65,9 @@ cudaEvent_t take_event(plm_ctx *c)
 struct ProfScope {
     plm_ctx *c;
     const char *name;
+    double bytes;
     cudaEvent_t a = nullptr;
-    ProfScope(plm_ctx *c_, const char *n) : c(c_), name(n)
+    ProfScope(plm_ctx *c_, const char *n, double bytes_ = 0.0) : c(c_), name(n), bytes(bytes_)
     {
         if (c->prof) {
             a = take_event(c);
@@ -77,7 +79,7 @@ struct ProfScope {
         if (c->prof && a) {
             cudaEvent_t b = take_event(c);
             cudaEventRecord(b, c->stream);
-            c->prof_records.push_back({name, a, b});
+            c->prof_records.push_back({name, a, b, bytes});
         }
     }
 };
@@ -99,7 +101,7 @@ void prof_stop(void *ctx, const char *name, void *start)
     plm_ctx *c = (plm_ctx *)ctx;
     cudaEvent_t b = take_event(c);
     cudaEventRecord(b, c->stream);
-    c->prof_records.push_back({name, (cudaEvent_t)start, b});
+    c->prof_records.push_back({name, (cudaEvent_t)start, b, 0.0});
 }
 }  // namespace plm
 
@@ -300,7 +302,9 @@ plm_status build_lbfgs_tables(plm_ctx *ctx, Problem &P)
     std::vector<ChunkInfo> ci;
     for (size_t f = 0; f < P.fam.size(); ++f) {
         const Fam &F = P.fam[f];
-        const int len4 = (int)(F.d.site_elems() / 4);
+        // the q state rows of the site; its padding rows (Q..QP-1) stay zero in
+        // theta and are never streamed
+        const int len4 = Q * F.d.KP / 4;
         const int nch = (len4 + LB_CHUNK4 - 1) / LB_CHUNK4;
         for (int r = 0; r < F.d.N; ++r) {
             SiteInfo x;
@@ -635,19 +639,67 @@ plm_status solve_core(plm_ctx *ctx, Problem &P, const plm_opts &o, std::vector<S
 
     int *hc = ctx->host_counters;
     int *round_ptr = (int *)cnt + 8;  // device round counter (commit matching)
-    // the per-iteration launches: eagerly, or replayed from two CUDA graphs
-    auto direction_step = [&]() -> plm_status {
-        CK(cudaMemsetAsync(cnt, 0, 2 * sizeof(int), st));
-        ProfScope ps(ctx, "lbfgs_direction");
-        CK(launch_lbfgs_direction((SiteState *)sst, (const float *)g, (float *)dir,
-                                  (const float *)Sh, (const float *)Yh, P.L, p, (double *)part,
-                                  st));
+    // One round advances every live site by one evaluation: sites whose last
+    // trial was accepted (READY) first form their next direction, then every
+    // searching site takes its trial point, all trial points are evaluated
+    // together and each site's line search decides.  A site never waits for
+    // the line searches of other sites, and its iterates do not depend on
+    // them (each site's objective involves only its own row block), so the
+    // solve needs about max over sites of that site's evaluations rounds.
+    // The round runs eagerly or is replayed from one CUDA graph.
+    // algorithmic bytes of the passes of one round, from the site states at
+    // its start (profiling only: each pass streams the elements of the sites
+    // it acts on, once per vector it reads or writes)
+    struct RoundBytes {
+        double dots = 0, apply = 0, trial = 0, ls = 0;
+    } rb;
+    std::vector<SiteState> snap;
+    std::vector<double> site_bytes;  // 4 x streamed elements of each site
+    if (ctx->prof) {
+        snap.resize(P.nsites);
+        for (const auto &F : P.fam)
+            for (int r = 0; r < F.d.N; ++r) site_bytes.push_back(4.0 * Q * F.d.KP);
+    }
+    const double split_b = o.prec == PLM_SPLIT_BF16 ? 1.0 : 0.0;  // hi + lo: 2 + 2 B an element
+    auto count_round = [&]() -> plm_status {
+        CK(cudaMemcpyAsync(snap.data(), sst, snap.size() * sizeof(SiteState),
+                           cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        rb = RoundBytes{};
+        for (int r = 0; r < P.nsites; ++r) {
+            const SiteState &x = snap[r];
+            const double e = site_bytes[r];
+            if (x.status == SITE_READY) {
+                rb.dots += 2.0 * x.hist * e;          // S_j, Y_j (y_n among them)
+                rb.apply += (2.0 * x.hist + 2.0) * e;  // g, S_j, Y_j in; d out
+            }
+            if (x.status == SITE_READY || x.status == SITE_SEARCHING) {
+                rb.trial += (3.0 + split_b) * e;  // theta, d in; theta_t (+ hi, lo) out
+                rb.ls += 2.0 * e;                 // g_t, d in
+            }
+        }
         return PLM_OK;
     };
+    int commit_rec = -1;  // profile record of this round's commit pass
     auto round_step = [&]() -> plm_status {
+        if (ctx->prof) {
+            plm_status s2 = count_round();
+            if (s2) return s2;
+        }
         CK(launch_round_begin(round_ptr, (int *)cnt, st));
         {
-            ProfScope ps(ctx, "lbfgs_trial");
+            ProfScope ps(ctx, "lbfgs_dir_dots", rb.dots);
+            CK(launch_lbfgs_dir_dots((SiteState *)sst, (const float *)Sh, (const float *)Yh, P.L,
+                                     p, (double *)part, st));
+        }
+        {
+            ProfScope ps(ctx, "lbfgs_dir_apply", rb.apply);
+            CK(launch_lbfgs_dir_apply((SiteState *)sst, (const float *)g, (float *)dir,
+                                      (const float *)Sh, (const float *)Yh, P.L, p,
+                                      (double *)part, st));
+        }
+        {
+            ProfScope ps(ctx, "lbfgs_trial", rb.trial);
             CK(launch_lbfgs_trial((SiteState *)sst, (const float *)theta, (const float *)g,
                                   (float *)dir, (float *)theta_t, (__nv_bfloat16 *)hi,
                                   (__nv_bfloat16 *)lo, P.L, p, (double *)part, st));
@@ -659,58 +711,74 @@ plm_status solve_core(plm_ctx *ctx, Problem &P, const plm_opts &o, std::vector<S
                                  (const uint8_t *)active);
         if (s2) return s2;
         {
-            ProfScope ps(ctx, "lbfgs_linesearch");
-            CK(launch_lbfgs_linesearch((SiteState *)sst, (const double *)fdat, (float *)theta,
-                                       (float *)g, (const float *)theta_t, (const float *)g_t,
-                                       (const float *)dir, (float *)Sh, (float *)Yh, P.L, p,
-                                       (double *)part, round_ptr, (int *)cnt, st));
+            ProfScope ps(ctx, "lbfgs_linesearch", rb.ls);
+            CK(launch_lbfgs_linesearch((SiteState *)sst, (const double *)fdat, (const float *)g_t,
+                                       (const float *)dir, P.L, p, (double *)part, round_ptr,
+                                       (int *)cnt, st));
         }
+        {
+            ProfScope ps(ctx, "lbfgs_commit");
+            CK(launch_lbfgs_commit((const SiteState *)sst, (float *)theta, (float *)g,
+                                   (const float *)theta_t, (const float *)g_t, (float *)Sh,
+                                   (float *)Yh, P.L, (double *)part, round_ptr, st));
+        }
+        if (ctx->prof) commit_rec = (int)ctx->prof_records.size() - 1;
         CK(cudaMemcpyAsync(hc, cnt, 5 * sizeof(int), cudaMemcpyDeviceToHost, st));
         return PLM_OK;
     };
-    cudaGraphExec_t g_dir = nullptr, g_round = nullptr;
+    cudaGraphExec_t g_round = nullptr;
     const bool use_graph = o.use_graph && st != nullptr && !ctx->prof;
+    int graph_kernels = 0;  // kernels one replay of the round graph launches
     if (use_graph) {
         cudaGraph_t gr;
-        for (int k = 0; k < 2; ++k) {
-            CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-            plm_status s2 = k == 0 ? direction_step() : round_step();
-            cudaError_t e = cudaStreamEndCapture(st, &gr);
-            if (s2) return s2;
-            if (e) return cuda_fail(ctx, e, "cudaStreamEndCapture");
-            e = cudaGraphInstantiate(k == 0 ? &g_dir : &g_round, gr, 0);
-            cudaGraphDestroy(gr);
-            if (e) return cuda_fail(ctx, e, "cudaGraphInstantiate");
-        }
+        const long long before = g_launches.load();
+        CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        plm_status s2 = round_step();
+        cudaError_t e = cudaStreamEndCapture(st, &gr);
+        // capture records the launches without running them: count replays instead
+        graph_kernels = (int)(g_launches.load() - before);
+        count_launches(-graph_kernels);
+        if (s2) return s2;
+        if (e) return cuda_fail(ctx, e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&g_round, gr, 0);
+        cudaGraphDestroy(gr);
+        if (e) return cuda_fail(ctx, e, "cudaGraphInstantiate");
     }
     struct GraphGuard {
-        cudaGraphExec_t a, b;
+        cudaGraphExec_t a;
         ~GraphGuard()
         {
             if (a) cudaGraphExecDestroy(a);
-            if (b) cudaGraphExecDestroy(b);
         }
-    } guard{g_dir, g_round};
-    for (int it = 0; it < o.max_iter; ++it) {
-        if (use_graph) CK(cudaGraphLaunch(g_dir, st));
-        else {
-            s = direction_step();
+    } guard{g_round};
+    // every site stops within max_iter iterations of at most max_ls trials
+    const long long max_rounds = (long long)o.max_iter * o.max_ls + 1;
+    for (long long rd = 0; rd < max_rounds; ++rd) {
+        if (use_graph) {
+            CK(cudaGraphLaunch(g_round, st));
+            count_launches(graph_kernels);
+        } else {
+            s = round_step();
             if (s) return s;
         }
-        for (int ls = 0; ls < o.max_ls + 1; ++ls) {
-            if (use_graph) CK(cudaGraphLaunch(g_round, st));
-            else {
-                s = round_step();
-                if (s) return s;
-            }
-            evals++;
+        evals++;
+        CK(cudaStreamSynchronize(st));
+        if (ctx->prof && commit_rec >= 0) {
+            // committed sites: theta_t, theta, g_t, g in; S, Y, theta, g out
+            CK(cudaMemcpyAsync(snap.data(), sst, snap.size() * sizeof(SiteState),
+                               cudaMemcpyDeviceToHost, st));
+            int rd_now = 0;
+            CK(cudaMemcpyAsync(&rd_now, round_ptr, sizeof(int), cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
-            if (hc[4])
-                return fail(ctx, PLM_ETIMEOUT, "tensor-core pipeline wait timed out (code 0x%x)",
-                            hc[4]);
-            if (hc[0] == 0) break;
+            double cb = 0.0;
+            for (int r = 0; r < P.nsites; ++r)
+                if (snap[r].commit_round == rd_now) cb += 8.0 * site_bytes[r];
+            ctx->prof_records[commit_rec].bytes = cb;
         }
-        if (hc[1] == 0) break;  // no site left to iterate
+        if (hc[4])
+            return fail(ctx, PLM_ETIMEOUT, "tensor-core pipeline wait timed out (code 0x%x)",
+                        hc[4]);
+        if (hc[0] == 0 && hc[1] == 0) break;  // no site searching or about to iterate
     }
 
     for (size_t f = 0; f < nf; ++f)
@@ -841,24 +909,27 @@ int plm_profile_report(plm_ctx *c, char *buf, int len)
     if (!c) return -1;
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
-    std::map<std::string, std::pair<long long, double>> agg;
+    struct Agg {
+        long long n = 0;
+        double ms = 0.0, bytes = 0.0;
+    };
+    std::map<std::string, Agg> agg;
     std::vector<std::string> order;
     for (auto &r : c->prof_records) {
         float ms = 0.0f;
         cudaEventElapsedTime(&ms, r.a, r.b);
         auto it = agg.find(r.name);
-        if (it == agg.end()) {
-            order.push_back(r.name);
-            agg[r.name] = {1, ms};
-        } else {
-            it->second.first++;
-            it->second.second += ms;
-        }
+        if (it == agg.end()) order.push_back(r.name);
+        Agg &x = agg[r.name];
+        x.n++;
+        x.ms += ms;
+        x.bytes += r.bytes;
     }
     std::string out;
     char line[256];
     for (auto &n : order) {
-        snprintf(line, sizeof line, "%s %lld %.6f\n", n.c_str(), agg[n].first, agg[n].second);
+        snprintf(line, sizeof line, "%s %lld %.6f %.0f\n", n.c_str(), agg[n].n, agg[n].ms,
+                 agg[n].bytes);
         out += line;
     }
     if (buf && len > 0) {

@@ -155,7 +155,7 @@ constexpr int LB_CHUNK4 = 2048;
 
 struct SiteInfo {
     long long off4;  // float4 offset of the segment in every arena vector
-    int len4;        // float4 count of the segment (QP * KP / 4)
+    int len4;        // float4 count streamed: the q state rows (Q * KP / 4)
     int KP;          // padded columns of the family
     int NQ;          // N_f * Q: the field column
     int chunk0;      // first chunk of the site
@@ -180,26 +180,33 @@ cudaError_t launch_lbfgs_init(SiteState *ss, const double *f, const float *g,
                               const LbLayout &L, const SolveParams &p, double *part,
                               cudaStream_t st);
 // direction d = -H g (compact representation) and line-search set-up
-cudaError_t launch_lbfgs_direction(SiteState *ss, const float *g, float *dir,
+// (in two passes: dots = S'y_n, Y'y_n and the small solve; apply = d and
+// the line-search set-up; sites not READY are skipped)
+cudaError_t launch_lbfgs_dir_dots(SiteState *ss, const float *S_hist, const float *Y_hist,
+                                  const LbLayout &L, const SolveParams &p, double *part,
+                                  cudaStream_t st);
+cudaError_t launch_lbfgs_dir_apply(SiteState *ss, const float *g, float *dir,
                                    const float *S_hist, const float *Y_hist,
-                                   const LbLayout &L, const SolveParams &p,
-                                   double *part, cudaStream_t st);
+                                   const LbLayout &L, const SolveParams &p, double *part,
+                                   cudaStream_t st);
 cudaError_t launch_lbfgs_trial(SiteState *ss, const float *theta,
                                const float *g, float *dir, float *theta_t,
                                __nv_bfloat16 *hi, __nv_bfloat16 *lo,
                                const LbLayout &L, const SolveParams &p, double *part,
                                cudaStream_t st);
 // consumes f_data[site] (data part of the objective at theta_t) and g_t; the
-// decision is taken per site; accepted steps are committed in the same call
-// (S, Y, theta, g updated).  counters[0] += #sites still searching,
+// decision is taken per site.  counters[0] += #sites still searching,
 // counters[1] += #sites that became ready for a new direction.
-cudaError_t launch_lbfgs_linesearch(SiteState *ss, const double *f_data,
-                                    float *theta, float *g,
-                                    const float *theta_t, const float *g_t,
-                                    const float *dir, float *S_hist,
-                                    float *Y_hist, const LbLayout &L,
-                                    const SolveParams &p, double *part,
-                                    const int *round_ptr, int *counters, cudaStream_t st);
+cudaError_t launch_lbfgs_linesearch(SiteState *ss, const double *f_data, const float *g_t,
+                                    const float *dir, const LbLayout &L, const SolveParams &p,
+                                    double *part, const int *round_ptr, int *counters,
+                                    cudaStream_t st);
+// commits the steps accepted in this round: S, Y ring slots, theta <- theta_t,
+// g <- g_t
+cudaError_t launch_lbfgs_commit(const SiteState *ss, float *theta, float *g,
+                                const float *theta_t, const float *g_t, float *S_hist,
+                                float *Y_hist, const LbLayout &L, double *part,
+                                const int *round_ptr, cudaStream_t st);
 // start of a line-search round: ++*round_ptr, counters[0] = 0
 cudaError_t launch_round_begin(int *round_ptr, int *counters, cudaStream_t st);
 // active[site] = 1 if the site is in a line search (its trial point needs an
