@@ -42,9 +42,10 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32-cmp", action="store_true",
                     help="skip timing the plain FP32 path beside the split-bf16 one")
-    ap.add_argument("--workload", default="family", choices=["family", "batch", "scale"],
-                    help="family: the benchmark line; batch (64 families) and scale "
-                         "(N=500, B=50000): separate measurements")
+    ap.add_argument("--workload", default="family", choices=["family", "batch", "scale", "eval"],
+                    help="family: the benchmark line; batch (64 families), scale "
+                         "(N=500, B=50000) and eval (full objective+gradient evaluations "
+                         "of the family at a random point): separate measurements")
     ap.add_argument("--cpu-sites", type=int, default=0,
                     help="sites per CPU-oracle sample (0 = one per host core, at most 16)")
     return ap.parse_args()
@@ -225,8 +226,52 @@ def run_scale(args):
                       "results": out}), flush=True)
 
 
+def run_eval(args):
+    """Full evaluations (every site) of the family workload at a random
+    point: device time per evaluation with L2 flushed before each (also the
+    small case the kernel captures run on)."""
+    import numpy as np
+    import torch
+    from paper_1401_4832_gb300 import api, synth
+    fam = synth.protein_family()
+    S = torch.from_numpy(fam.msa).cuda()
+    stream = torch.cuda.Stream()
+    ctx = api.Context(0, stream)
+    m, w, beff = api.msa_reweight(ctx, S)
+    N = fam.N
+    rng = np.random.default_rng(0)
+    h = torch.from_numpy(rng.normal(0, 0.05, (N, 21)).astype(np.float32)).cuda()
+    J = rng.normal(0, 0.05, (N, 21, N, 21)).astype(np.float32)
+    for r in range(N):
+        J[r, :, r, :] = 0
+    J = torch.from_numpy(J).cuda()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    prec = "split_bf16" if args.prec == "auto" else args.prec
+    out = {}
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            api.plm_site_objective_grad(ctx, S, w, beff, h, J, prec=prec)
+        times = []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            f, gh, gJ = api.plm_site_objective_grad(ctx, S, w, beff, h, J, prec=prec)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1) / 1000.0)
+    t = statistics.mean(times)
+    print(json.dumps({"workload": "eval: " + WORKLOAD, "precision": prec, "steps": args.steps,
+                      "s_per_eval": t, "evals_per_s": 1.0 / t,
+                      "f_sum": float(f.double().sum())}), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse_args()
+    if args.workload == "eval":
+        return run_eval(args)
     if args.workload == "batch":
         return run_batch(args)
     if args.workload == "scale":

@@ -7,8 +7,8 @@
 // site keeps its own curvature pairs, step length and stopping state.
 //
 // Vectors are FP32.  Inner products are accumulated per thread in
-// double-float (error-free FP32 products and sums, ~44 significant bits),
-// then reduced across threads and chunks in FP64; every scalar of the
+// double-float (FP32 arithmetic, ~44 significant bits; each float4's four
+// products summed by FMAs, then added without error), then reduced across threads and chunks in FP64; every scalar of the
 // recursion and of the line search is FP64.  Each site's segment is cut
 // into chunks; one CTA per (chunk, site) streams the vectors and writes
 // partial sums, and a one-warp-per-site kernel reduces them in a fixed
@@ -70,6 +70,16 @@ __device__ __forceinline__ double chunk_sum(const double *part, const SiteInfo &
     double t = 0.0;
     for (int c = lane; c < si.nchunks; c += 32) t += part[(size_t)(si.chunk0 + c) * LB_PART + k];
     return warp_sum_d(t);
+}
+
+// the same total for one slot, summed by a single thread in chunk order (a
+// warp sums several slots at once this way)
+__device__ __forceinline__ double lane_chunk_sum(const double *part, const SiteInfo &si, int k)
+{
+    const double *q = part + (size_t)si.chunk0 * LB_PART + k;
+    double t = 0.0;
+    for (int c = 0; c < si.nchunks; ++c) t += q[(size_t)c * LB_PART];
+    return t;
 }
 
 struct Chunk {
@@ -185,15 +195,10 @@ __global__ void k_dir_solve(SiteState *ss, const double *part, const SiteInfo *s
     const int hist = s.hist, head = s.head;
     const int lane = threadIdx.x;
     if (hist > 0) {
-        for (int k = 0; k < 2 * M; ++k) {
-            const double t = chunk_sum(part, si[r], k);
-            if (lane == 0) tot[k] = t;
-        }
-        const double sg = chunk_sum(part, si[r], LB_SLOT_SG);
-        const double yg = chunk_sum(part, si[r], LB_SLOT_YG);
-        if (lane == 0) {
-            tot[2 * M] = sg;
-            tot[2 * M + 1] = yg;
+        // slots 0..2M-1: S'y_n, Y'y_n; then s_n'g_new and y_n'g_old
+        if (lane < 2 * M + 2) {
+            const int k = lane < 2 * M ? lane : (lane == 2 * M ? LB_SLOT_SG : LB_SLOT_YG);
+            tot[lane] = lane_chunk_sum(part, si[r], k);
         }
         for (int k = lane; k < M * M; k += 32) {
             SY[k / M][k % M] = s.SY[k / M][k % M];
@@ -472,11 +477,11 @@ __global__ void k_ls_decide(SiteState *ss, const double *__restrict__ f_data, co
     const int r = blockIdx.x;
     SiteState &s = ss[r];
     if (s.status != SITE_SEARCHING) return;
-    const double pj = chunk_sum(part, si[r], 0);
-    const double ph = chunk_sum(part, si[r], 1);
-    const double dgt = chunk_sum(part, si[r], 2);
-    const double gn2 = chunk_sum(part, si[r], 3);
+    __shared__ double t4[4];
+    if (threadIdx.x < 4) t4[threadIdx.x] = lane_chunk_sum(part, si[r], threadIdx.x);
+    __syncwarp();
     if (threadIdx.x != 0) return;
+    const double pj = t4[0], ph = t4[1], dgt = t4[2], gn2 = t4[3];
     s.pen_t = p.lambda_h * ph + p.lambda_Jp * pj;
     const double ft = f_data[r] + s.pen_t;
     const double a = s.alpha, f0 = s.f0, dg0 = s.dg0;

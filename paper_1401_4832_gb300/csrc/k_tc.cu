@@ -221,6 +221,36 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v)
     for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
 }
 
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v)
+{
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                   "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+// sum over the warp of a float, carried as an unevaluated pair (hi, lo):
+// each step adds the partner's pair with Knuth's two-sum, so the total keeps
+// about 44 bits whatever the magnitudes
+__device__ __forceinline__ double warp_sum_pair(float x)
+{
+    float hi = x, lo = 0.0f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float bh = __shfl_xor_sync(0xffffffffu, hi, o);
+        const float bl = __shfl_xor_sync(0xffffffffu, lo, o);
+        const float t = __fadd_rn(hi, bh);
+        const float bp = __fsub_rn(t, hi);
+        const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(bh, bp));
+        hi = t;
+        lo = __fadd_rn(__fadd_rn(lo, bl), e);
+    }
+    return (double)hi + (double)lo;
+}
+
 __device__ __forceinline__ void tmem_wait_ld()
 {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
@@ -265,9 +295,10 @@ __device__ __forceinline__ int family_of(const TcBatch &b, int tile, bool grad)
     return f;
 }
 
-__device__ __forceinline__ void epi_bar2()
+// the eight epilogue warps of the logits kernel
+__device__ __forceinline__ void epi_bar_all()
 {
-    asm volatile("bar.sync 2, 128;" ::: "memory");
+    asm volatile("bar.sync 3, 256;" ::: "memory");
 }
 
 // tile t of the logits grid: family, sequence tile, site tile
@@ -293,18 +324,19 @@ __device__ __forceinline__ bool sites_active(const FamDesc &F, int r_lo, int r_h
 // ---------------------------------------------------------------- logits
 // Persistent: one CTA per SM walks the tile list (stride gridDim.x).  Warp
 // 0: TMA for Theta hi/lo; warp 1: TMEM (2 x 256 columns) and MMA issue;
-// warps 2-5: one-hot producers; warps 6-9: epilogue.  The accumulator is
-// double-buffered, so a tile's epilogue overlaps the next tile's main loop.
-__global__ void __launch_bounds__(320, 1)
+// warps 2-5: one-hot producers; warps 6-13: epilogue, two groups of four
+// warps (one per TMEM lane quarter) that take alternate sites of a tile.
+// The accumulator is double-buffered, so a tile's epilogue overlaps the
+// next tile's main loop.
+constexpr int LG_THREADS = 448;
+constexpr int LG_EPI = 256;  // epilogue threads
+__global__ void __launch_bounds__(LG_THREADS, 1)
 k_tc_logits(const __grid_constant__ LogitsParams P, int *__restrict__ err)
 {
     extern __shared__ uint8_t dsmem[];
     uint8_t *smem = align1024(dsmem);
     const int LGS = P.sites, NST = P.stages, LGSTAGE = P.stage_bytes;
     const int LGB = P.ncols * TC_BK * 2;
-    // epilogue slab: the residual rows of two sites, [48][128] bf16, hi then lo
-    __nv_bfloat16 *slab_hi = (__nv_bfloat16 *)(smem + NST * LGSTAGE);
-    __nv_bfloat16 *slab_lo = slab_hi + 2 * QP * TC_M;
     __shared__ __align__(8) uint64_t full_b[MAX_STAGES], full_a[MAX_STAGES], empty_[MAX_STAGES];
     __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2], mma_done;
     __shared__ uint32_t tmem_sh;
@@ -321,7 +353,7 @@ k_tc_logits(const __grid_constant__ LogitsParams P, int *__restrict__ err)
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(&acc_full[a], 1);
-            mbar_init(&acc_empty[a], 128);
+            mbar_init(&acc_empty[a], LG_EPI);
         }
         mbar_init(&mma_done, 1);
         abort_sh = 0;
@@ -473,12 +505,13 @@ k_tc_logits(const __grid_constant__ LogitsParams P, int *__restrict__ err)
             }
         }
     } else {
-        // ---- epilogue: one sequence per thread (its TMEM lane).  Residual
-        // rows of two sites at a time are staged in the slab and written out
-        // with 16-byte stores.
+        // ---- epilogue: one sequence per thread (its TMEM lane); group g
+        // takes sites g, g + 2, ... of the tile.  Residual rows go straight
+        // to global memory: for a fixed state row the 32 lanes of a warp
+        // write 32 consecutive sequences (64 contiguous bytes).
         const int q4 = warp & 3;
+        const int g = (warp - 6) >> 2;
         const int er = q4 * 32 + lane;
-        const int t128 = threadIdx.x - 192;
         int ti = 0;
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
             int fi, tb, tr;
@@ -487,77 +520,78 @@ k_tc_logits(const __grid_constant__ LogitsParams P, int *__restrict__ err)
             const int r0 = tr * LGS;
             if (!sites_active(F, r0, r0 + LGS - 1)) continue;
             const int a = ti & 1, use = ti >> 1;
-            const bool ok = mbar_wait(&acc_full[a], (uint32_t)(use & 1), &abort_sh, err, ERR_TIMEOUT_EPI);
-            tc_fence_after();
             const int b0 = tb * TC_M, row0 = r0 * QP, BP = F.BP;
             const int eb = b0 + er;
             const bool ev = eb < F.B;
+            // operands of the epilogue, fetched while the MMAs run
             const float wb = ev ? F.w[eb] : 0.0f;
             const float scale = (float)((double)wb * F.inv_beff);
-            const uint32_t tl = tmem + a * TMEM_COLS + ((uint32_t)(q4 * 32) << 16);
-#pragma unroll 1
-            for (int jp = 0; jp < LGS / 2; ++jp) {
-                float v[48];
-                tmem_ld16(tl + jp * 48, v);
-                tmem_ld16(tl + jp * 48 + 16, v + 16);
-                tmem_ld16(tl + jp * 48 + 32, v + 32);
-                tmem_wait_ld();
-                if (jp == LGS / 2 - 1) {
-                    // all tensor-memory reads of this tile are done: release it
-                    tc_fence_before();
-                    mbar_arrive(&acc_empty[a]);
-                }
+            int sr[(MAX_LG_SITES + 1) / 2];
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int j = 2 * jp + h;
-                    const int r = r0 + j;
-                    const float *l = v + 24 * h;
-                    float mx = l[0];
-#pragma unroll
-                    for (int s2 = 1; s2 < Q; ++s2) mx = fmaxf(mx, l[s2]);
-                    float z = 0.0f;
-#pragma unroll
-                    for (int s2 = 0; s2 < Q; ++s2) z += __expf(l[s2] - mx);
-                    const float lse = mx + __logf(z);
-                    const int sr = (ev && r < F.N) ? F.msa[(size_t)eb * F.N + r] : -1;
-                    float lsr = 0.0f;
-#pragma unroll
-                    for (int s2 = 0; s2 < Q; ++s2)
-                        if (s2 == sr) lsr = l[s2];
-                    double contrib = 0.0;
-                    if (ev && r < F.N && ok) contrib = (double)wb * (double)(lsr - lse);
-#pragma unroll
-                    for (int s2 = 0; s2 < QP; ++s2) {
-                        float dv = 0.0f;
-                        if (s2 < Q && ev && r < F.N)
-                            dv = scale * (__expf(l[s2] - lse) - (s2 == sr ? 1.0f : 0.0f));
-                        const __nv_bfloat16 hi = __float2bfloat16_rn(dv);
-                        slab_hi[(h * QP + s2) * TC_M + er] = hi;
-                        slab_lo[(h * QP + s2) * TC_M + er] =
-                            __float2bfloat16_rn(dv - __bfloat162float(hi));
-                    }
-                    contrib = warp_sum_d(contrib);
-                    if (lane == 0) red[q4][j] = contrib;
-                }
-                epi_bar2();
-                // copy-out: 2 sites x 24 rows x 128 sequences, hi and lo
-                const int nrows = min(2 * QP, F.R - (row0 + jp * 2 * QP));
-                for (int e = t128; e < 2 * 2 * QP * 16; e += 128) {
-                    const int half = e / (2 * QP * 16);
-                    const int rem = e % (2 * QP * 16);
-                    const int row = rem / 16, c16 = rem % 16;
-                    if (!ok || row >= nrows) continue;
-                    const __nv_bfloat16 *src = (half ? slab_lo : slab_hi) + row * TC_M + c16 * 8;
-                    __nv_bfloat16 *dst = (half ? F.dt_lo : F.dt_hi) +
-                                         (size_t)(row0 + jp * 2 * QP + row) * BP + b0 + c16 * 8;
-                    *(uint4 *)dst = *(const uint4 *)src;
-                }
-                epi_bar2();
+            for (int u = 0; u < (MAX_LG_SITES + 1) / 2; ++u) {
+                const int r = r0 + g + 2 * u;
+                sr[u] = (g + 2 * u < LGS && r < F.N) ? (int)F.msaT[(size_t)r * BP + eb] : -1;
             }
-            if (t128 < LGS && r0 + t128 < F.N && ok)
-                F.partial[(size_t)tb * F.N + r0 + t128] =
-                    ((red[0][t128] + red[1][t128]) + red[2][t128]) + red[3][t128];
-            epi_bar2();
+            const bool ok = mbar_wait(&acc_full[a], (uint32_t)(use & 1), &abort_sh, err, ERR_TIMEOUT_EPI);
+            tc_fence_after();
+            const uint32_t tl = tmem + a * TMEM_COLS + ((uint32_t)(q4 * 32) << 16);
+            const int nmine = (LGS - g + 1) / 2;
+            if (nmine == 0) {
+                tc_fence_before();
+                mbar_arrive(&acc_empty[a]);
+            }
+#pragma unroll
+            for (int u = 0; u < (MAX_LG_SITES + 1) / 2; ++u) {
+                if (u < nmine) {
+                    const int j = g + 2 * u;
+                    const int r = r0 + j;
+                    const int srv = sr[u];
+                    float l[24];
+                    tmem_ld16(tl + j * QP, l);
+                    tmem_ld8(tl + j * QP + 16, l + 16);
+                    tmem_wait_ld();
+                    if (u == nmine - 1) {
+                        // this thread's last tensor-memory read of the tile
+                        tc_fence_before();
+                        mbar_arrive(&acc_empty[a]);
+                    }
+                    const bool live = ev && r < F.N && ok;
+                    // numerically stable log-softmax over the q states (Eq. condpfinal)
+                    float mx = l[0];
+    #pragma unroll
+                    for (int s2 = 1; s2 < Q; ++s2) mx = fmaxf(mx, l[s2]);
+                    float z = 0.0f, lsr = 0.0f;
+    #pragma unroll
+                    for (int s2 = 0; s2 < Q; ++s2) {
+                        if (s2 == srv) lsr = l[s2];
+                        l[s2] = __expf(l[s2] - mx);
+                        z += l[s2];
+                    }
+                    const float lse = mx + __logf(z);
+                    const float iz = __fdividef(1.0f, z);
+                    const double c = warp_sum_pair(live ? wb * (lsr - lse) : 0.0f);
+                    if (lane == 0) red[q4][j] = c;
+                    if (ok && r < F.N) {
+                        __nv_bfloat16 *dh = F.dt_hi + (size_t)(row0 + j * QP) * BP + eb;
+                        __nv_bfloat16 *dl = F.dt_lo + (size_t)(row0 + j * QP) * BP + eb;
+    #pragma unroll
+                        for (int s2 = 0; s2 < QP; ++s2) {
+                            float dv = 0.0f;
+                            if (s2 < Q && ev)
+                                dv = scale * (l[s2] * iz - (s2 == srv ? 1.0f : 0.0f));
+                            const __nv_bfloat16 hi = __float2bfloat16_rn(dv);
+                            dh[(size_t)s2 * BP] = hi;
+                            dl[(size_t)s2 * BP] = __float2bfloat16_rn(dv - __bfloat162float(hi));
+                        }
+                    }
+                }
+            }
+            epi_bar_all();
+            const int t256 = threadIdx.x - 192;
+            if (t256 < LGS && r0 + t256 < F.N && ok)
+                F.partial[(size_t)tb * F.N + r0 + t256] =
+                    ((red[0][t256] + red[1][t256]) + red[2][t256]) + red[3][t256];
+            epi_bar_all();
             ++ti;
         }
     }
@@ -933,7 +967,6 @@ cudaError_t launch_tc_prepare(TcBatch &b, void *const *scratch, cudaStream_t st)
     return cudaGetLastError();
 }
 
-constexpr int LG_SLAB = 2 * 2 * QP * TC_M * 2;  // two sites of residual rows, hi + lo
 
 int tc_stages(int stage_bytes, int slab_bytes)
 {
@@ -993,7 +1026,7 @@ cudaError_t launch_tc_eval(void *prof, const TcBatch &b_in, const TcConfig &cfg,
     lp.sites = cfg.lg_sites;
     lp.ncols = lg_ncols;
     lp.stage_bytes = LG_A_BYTES + 2 * lg_ncols * TC_BK * 2;
-    lp.stages = tc_stages(lp.stage_bytes, LG_SLAB);
+    lp.stages = tc_stages(lp.stage_bytes, 0);
     gp.ncols = cfg.gr_ncols;
     gp.stage_bytes = 2 * GR_A_BYTES + cfg.gr_ncols * TC_BK * 2;
     gp.stages = tc_stages(gp.stage_bytes, 0);
@@ -1009,7 +1042,7 @@ cudaError_t launch_tc_eval(void *prof, const TcBatch &b_in, const TcConfig &cfg,
         void *t0 = prof ? prof_start(prof) : nullptr;
         const int grid = std::min(tl, num_sms());
         if (grid > 0)
-            k_tc_logits<<<grid, 320, lp.stages * lp.stage_bytes + LG_SLAB + 1024, st>>>(lp, err);
+            k_tc_logits<<<grid, LG_THREADS, lp.stages * lp.stage_bytes + 1024, st>>>(lp, err);
         if (prof) prof_stop(prof, "tc_logits", t0);
         k_tc_finish<<<lp.b.nfam, 128, 0, st>>>(lp.b);
         count_launches(2);

@@ -50,16 +50,30 @@ __device__ __forceinline__ void block_sum2_d(double &a, double &b, double *red)
     b = tb;
 }
 
-// Double-float accumulator of products of FP32 numbers, in FP32 arithmetic.
-// Each product is split exactly into p + e (Dekker's two-product, with the
-// FMA giving the rounding error of a*b) and added to (hi, lo) with Knuth's
-// two-sum, so hi + lo carries about 44 significant bits -- FP64-class inner
-// products at FP32 throughput (the FP64 pipe of this GPU is ~1/64 of FP32).
+// Double-float accumulator (hi + lo, about 44 significant bits) of sums of
+// FP32 products, in FP32 arithmetic (the FP64 pipe of this GPU is ~1/64 of
+// FP32).  Terms enter through Knuth's two-sum, which adds them to (hi, lo)
+// without rounding error, so the length of the sum adds no error.
+//   df_fma  adds one product exactly: Dekker's two-product (the FMA gives
+//           the rounding error of a*b), then the two-sum.
+//   df_dot4 adds the four products of a float4 pair summed by an FMA chain:
+//           its error is at most 4u of the sum of their magnitudes (u = 2^-24),
+//           the order of the rounding already in the FP32 inputs, at a
+//           quarter of df_fma's instructions per element.
 // The _rn intrinsics keep the compiler from fusing or reassociating the
 // error-free transformations.
 struct DF {
     float hi = 0.0f, lo = 0.0f;
 };
+
+__device__ __forceinline__ void df_add(DF &s, float p)
+{
+    const float t = __fadd_rn(s.hi, p);
+    const float bp = __fsub_rn(t, s.hi);
+    const float err = __fadd_rn(__fsub_rn(s.hi, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+    s.hi = t;
+    s.lo = __fadd_rn(s.lo, err);
+}
 
 __device__ __forceinline__ void df_fma(DF &s, float a, float b)
 {
@@ -74,10 +88,8 @@ __device__ __forceinline__ void df_fma(DF &s, float a, float b)
 
 __device__ __forceinline__ void df_dot4(DF &s, const float4 a, const float4 b)
 {
-    df_fma(s, a.x, b.x);
-    df_fma(s, a.y, b.y);
-    df_fma(s, a.z, b.z);
-    df_fma(s, a.w, b.w);
+    const float p = fmaf(a.w, b.w, fmaf(a.z, b.z, fmaf(a.y, b.y, __fmul_rn(a.x, b.x))));
+    df_add(s, p);
 }
 
 __device__ __forceinline__ double df_value(const DF &s)
