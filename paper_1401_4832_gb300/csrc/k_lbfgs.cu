@@ -34,6 +34,10 @@
 // the line even where FP32 rounding makes differences of f unresolvable.
 // Sufficient decrease allows a noise band `noise * max(1, |f0|)` on f, or
 // is certified by phi'(alpha) <= c1 phi'(0) (convexity).
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "plm_device.cuh"
 #include "plm_internal.cuh"
 
@@ -43,23 +47,41 @@ namespace {
 
 constexpr int LB_THREADS = 256;
 
-// sum K per-thread values over the block (fixed order) and write them
+// sum K per-thread double-float values over the block (fixed order) and
+// write them as FP64: a butterfly of error-free FP32 pair additions inside
+// each warp, then one thread per value adds the warps' pairs in FP64.  The
+// block's threads all take part; the shared buffer is free again on return.
 template <int K>
-__device__ __forceinline__ void block_write(double (&v)[K], double *out)
+__device__ __forceinline__ void block_write(DF (&v)[K], double *out)
 {
-    __shared__ double red[LB_THREADS / 32][K];
+    __shared__ float rh[LB_THREADS / 32][K], rl[LB_THREADS / 32][K];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-    for (int k = 0; k < K; ++k) v[k] = warp_sum_d(v[k]);
-    if (lane == 0)
+    for (int k = 0; k < K; ++k) {
+        float hi = v[k].hi, lo = v[k].lo;
 #pragma unroll
-        for (int k = 0; k < K; ++k) red[wid][k] = v[k];
+        for (int o = 16; o > 0; o >>= 1) {
+            const float bh = __shfl_xor_sync(0xffffffffu, hi, o);
+            const float bl = __shfl_xor_sync(0xffffffffu, lo, o);
+            const float t = __fadd_rn(hi, bh);
+            const float bp = __fsub_rn(t, hi);
+            const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(bh, bp));
+            hi = t;
+            lo = __fadd_rn(__fadd_rn(lo, bl), e);
+        }
+        if (lane == 0) {
+            rh[wid][k] = hi;
+            rl[wid][k] = lo;
+        }
+    }
     __syncthreads();
     if (threadIdx.x < K) {
         double t = 0.0;
-        for (int w = 0; w < LB_THREADS / 32; ++w) t += red[w][threadIdx.x];
+        for (int w = 0; w < LB_THREADS / 32; ++w)
+            t += (double)rh[w][threadIdx.x] + (double)rl[w][threadIdx.x];
         out[threadIdx.x] = t;
     }
+    __syncthreads();
 }
 
 // fixed-order sum over the chunks of one site (one warp): returns the
@@ -87,32 +109,39 @@ struct Chunk {
     int site;
 };
 
-__device__ __forceinline__ Chunk chunk_of(const SiteInfo *si, const ChunkInfo *ci)
+__device__ __forceinline__ Chunk chunk_at(const SiteInfo *si, const ChunkInfo *ci, int c)
 {
-    const ChunkInfo c = ci[blockIdx.x];
+    const ChunkInfo x = ci[c];
     Chunk ch;
-    ch.site = c.site;
-    ch.base4 = (size_t)si[c.site].off4;
-    ch.e0 = (size_t)c.e0;
-    ch.e1 = (size_t)c.e1;
+    ch.site = x.site;
+    ch.base4 = (size_t)si[x.site].off4;
+    ch.e0 = (size_t)x.e0;
+    ch.e1 = (size_t)x.e1;
     return ch;
 }
 
-__device__ __forceinline__ double *part_rec(double *part)
+__device__ __forceinline__ double *part_rec(double *part, int c)
 {
-    return part + (size_t)blockIdx.x * LB_PART;
+    return part + (size_t)c * LB_PART;
 }
+
+__device__ __forceinline__ float4 f4z() { return make_float4(0.f, 0.f, 0.f, 0.f); }
 
 // ------------------------------------------------------------ start
 __global__ void __launch_bounds__(LB_THREADS)
-k_init_dots(const float *__restrict__ g, const SiteInfo *si, const ChunkInfo *ci, double *part)
+k_init_dots(const float *__restrict__ g, const SiteInfo *si, const ChunkInfo *ci, int nchunks,
+            double *part)
 {
-    const Chunk ch = chunk_of(si, ci);
-    const float4 *g4 = (const float4 *)g + ch.base4;
-    DF acc;
-    for (size_t e = ch.e0 + threadIdx.x; e < ch.e1; e += LB_THREADS) df_dot4(acc, g4[e], g4[e]);
-    double v[1] = {df_value(acc)};
-    block_write<1>(v, part_rec(part));
+    for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        const Chunk ch = chunk_at(si, ci, c);
+        const float4 *g4 = (const float4 *)g + ch.base4;
+        DF acc[1];
+        for (size_t e = ch.e0 + threadIdx.x; e < ch.e1; e += LB_THREADS) {
+            const float4 gv = g4[e];
+            df_dot4(acc[0], gv, gv);
+        }
+        block_write<1>(acc, part_rec(part, c));
+    }
 }
 
 __global__ void k_init_finish(SiteState *ss, const double *__restrict__ f, const double *part,
@@ -148,38 +177,45 @@ __device__ __forceinline__ bool slot_valid(int j, int head, int hist, int M)
     return ((head - 1 - j + 2 * M) % M) < hist;  // distance from the newest slot
 }
 
-// pass 1: S'y_n and Y'y_n for the newest pair n
+// pass 1: S'y_n and Y'y_n for the newest pair n.  Every vector an element
+// needs is loaded before any arithmetic, so each thread keeps 2M + 1
+// independent 16-byte loads in flight.
 template <int M>
 __global__ void __launch_bounds__(LB_THREADS)
 k_dir_dots(const SiteState *ss, const float *__restrict__ S, const float *__restrict__ Y,
-           const SiteInfo *si, const ChunkInfo *ci, long long vec4, double *part)
+           const SiteInfo *si, const ChunkInfo *ci, int nchunks, long long vec4, double *part)
 {
-    const Chunk ch = chunk_of(si, ci);
-    const SiteState &s = ss[ch.site];
-    if (s.status != SITE_READY || s.hist == 0) return;
-    const int hist = s.hist, head = s.head;
-    const int newest = (head - 1 + M) % M;
-    const float4 *S4 = (const float4 *)S + ch.base4;
-    const float4 *Y4 = (const float4 *)Y + ch.base4;
-    bool valid[M];
+    for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        const Chunk ch = chunk_at(si, ci, c);
+        const SiteState &s = ss[ch.site];
+        if (s.status != SITE_READY || s.hist == 0) continue;
+        const int hist = s.hist, head = s.head;
+        const int newest = (head - 1 + M) % M;
+        const float4 *S4 = (const float4 *)S + ch.base4;
+        const float4 *Y4 = (const float4 *)Y + ch.base4;
+        bool valid[M];
 #pragma unroll
-    for (int j = 0; j < M; ++j) valid[j] = slot_valid(j, head, hist, M);
-    DF acc[2 * M];
-    for (size_t e = ch.e0 + threadIdx.x; e < ch.e1; e += LB_THREADS) {
-        const float4 yn = Y4[(size_t)newest * vec4 + e];
+        for (int j = 0; j < M; ++j) valid[j] = slot_valid(j, head, hist, M);
+        DF acc[2 * M];
+        for (size_t e = ch.e0 + threadIdx.x; e < ch.e1; e += LB_THREADS) {
+            float4 sv[M], yv[M];
 #pragma unroll
-        for (int j = 0; j < M; ++j) {
-            if (!valid[j]) continue;
-            const float4 sv = S4[(size_t)j * vec4 + e];
-            const float4 yv = (j == newest) ? yn : Y4[(size_t)j * vec4 + e];
-            df_dot4(acc[j], sv, yn);
-            df_dot4(acc[M + j], yv, yn);
+            for (int j = 0; j < M; ++j) {
+                sv[j] = valid[j] ? S4[(size_t)j * vec4 + e] : f4z();
+                yv[j] = valid[j] ? Y4[(size_t)j * vec4 + e] : f4z();
+            }
+            float4 yn = yv[0];
+#pragma unroll
+            for (int j = 1; j < M; ++j)
+                if (j == newest) yn = yv[j];
+#pragma unroll
+            for (int j = 0; j < M; ++j) {
+                df_dot4(acc[j], sv[j], yn);
+                df_dot4(acc[M + j], yv[j], yn);
+            }
         }
+        block_write<2 * M>(acc, part_rec(part, c));
     }
-    double v[2 * M];
-#pragma unroll
-    for (int k = 0; k < 2 * M; ++k) v[k] = df_value(acc[k]);
-    block_write<2 * M>(v, part_rec(part));
 }
 
 // the small FP64 algebra of the compact form, one warp per site (the site's
@@ -275,64 +311,49 @@ template <int M>
 __global__ void __launch_bounds__(LB_THREADS)
 k_dir_apply(const SiteState *ss, const float *__restrict__ g, const float *__restrict__ S,
             const float *__restrict__ Y, float *__restrict__ dir, const SiteInfo *si,
-            const ChunkInfo *ci, long long vec4, double *part)
+            const ChunkInfo *ci, int nchunks, long long vec4, double *part)
 {
-    const Chunk ch = chunk_of(si, ci);
-    const SiteState &s = ss[ch.site];
-    if (s.status != SITE_READY) return;
-    const int hist = s.hist, head = s.head;
-    const float4 *g4 = (const float4 *)g + ch.base4;
-    const float4 *S4 = (const float4 *)S + ch.base4;
-    const float4 *Y4 = (const float4 *)Y + ch.base4;
-    float4 *d4 = (float4 *)dir + ch.base4;
-    const float cg = (float)s.cg;
-    bool valid[M];
-    float cs[M], cy[M];
-#pragma unroll
-    for (int j = 0; j < M; ++j) {
-        valid[j] = slot_valid(j, head, hist, M);
-        cs[j] = (float)s.cs[j];
-        cy[j] = (float)s.cy[j];
-    }
-    DF acc;
-    // two elements per pass keep twice the loads in flight
-    for (size_t e = ch.e0 + threadIdx.x; e < ch.e1; e += 2 * LB_THREADS) {
-        const size_t e2 = e + LB_THREADS;
-        const bool two = e2 < ch.e1;
-        const float4 gv = g4[e];
-        const float4 gw = two ? g4[e2] : make_float4(0.f, 0.f, 0.f, 0.f);
-        float4 a = make_float4(cg * gv.x, cg * gv.y, cg * gv.z, cg * gv.w);
-        float4 b = make_float4(cg * gw.x, cg * gw.y, cg * gw.z, cg * gw.w);
+    for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        const Chunk ch = chunk_at(si, ci, c);
+        const SiteState &s = ss[ch.site];
+        if (s.status != SITE_READY) continue;
+        const int hist = s.hist, head = s.head;
+        const float4 *g4 = (const float4 *)g + ch.base4;
+        const float4 *S4 = (const float4 *)S + ch.base4;
+        const float4 *Y4 = (const float4 *)Y + ch.base4;
+        float4 *d4 = (float4 *)dir + ch.base4;
+        const float cg = (float)s.cg;
+        bool valid[M];
+        float cs[M], cy[M];
 #pragma unroll
         for (int j = 0; j < M; ++j) {
-            if (!valid[j]) continue;
-            const float4 sv = S4[(size_t)j * vec4 + e];
-            const float4 yv = Y4[(size_t)j * vec4 + e];
-            float4 sw = make_float4(0.f, 0.f, 0.f, 0.f), yw = sw;
-            if (two) {
-                sw = S4[(size_t)j * vec4 + e2];
-                yw = Y4[(size_t)j * vec4 + e2];
+            valid[j] = slot_valid(j, head, hist, M);
+            cs[j] = (float)s.cs[j];
+            cy[j] = (float)s.cy[j];
+        }
+        DF acc[1];
+        for (size_t e = ch.e0 + threadIdx.x; e < ch.e1; e += LB_THREADS) {
+            const float4 gv = g4[e];
+            float4 sv[M], yv[M];
+#pragma unroll
+            for (int j = 0; j < M; ++j) {
+                sv[j] = valid[j] ? S4[(size_t)j * vec4 + e] : f4z();
+                yv[j] = valid[j] ? Y4[(size_t)j * vec4 + e] : f4z();
             }
-            a.x += cs[j] * sv.x + cy[j] * yv.x;
-            a.y += cs[j] * sv.y + cy[j] * yv.y;
-            a.z += cs[j] * sv.z + cy[j] * yv.z;
-            a.w += cs[j] * sv.w + cy[j] * yv.w;
-            b.x += cs[j] * sw.x + cy[j] * yw.x;
-            b.y += cs[j] * sw.y + cy[j] * yw.y;
-            b.z += cs[j] * sw.z + cy[j] * yw.z;
-            b.w += cs[j] * sw.w + cy[j] * yw.w;
+            float4 a = make_float4(cg * gv.x, cg * gv.y, cg * gv.z, cg * gv.w);
+#pragma unroll
+            for (int j = 0; j < M; ++j) {
+                a.x += cs[j] * sv[j].x + cy[j] * yv[j].x;
+                a.y += cs[j] * sv[j].y + cy[j] * yv[j].y;
+                a.z += cs[j] * sv[j].z + cy[j] * yv[j].z;
+                a.w += cs[j] * sv[j].w + cy[j] * yv[j].w;
+            }
+            const float4 dv = make_float4(-a.x, -a.y, -a.z, -a.w);
+            d4[e] = dv;
+            df_dot4(acc[0], gv, dv);
         }
-        const float4 dv = make_float4(-a.x, -a.y, -a.z, -a.w);
-        d4[e] = dv;
-        df_dot4(acc, gv, dv);
-        if (two) {
-            const float4 dw = make_float4(-b.x, -b.y, -b.z, -b.w);
-            d4[e2] = dw;
-            df_dot4(acc, gw, dw);
-        }
+        block_write<1>(acc, part_rec(part, c));
     }
-    double v[1] = {df_value(acc)};
-    block_write<1>(v, part_rec(part));
 }
 
 // line-search set-up; a direction that is not a descent direction (rounding
@@ -373,71 +394,79 @@ __global__ void k_dir_finish(SiteState *ss, const double *part, const SiteInfo *
 __global__ void __launch_bounds__(LB_THREADS)
 k_trial(const SiteState *ss, const float *__restrict__ theta, const float *__restrict__ g,
         float *__restrict__ dir, float *__restrict__ theta_t, __nv_bfloat16 *__restrict__ hi,
-        __nv_bfloat16 *__restrict__ lo, const SiteInfo *si, const ChunkInfo *ci, double *part)
+        __nv_bfloat16 *__restrict__ lo, const SiteInfo *si, const ChunkInfo *ci, int nchunks,
+        double *part)
 {
-    const Chunk ch = chunk_of(si, ci);
-    const SiteState &s = ss[ch.site];
-    if (s.status != SITE_SEARCHING) return;
-    const float a = (float)s.alpha;
-    const bool neg = s.neg_g != 0;
-    const int NQ = si[ch.site].NQ, KP = si[ch.site].KP;
-    const float4 *t4 = (const float4 *)theta + ch.base4;
-    const float4 *g4 = (const float4 *)g + ch.base4;
-    float4 *d4 = (float4 *)dir + ch.base4;
-    float4 *o4 = (float4 *)theta_t + ch.base4;
-    DF pj, ph;  // sums of squares: couplings, fields
-    for (size_t e = ch.e0 + threadIdx.x; e < ch.e1; e += LB_THREADS) {
-        const float4 t = t4[e];
-        float4 dv;
-        if (neg) {
-            const float4 gv = g4[e];
-            dv = make_float4(-gv.x, -gv.y, -gv.z, -gv.w);
-            d4[e] = dv;
-        } else {
-            dv = d4[e];
-        }
-        const float4 x = make_float4(fmaf(a, dv.x, t.x), fmaf(a, dv.y, t.y), fmaf(a, dv.z, t.z),
-                                     fmaf(a, dv.w, t.w));
-        o4[e] = x;
-        const float xv[4] = {x.x, x.y, x.z, x.w};
-        const int c0 = (int)((4 * e) % KP);
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            if (c0 + u == NQ) df_fma(ph, xv[u], xv[u]);
-            else df_fma(pj, xv[u], xv[u]);
-        }
-        if (hi) {
-            const size_t at = 4 * (ch.base4 + e);
+    for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        const Chunk ch = chunk_at(si, ci, c);
+        const SiteState &s = ss[ch.site];
+        if (s.status != SITE_SEARCHING) continue;
+        const float a = (float)s.alpha;
+        const bool neg = s.neg_g != 0;
+        const int NQ = si[ch.site].NQ, KP = si[ch.site].KP;
+        const float4 *t4 = (const float4 *)theta + ch.base4;
+        const float4 *g4 = (const float4 *)g + ch.base4;
+        float4 *d4 = (float4 *)dir + ch.base4;
+        float4 *o4 = (float4 *)theta_t + ch.base4;
+        DF acc[2];  // sums of squares: couplings, fields
+        for (size_t e = ch.e0 + threadIdx.x; e < ch.e1; e += LB_THREADS) {
+            const float4 t = t4[e];
+            float4 dv;
+            if (neg) {
+                const float4 gv = g4[e];
+                dv = make_float4(-gv.x, -gv.y, -gv.z, -gv.w);
+                d4[e] = dv;
+            } else {
+                dv = d4[e];
+            }
+            const float4 x = make_float4(fmaf(a, dv.x, t.x), fmaf(a, dv.y, t.y),
+                                         fmaf(a, dv.z, t.z), fmaf(a, dv.w, t.w));
+            o4[e] = x;
+            const float xv[4] = {x.x, x.y, x.z, x.w};
+            const int c0 = (int)((4 * e) % KP);
+            float pj = 0.0f, ph = 0.0f;
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const __nv_bfloat16 h = __float2bfloat16_rn(xv[u]);
-                hi[at + u] = h;
-                lo[at + u] = __float2bfloat16_rn(xv[u] - __bfloat162float(h));
+                if (c0 + u == NQ) ph = fmaf(xv[u], xv[u], ph);
+                else pj = fmaf(xv[u], xv[u], pj);
+            }
+            df_add(acc[0], pj);
+            df_add(acc[1], ph);
+            if (hi) {
+                const size_t at = 4 * (ch.base4 + e);
+                __align__(8) __nv_bfloat16 h4[4], l4[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    h4[u] = __float2bfloat16_rn(xv[u]);
+                    l4[u] = __float2bfloat16_rn(xv[u] - __bfloat162float(h4[u]));
+                }
+                *(uint2 *)(hi + at) = *(const uint2 *)h4;
+                *(uint2 *)(lo + at) = *(const uint2 *)l4;
             }
         }
+        block_write<2>(acc, part_rec(part, c));
     }
-    double v[2] = {df_value(pj), df_value(ph)};
-    block_write<2>(v, part_rec(part));
 }
 
 // partial g_t . d and ||g_t||^2 (slots 2 and 3; slots 0, 1 hold the penalty)
 __global__ void __launch_bounds__(LB_THREADS)
 k_ls_dots(const SiteState *ss, const float *__restrict__ g_t, const float *__restrict__ dir,
-          const SiteInfo *si, const ChunkInfo *ci, double *part)
+          const SiteInfo *si, const ChunkInfo *ci, int nchunks, double *part)
 {
-    const Chunk ch = chunk_of(si, ci);
-    const SiteState &s = ss[ch.site];
-    if (s.status != SITE_SEARCHING) return;
-    const float4 *gt4 = (const float4 *)g_t + ch.base4;
-    const float4 *d4 = (const float4 *)dir + ch.base4;
-    DF dgt, gn2;
-    for (size_t e = ch.e0 + threadIdx.x; e < ch.e1; e += LB_THREADS) {
-        const float4 gv = gt4[e];
-        df_dot4(dgt, gv, d4[e]);
-        df_dot4(gn2, gv, gv);
+    for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        const Chunk ch = chunk_at(si, ci, c);
+        const SiteState &s = ss[ch.site];
+        if (s.status != SITE_SEARCHING) continue;
+        const float4 *gt4 = (const float4 *)g_t + ch.base4;
+        const float4 *d4 = (const float4 *)dir + ch.base4;
+        DF acc[2];
+        for (size_t e = ch.e0 + threadIdx.x; e < ch.e1; e += LB_THREADS) {
+            const float4 gv = gt4[e], dv = d4[e];
+            df_dot4(acc[0], gv, dv);
+            df_dot4(acc[1], gv, gv);
+        }
+        block_write<2>(acc, part_rec(part, c) + 2);
     }
-    double v[2] = {df_value(dgt), df_value(gn2)};
-    block_write<2>(v, part_rec(part) + 2);
 }
 
 __device__ double safe_interp(double lo, double flo, double dlo, double hi, double fhi,
@@ -550,33 +579,60 @@ __global__ void __launch_bounds__(LB_THREADS)
 k_commit(const SiteState *ss, float *__restrict__ theta, float *__restrict__ g,
          const float *__restrict__ theta_t, const float *__restrict__ g_t,
          float *__restrict__ S, float *__restrict__ Y, const SiteInfo *si, const ChunkInfo *ci,
-         long long vec4, const int *round_ptr, double *part)
+         int nchunks, long long vec4, const int *round_ptr, double *part)
 {
     const int round = *round_ptr;
-    const Chunk ch = chunk_of(si, ci);
-    const SiteState &s = ss[ch.site];
-    if (s.commit_round != round) return;
-    const size_t slot = (size_t)s.commit_slot;
-    float4 *th4 = (float4 *)theta + ch.base4;
-    float4 *g4 = (float4 *)g + ch.base4;
-    const float4 *tt4 = (const float4 *)theta_t + ch.base4;
-    const float4 *gt4 = (const float4 *)g_t + ch.base4;
-    float4 *s4 = (float4 *)S + slot * vec4 + ch.base4;
-    float4 *y4 = (float4 *)Y + slot * vec4 + ch.base4;
-    DF sg, yg;
-    for (size_t e = ch.e0 + threadIdx.x; e < ch.e1; e += LB_THREADS) {
-        const float4 tn = tt4[e], to = th4[e], gn = gt4[e], go = g4[e];
-        const float4 sv = make_float4(tn.x - to.x, tn.y - to.y, tn.z - to.z, tn.w - to.w);
-        const float4 yv = make_float4(gn.x - go.x, gn.y - go.y, gn.z - go.z, gn.w - go.w);
-        s4[e] = sv;
-        y4[e] = yv;
-        th4[e] = tn;
-        g4[e] = gn;
-        df_dot4(sg, sv, gn);  // s_n . g_new
-        df_dot4(yg, yv, go);  // y_n . g_old
+    for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        const Chunk ch = chunk_at(si, ci, c);
+        const SiteState &s = ss[ch.site];
+        if (s.commit_round != round) continue;
+        const size_t slot = (size_t)s.commit_slot;
+        float4 *th4 = (float4 *)theta + ch.base4;
+        float4 *g4 = (float4 *)g + ch.base4;
+        const float4 *tt4 = (const float4 *)theta_t + ch.base4;
+        const float4 *gt4 = (const float4 *)g_t + ch.base4;
+        float4 *s4 = (float4 *)S + slot * vec4 + ch.base4;
+        float4 *y4 = (float4 *)Y + slot * vec4 + ch.base4;
+        DF acc[2];
+        for (size_t e = ch.e0 + threadIdx.x; e < ch.e1; e += LB_THREADS) {
+            const float4 tn = tt4[e], to = th4[e], gn = gt4[e], go = g4[e];
+            const float4 sv = make_float4(tn.x - to.x, tn.y - to.y, tn.z - to.z, tn.w - to.w);
+            const float4 yv = make_float4(gn.x - go.x, gn.y - go.y, gn.z - go.z, gn.w - go.w);
+            s4[e] = sv;
+            y4[e] = yv;
+            th4[e] = tn;
+            g4[e] = gn;
+            df_dot4(acc[0], sv, gn);  // s_n . g_new
+            df_dot4(acc[1], yv, go);  // y_n . g_old
+        }
+        block_write<2>(acc, part_rec(part, c) + LB_SLOT_SG);
     }
-    double v[2] = {df_value(sg), df_value(yg)};
-    block_write<2>(v, part_rec(part) + LB_SLOT_SG);
+}
+
+// resident CTAs of a streaming kernel on this device (at most one per chunk)
+template <typename Kern>
+int lb_grid(Kern k, int nchunks)
+{
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, int> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int slots = 0;
+    {
+        std::lock_guard<std::mutex> g(mu);
+        auto key = std::make_pair((const void *)k, dev);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            slots = it->second;
+        } else {
+            int per_sm = 0, sms = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, LB_THREADS, 0);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            slots = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+            cache[key] = slots;
+        }
+    }
+    return nchunks < slots ? (nchunks > 0 ? nchunks : 1) : slots;
 }
 
 }  // namespace
@@ -584,7 +640,8 @@ k_commit(const SiteState *ss, float *__restrict__ theta, float *__restrict__ g,
 cudaError_t launch_lbfgs_init(SiteState *ss, const double *f, const float *g, const LbLayout &L,
                               const SolveParams &p, double *part, cudaStream_t st)
 {
-    k_init_dots<<<L.nchunks, LB_THREADS, 0, st>>>(g, L.si, L.ci, part);
+    k_init_dots<<<lb_grid(k_init_dots, L.nchunks), LB_THREADS, 0, st>>>(g, L.si, L.ci, L.nchunks,
+                                                                      part);
     k_init_finish<<<L.nsites, 32, 0, st>>>(ss, f, part, L.si, p);
     count_launches(2);
     return cudaGetLastError();
@@ -594,7 +651,8 @@ template <int M>
 static void dir_dots_m(SiteState *ss, const float *S, const float *Y, const LbLayout &L,
                        double *part, cudaStream_t st)
 {
-    k_dir_dots<M><<<L.nchunks, LB_THREADS, 0, st>>>(ss, S, Y, L.si, L.ci, L.vec4, part);
+    k_dir_dots<M><<<lb_grid(k_dir_dots<M>, L.nchunks), LB_THREADS, 0, st>>>(
+        ss, S, Y, L.si, L.ci, L.nchunks, L.vec4, part);
     k_dir_solve<M><<<L.nsites, 32, 0, st>>>(ss, part, L.si);
 }
 
@@ -602,7 +660,8 @@ template <int M>
 static void dir_apply_m(SiteState *ss, const float *g, float *dir, const float *S,
                         const float *Y, const LbLayout &L, double *part, cudaStream_t st)
 {
-    k_dir_apply<M><<<L.nchunks, LB_THREADS, 0, st>>>(ss, g, S, Y, dir, L.si, L.ci, L.vec4, part);
+    k_dir_apply<M><<<lb_grid(k_dir_apply<M>, L.nchunks), LB_THREADS, 0, st>>>(
+        ss, g, S, Y, dir, L.si, L.ci, L.nchunks, L.vec4, part);
 }
 
 cudaError_t launch_lbfgs_dir_dots(SiteState *ss, const float *S_hist, const float *Y_hist,
@@ -650,8 +709,8 @@ cudaError_t launch_lbfgs_trial(SiteState *ss, const float *theta, const float *g
                                cudaStream_t st)
 {
     (void)p;
-    k_trial<<<L.nchunks, LB_THREADS, 0, st>>>(ss, theta, g, dir, theta_t, hi, lo, L.si, L.ci,
-                                               part);
+    k_trial<<<lb_grid(k_trial, L.nchunks), LB_THREADS, 0, st>>>(ss, theta, g, dir, theta_t, hi,
+                                                                  lo, L.si, L.ci, L.nchunks, part);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -661,7 +720,8 @@ cudaError_t launch_lbfgs_linesearch(SiteState *ss, const double *f_data, const f
                                     double *part, const int *round_ptr, int *counters,
                                     cudaStream_t st)
 {
-    k_ls_dots<<<L.nchunks, LB_THREADS, 0, st>>>(ss, g_t, dir, L.si, L.ci, part);
+    k_ls_dots<<<lb_grid(k_ls_dots, L.nchunks), LB_THREADS, 0, st>>>(ss, g_t, dir, L.si, L.ci,
+                                                                      L.nchunks, part);
     k_ls_decide<<<L.nsites, 32, 0, st>>>(ss, f_data, part, L.si, p, round_ptr, counters);
     count_launches(2);
     return cudaGetLastError();
@@ -672,8 +732,8 @@ cudaError_t launch_lbfgs_commit(const SiteState *ss, float *theta, float *g,
                                 float *Y_hist, const LbLayout &L, double *part,
                                 const int *round_ptr, cudaStream_t st)
 {
-    k_commit<<<L.nchunks, LB_THREADS, 0, st>>>(ss, theta, g, theta_t, g_t, S_hist, Y_hist, L.si,
-                                                L.ci, L.vec4, round_ptr, part);
+    k_commit<<<lb_grid(k_commit, L.nchunks), LB_THREADS, 0, st>>>(
+        ss, theta, g, theta_t, g_t, S_hist, Y_hist, L.si, L.ci, L.nchunks, L.vec4, round_ptr, part);
     count_launches(1);
     return cudaGetLastError();
 }

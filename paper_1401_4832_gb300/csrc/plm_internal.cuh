@@ -148,10 +148,12 @@ cudaError_t launch_grad_gather(const int8_t *msa, const float *D,
 // All vectors of the solver (theta, g, d, S, Y ...) are arenas holding the
 // padded Theta blocks of every family one after another.  A site is a row
 // block of one family; its segment is described by SiteInfo, cut into
-// chunks of at most LB_CHUNK4 float4 (ChunkInfo).  Vector kernels run one
-// CTA per chunk and write FP64 partial sums to part[chunk * LB_PART + k];
-// one-warp-per-site kernels reduce a site's chunks in a fixed order.
-constexpr int LB_CHUNK4 = 2048;
+// chunks of at most LB_CHUNK4 float4 (ChunkInfo).  Vector kernels run a
+// grid of resident CTAs that take the chunks in turn (chunk c goes to CTA
+// c mod gridDim) and write FP64 partial sums to part[chunk * LB_PART + k];
+// one-warp-per-site kernels reduce a site's chunks in a fixed order, so no
+// result depends on the grid size.
+constexpr int LB_CHUNK4 = 1024;
 
 struct SiteInfo {
     long long off4;  // float4 offset of the segment in every arena vector
