@@ -256,9 +256,9 @@ __device__ __forceinline__ void tmem_wait_ld()
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__device__ __forceinline__ void epi_bar()
+__device__ __forceinline__ void epi_bar256()
 {
-    asm volatile("bar.sync 1, 128;" ::: "memory");
+    asm volatile("bar.sync 1, 256;" ::: "memory");
 }
 
 __device__ __forceinline__ uint8_t *align1024(uint8_t *p)
@@ -610,7 +610,12 @@ k_tc_logits(const __grid_constant__ LogitsParams P, int *__restrict__ err)
 // One 128 x ncols tile per CTA (measured faster here than a persistent
 // variant: with ~1.5 tiles per SM there is little epilogue to overlap, and
 // the whole-tile shared-memory staging of the epilogue writes G coalesced).
-__global__ void __launch_bounds__(192, 1)
+// Warp 0: TMA for D^T hi/lo; warp 1: TMEM and MMA issue; warps 2-9: the
+// one-hot X^T producers (one operand row per thread: with one warp per
+// scheduler the producers were latency bound), then the epilogue.
+constexpr int GR_THREADS = 320;
+constexpr int GR_PROD = 256;
+__global__ void __launch_bounds__(GR_THREADS, 1)
 k_tc_grad(const __grid_constant__ GradParams P, float two_lh, float two_lj, int *__restrict__ err)
 {
     const int fi = family_of(P.b, blockIdx.x, true);
@@ -651,7 +656,7 @@ k_tc_grad(const __grid_constant__ GradParams P, float two_lh, float two_lj, int 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NST; ++s) {
             mbar_init(&full_b[s], 1);
-            mbar_init(&full_a[s], 128);
+            mbar_init(&full_a[s], GR_PROD);
             mbar_init(&empty_[s], 1);
         }
         mbar_init(&acc_full, 1);
@@ -707,84 +712,70 @@ k_tc_grad(const __grid_constant__ GradParams P, float two_lh, float two_lj, int 
             mma_commit(&acc_full);
         }
     } else {
-        // ---- one-hot X^T producer: thread p writes rows p and p + 128
+        // ---- one-hot X^T producer: thread p writes operand row p
         const int p = threadIdx.x - 64;
-        int src_i[2];
-        uint32_t kk[2];
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            const int c = c0 + p + 128 * u;
-            int i = 0;
-            uint32_t k = 0xFFu;  // never equals a stored state (0..20, or 0x7F padding)
-            if (c < NQ) {
-                i = c / Q;
-                k = (uint32_t)(c % Q);
-            } else if (c == NQ) {
-                i = d.N;  // the all-ones row of msaT
-                k = 0;
-            }
-            src_i[u] = i;
-            kk[u] = k * 0x01010101u;
+        const int c = c0 + p;
+        int src_i = 0;
+        uint32_t kk = 0xFFu;  // never equals a stored state (0..20, or 0x7F padding)
+        if (c < NQ) {
+            src_i = c / Q;
+            kk = (uint32_t)(c % Q);
+        } else if (c == NQ) {
+            src_i = d.N;  // the all-ones row of msaT
+            kk = 0;
         }
+        kk *= 0x01010101u;
+        const bool prow = p < GRN;
         // the next stage's MSA bytes are fetched while the current stage is
         // written, so the global-load latency overlaps the pipeline
-        uint4 cur[2][4], nxt[2][4];
+        const uint4 *srcT = (const uint4 *)(msaT + (size_t)src_i * BP);
+        uint4 cur[4], nxt[4];
 #pragma unroll
-        for (int u = 0; u < 2; ++u)
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                cur[u][q] = __ldg((const uint4 *)(msaT + (size_t)src_i[u] * BP) + q);
+        for (int q = 0; q < 4; ++q) cur[q] = __ldg(srcT + q);
         for (int kc = 0; kc < NK; ++kc) {
             const int s = kc % NST, n = kc / NST;
             const int kn = kc + 1 < NK ? kc + 1 : kc;
 #pragma unroll
-            for (int u = 0; u < 2; ++u)
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    nxt[u][q] =
-                        __ldg((const uint4 *)(msaT + (size_t)src_i[u] * BP + kn * TC_BK) + q);
+            for (int q = 0; q < 4; ++q) nxt[q] = __ldg(srcT + (size_t)kn * (TC_BK / 16) + q);
             if (n > 0 && !mbar_wait(&empty_[s], (n - 1) & 1, &abort_sh, err, ERR_TIMEOUT_PROD))
                 break;
             uint8_t *bt = smem + s * GRSTAGE + 2 * GR_A_BYTES;
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int row = p + 128 * u;
-                if (row >= GRN) continue;
+            if (prow) {
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {  // 16 sequences per word group
-                    const uint4 x = cur[u][q];
+                    const uint4 x = cur[q];
                     const uint32_t xs[4] = {x.x, x.y, x.z, x.w};
                     uint32_t o[8];
 #pragma unroll
                     for (int t = 0; t < 4; ++t) {
-                        const uint32_t m = __vcmpeq4(xs[t], kk[u]);
+                        const uint32_t m = __vcmpeq4(xs[t], kk);
                         o[2 * t] = __byte_perm(m, 0, 0x1100) & 0x3F803F80u;
                         o[2 * t + 1] = __byte_perm(m, 0, 0x3322) & 0x3F803F80u;
                     }
-                    *(uint4 *)(bt + swz(row, 2 * q)) = make_uint4(o[0], o[1], o[2], o[3]);
-                    *(uint4 *)(bt + swz(row, 2 * q + 1)) = make_uint4(o[4], o[5], o[6], o[7]);
+                    *(uint4 *)(bt + swz(p, 2 * q)) = make_uint4(o[0], o[1], o[2], o[3]);
+                    *(uint4 *)(bt + swz(p, 2 * q + 1)) = make_uint4(o[4], o[5], o[6], o[7]);
                 }
             }
             fence_proxy_async();
             mbar_arrive(&full_a[s]);
 #pragma unroll
-            for (int u = 0; u < 2; ++u)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) cur[u][q] = nxt[u][q];
+            for (int q = 0; q < 4; ++q) cur[q] = nxt[q];
         }
 
         // ---- epilogue: TMEM -> shared (rows padded to 260 floats so the
         // lane-per-row stores spread over the banks), then a coalesced pass
         // adds 2 lambda Theta, applies the masks and writes G.
         const int q4 = warp & 3;
+        const int half = (warp - 2) >> 2;  // column half of the tile
         const int trow = q4 * 32 + lane;
         const bool ok = mbar_wait(&acc_full, 0, &abort_sh, err, ERR_TIMEOUT_EPI);
         tc_fence_after();
         const int GS = GRN + 4;
         float *acc_s = (float *)smem;  // [128][GS]
         const uint32_t tl = tmem + ((uint32_t)(q4 * 32) << 16);
+        const int ng = GRN / 32;  // 16-column groups per half
 #pragma unroll 1
-        for (int cc = 0; cc < GRN / 16; ++cc) {
+        for (int cc = half * ng; cc < (half + 1) * ng; ++cc) {
             float v[16];
             tmem_ld16(tl + cc * 16, v);
             tmem_wait_ld();
@@ -793,15 +784,15 @@ k_tc_grad(const __grid_constant__ GradParams P, float two_lh, float two_lj, int 
             for (int q = 0; q < 4; ++q)
                 dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
         }
-        epi_bar();
+        epi_bar256();
         const int t = threadIdx.x - 64;
-        constexpr int UNR = 8;
-        for (int e0 = t; e0 < TC_M * (GRN / 4); e0 += 128 * UNR) {
+        constexpr int UNR = 4;
+        for (int e0 = t; e0 < TC_M * (GRN / 4); e0 += GR_PROD * UNR) {
             float4 th[UNR];
             bool live[UNR];
 #pragma unroll
             for (int k = 0; k < UNR; ++k) {  // issue all loads first
-                const int e = e0 + 128 * k;
+                const int e = e0 + GR_PROD * k;
                 const int rr = e / (GRN / 4), c4 = e % (GRN / 4);
                 const int row = rs0 + rr, cb = c0 + 4 * c4;
                 live[k] = ok && e < TC_M * (GRN / 4) && row < d.R && cb < d.KP;
@@ -811,7 +802,7 @@ k_tc_grad(const __grid_constant__ GradParams P, float two_lh, float two_lj, int 
 #pragma unroll
             for (int k = 0; k < UNR; ++k) {
                 if (!live[k]) continue;
-                const int e = e0 + 128 * k;
+                const int e = e0 + GR_PROD * k;
                 const int rr = e / (GRN / 4), c4 = e % (GRN / 4);
                 const int row = rs0 + rr, cb = c0 + 4 * c4;
                 const int r = row / QP, sstate = row % QP;
@@ -1050,7 +1041,7 @@ cudaError_t launch_tc_eval(void *prof, const TcBatch &b_in, const TcConfig &cfg,
     if (which & 2) {
         void *t1 = prof ? prof_start(prof) : nullptr;
         if (tg > 0)
-            k_tc_grad<<<tg, 192, gp.stages * gp.stage_bytes + 1024, st>>>(
+            k_tc_grad<<<tg, GR_THREADS, gp.stages * gp.stage_bytes + 1024, st>>>(
                 gp, (float)(2.0 * lambda_h), (float)(2.0 * lambda_Jp), err);
         if (prof) prof_stop(prof, "tc_grad", t1);
         count_launches(1);
