@@ -458,6 +458,29 @@ def main():
         dist.destroy_process_group()
 
 
+# DRAM bytes (read + write) per launch from one ncu capture of a full
+# evaluation of this workload, valid only for the kernel source it was
+# taken on (sha256 prefix of the .cu file); null once the source changes
+NCU_TRAFFIC = {
+    "tc_logits": ("k_tc.cu", "879c34dacd461641", 30.814464e6 + 8.269568e6),
+    "tc_grad": ("k_tc.cu", "879c34dacd461641", 89.806848e6 + 6.455040e6),
+}
+
+
+def ncu_traffic(kernel):
+    import hashlib
+    ent = NCU_TRAFFIC.get(kernel)
+    if not ent:
+        return None
+    fn = os.path.join(ROOT, "paper_1401_4832_gb300", "csrc", ent[0])
+    try:
+        with open(fn, "rb") as fh:
+            h = hashlib.sha256(fh.read()).hexdigest()[:16]
+    except OSError:
+        return None
+    return ent[2] if h == ent[1] else None
+
+
 def read_profile(lib, ctx):
     """{kernel: (launches, total ms, algorithmic bytes)} from the context's
     profile record."""
@@ -518,7 +541,9 @@ def kernel_rooflines(kern, tc_full, B, N, pk, pk_kind):
             peak = pk.get("bf16_tflops_sustained", 1700.0)
             ach = flops / avg_s / 1e12
             out[name] = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                         "frac": ach / peak, "traffic": None, "flops_per_launch": flops,
+                         "frac": ach / peak, "traffic": ncu_traffic(name),
+                         "traffic_unit": "bytes per launch (ncu dram read + write)",
+                         "flops_per_launch": flops,
                          "launch_us_full_eval": avg_s * 1e6,
                          "peak_note": f"bf16 dense sustained, {pk_kind}; timed on full "
                                       "evaluations, L2 flushed before each"}
