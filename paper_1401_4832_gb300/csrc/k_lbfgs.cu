@@ -159,7 +159,6 @@ __global__ void k_init_finish(SiteState *ss, const double *__restrict__ f, const
     s.trials = 0;
     s.phase = 0;
     s.gamma = 1.0;
-    s.neg_g = 0;
     s.commit_round = -1;
     s.commit_slot = 0;
     for (int i = 0; i < MAX_M; ++i)
@@ -177,44 +176,33 @@ __device__ __forceinline__ bool slot_valid(int j, int head, int hist, int M)
     return ((head - 1 - j + 2 * M) % M) < hist;  // distance from the newest slot
 }
 
-// pass 1: S'y_n and Y'y_n for the newest pair n.  Every vector an element
-// needs is loaded before any arithmetic, so each thread keeps 2M + 1
-// independent 16-byte loads in flight.
-template <int M>
-__global__ void __launch_bounds__(LB_THREADS)
-k_dir_dots(const SiteState *ss, const float *__restrict__ S, const float *__restrict__ Y,
-           const SiteInfo *si, const ChunkInfo *ci, int nchunks, long long vec4, double *part)
+// squares of theta_t into the penalty sums (field column separately) and
+// its bf16 hi/lo split for the tensor-core evaluation
+__device__ __forceinline__ void trial_penalty_split(const float4 x, size_t e, size_t base4, int NQ,
+                                                    int KP, __nv_bfloat16 *__restrict__ hi,
+                                                    __nv_bfloat16 *__restrict__ lo, DF &pj,
+                                                    DF &ph)
 {
-    for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
-        const Chunk ch = chunk_at(si, ci, c);
-        const SiteState &s = ss[ch.site];
-        if (s.status != SITE_READY || s.hist == 0) continue;
-        const int hist = s.hist, head = s.head;
-        const int newest = (head - 1 + M) % M;
-        const float4 *S4 = (const float4 *)S + ch.base4;
-        const float4 *Y4 = (const float4 *)Y + ch.base4;
-        bool valid[M];
+    const float xv[4] = {x.x, x.y, x.z, x.w};
+    const int c0 = (int)((4 * e) % KP);
+    float sj = 0.0f, sh = 0.0f;
 #pragma unroll
-        for (int j = 0; j < M; ++j) valid[j] = slot_valid(j, head, hist, M);
-        DF acc[2 * M];
-        for (size_t e = ch.e0 + threadIdx.x; e < ch.e1; e += LB_THREADS) {
-            float4 sv[M], yv[M];
+    for (int u = 0; u < 4; ++u) {
+        if (c0 + u == NQ) sh = fmaf(xv[u], xv[u], sh);
+        else sj = fmaf(xv[u], xv[u], sj);
+    }
+    df_add(pj, sj);
+    df_add(ph, sh);
+    if (hi) {
+        const size_t at = 4 * (base4 + e);
+        __align__(8) __nv_bfloat16 h4[4], l4[4];
 #pragma unroll
-            for (int j = 0; j < M; ++j) {
-                sv[j] = valid[j] ? S4[(size_t)j * vec4 + e] : f4z();
-                yv[j] = valid[j] ? Y4[(size_t)j * vec4 + e] : f4z();
-            }
-            float4 yn = yv[0];
-#pragma unroll
-            for (int j = 1; j < M; ++j)
-                if (j == newest) yn = yv[j];
-#pragma unroll
-            for (int j = 0; j < M; ++j) {
-                df_dot4(acc[j], sv[j], yn);
-                df_dot4(acc[M + j], yv[j], yn);
-            }
+        for (int u = 0; u < 4; ++u) {
+            h4[u] = __float2bfloat16_rn(xv[u]);
+            l4[u] = __float2bfloat16_rn(xv[u] - __bfloat162float(h4[u]));
         }
-        block_write<2 * M>(acc, part_rec(part, c));
+        *(uint2 *)(hi + at) = *(const uint2 *)h4;
+        *(uint2 *)(lo + at) = *(const uint2 *)l4;
     }
 }
 
@@ -245,6 +233,8 @@ __global__ void k_dir_solve(SiteState *ss, const double *part, const SiteInfo *s
     if (lane != 0) return;
     for (int j = 0; j < MAX_M; ++j) s.cs[j] = s.cy[j] = 0.0;
     s.cg = 1.0;
+    // first trial step: 1/||g|| on the very first (steepest-descent) step, else 1
+    s.alpha = (s.iters == 0) ? 1.0 / sqrt(s.gnorm2) : 1.0;
     if (hist == 0) return;
     const int n = (head - 1 + M) % M;
     // new column of S'Y and row/column of Y'Y; u, v moved to g_new
@@ -272,6 +262,7 @@ __global__ void k_dir_solve(SiteState *ss, const double *part, const SiteInfo *s
         s.head = 0;
         return;
     }
+    s.alpha = 1.0;
     const double gamma = SY[n][n] / YY[n][n];
     int idx[M];
     double u[M], v[M], t1[M], t2[M], pp[M];
@@ -306,23 +297,32 @@ __global__ void k_dir_solve(SiteState *ss, const double *part, const SiteInfo *s
     }
 }
 
-// pass 2: d = -(cg g + sum cs_j s_j + sum cy_j y_j); partial g.d
+// d = -(cg g + sum cs_j s_j + sum cy_j y_j) and, in the same pass, the
+// first trial point theta_t = theta + alpha d (with its bf16 split) of the
+// new line search.  Partials: slots 0, 1 the penalty sums of theta_t
+// (couplings, fields), slot 2 g.d.  Every vector an element needs is loaded
+// before any arithmetic.
 template <int M>
-__global__ void __launch_bounds__(LB_THREADS)
+__global__ void __launch_bounds__(LB_THREADS, 3)
 k_dir_apply(const SiteState *ss, const float *__restrict__ g, const float *__restrict__ S,
-            const float *__restrict__ Y, float *__restrict__ dir, const SiteInfo *si,
-            const ChunkInfo *ci, int nchunks, long long vec4, double *part)
+            const float *__restrict__ Y, float *__restrict__ dir, const float *__restrict__ theta,
+            float *__restrict__ theta_t, __nv_bfloat16 *__restrict__ hi,
+            __nv_bfloat16 *__restrict__ lo, const SiteInfo *si, const ChunkInfo *ci, int nchunks,
+            long long vec4, double *part)
 {
     for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
         const Chunk ch = chunk_at(si, ci, c);
         const SiteState &s = ss[ch.site];
         if (s.status != SITE_READY) continue;
         const int hist = s.hist, head = s.head;
+        const int NQ = si[ch.site].NQ, KP = si[ch.site].KP;
         const float4 *g4 = (const float4 *)g + ch.base4;
         const float4 *S4 = (const float4 *)S + ch.base4;
         const float4 *Y4 = (const float4 *)Y + ch.base4;
+        const float4 *t4 = (const float4 *)theta + ch.base4;
         float4 *d4 = (float4 *)dir + ch.base4;
-        const float cg = (float)s.cg;
+        float4 *o4 = (float4 *)theta_t + ch.base4;
+        const float cg = (float)s.cg, al = (float)s.alpha;
         bool valid[M];
         float cs[M], cy[M];
 #pragma unroll
@@ -331,9 +331,9 @@ k_dir_apply(const SiteState *ss, const float *__restrict__ g, const float *__res
             cs[j] = (float)s.cs[j];
             cy[j] = (float)s.cy[j];
         }
-        DF acc[1];
+        DF acc[3];
         for (size_t e = ch.e0 + threadIdx.x; e < ch.e1; e += LB_THREADS) {
-            const float4 gv = g4[e];
+            const float4 gv = g4[e], tv = t4[e];
             float4 sv[M], yv[M];
 #pragma unroll
             for (int j = 0; j < M; ++j) {
@@ -350,31 +350,35 @@ k_dir_apply(const SiteState *ss, const float *__restrict__ g, const float *__res
             }
             const float4 dv = make_float4(-a.x, -a.y, -a.z, -a.w);
             d4[e] = dv;
-            df_dot4(acc[0], gv, dv);
+            df_dot4(acc[2], gv, dv);
+            const float4 x = make_float4(fmaf(al, dv.x, tv.x), fmaf(al, dv.y, tv.y),
+                                         fmaf(al, dv.z, tv.z), fmaf(al, dv.w, tv.w));
+            o4[e] = x;
+            trial_penalty_split(x, e, ch.base4, NQ, KP, hi, lo, acc[0], acc[1]);
         }
-        block_write<1>(acc, part_rec(part, c));
+        block_write<3>(acc, part_rec(part, c));
     }
 }
 
-// line-search set-up; a direction that is not a descent direction (rounding
-// in FP32) is replaced by -g and the history is dropped
+// line-search set-up.  A direction that is not a descent direction
+// (rounding in FP32) drops the history: the site stays READY and takes the
+// steepest-descent direction in the next round (its trial point of this
+// round is not evaluated).
 __global__ void k_dir_finish(SiteState *ss, const double *part, const SiteInfo *si)
 {
     const int r = blockIdx.x;
     SiteState &s = ss[r];
     if (s.status != SITE_READY) return;
-    double dg0 = chunk_sum(part, si[r], 0);
+    const double dg0 = chunk_sum(part, si[r], 2);
     if (threadIdx.x != 0) return;
-    s.neg_g = 0;
     if (!(dg0 < 0.0)) {
-        s.neg_g = 1;
+        if (s.hist == 0) s.status = SITE_FAILED;  // -g itself is not a descent direction
         s.hist = 0;
         s.head = 0;
-        dg0 = -s.gnorm2;
+        return;
     }
     s.f0 = s.f;
     s.dg0 = dg0;
-    s.alpha = (s.iters == 0 && s.hist == 0) ? 1.0 / sqrt(s.gnorm2) : 1.0;
     s.a_prev = 0.0;
     s.f_prev = s.f;
     s.dg_prev = dg0;
@@ -390,59 +394,31 @@ __global__ void k_dir_finish(SiteState *ss, const double *part, const SiteInfo *
 }
 
 // ------------------------------------------------------------ line search
-// theta_t = theta + alpha d (and its bf16 hi/lo split); penalty partials
+// later trial points of a line search: theta_t = theta + alpha d (and its
+// bf16 split); penalty partials in slots 0, 1.  (The first trial point of
+// each search is formed with the direction.)
 __global__ void __launch_bounds__(LB_THREADS)
-k_trial(const SiteState *ss, const float *__restrict__ theta, const float *__restrict__ g,
-        float *__restrict__ dir, float *__restrict__ theta_t, __nv_bfloat16 *__restrict__ hi,
+k_trial(const SiteState *ss, const float *__restrict__ theta, const float *__restrict__ dir,
+        float *__restrict__ theta_t, __nv_bfloat16 *__restrict__ hi,
         __nv_bfloat16 *__restrict__ lo, const SiteInfo *si, const ChunkInfo *ci, int nchunks,
         double *part)
 {
     for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
         const Chunk ch = chunk_at(si, ci, c);
         const SiteState &s = ss[ch.site];
-        if (s.status != SITE_SEARCHING) continue;
+        if (s.status != SITE_SEARCHING || s.trials == 0) continue;
         const float a = (float)s.alpha;
-        const bool neg = s.neg_g != 0;
         const int NQ = si[ch.site].NQ, KP = si[ch.site].KP;
         const float4 *t4 = (const float4 *)theta + ch.base4;
-        const float4 *g4 = (const float4 *)g + ch.base4;
-        float4 *d4 = (float4 *)dir + ch.base4;
+        const float4 *d4 = (const float4 *)dir + ch.base4;
         float4 *o4 = (float4 *)theta_t + ch.base4;
         DF acc[2];  // sums of squares: couplings, fields
         for (size_t e = ch.e0 + threadIdx.x; e < ch.e1; e += LB_THREADS) {
-            const float4 t = t4[e];
-            float4 dv;
-            if (neg) {
-                const float4 gv = g4[e];
-                dv = make_float4(-gv.x, -gv.y, -gv.z, -gv.w);
-                d4[e] = dv;
-            } else {
-                dv = d4[e];
-            }
+            const float4 t = t4[e], dv = d4[e];
             const float4 x = make_float4(fmaf(a, dv.x, t.x), fmaf(a, dv.y, t.y),
                                          fmaf(a, dv.z, t.z), fmaf(a, dv.w, t.w));
             o4[e] = x;
-            const float xv[4] = {x.x, x.y, x.z, x.w};
-            const int c0 = (int)((4 * e) % KP);
-            float pj = 0.0f, ph = 0.0f;
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                if (c0 + u == NQ) ph = fmaf(xv[u], xv[u], ph);
-                else pj = fmaf(xv[u], xv[u], pj);
-            }
-            df_add(acc[0], pj);
-            df_add(acc[1], ph);
-            if (hi) {
-                const size_t at = 4 * (ch.base4 + e);
-                __align__(8) __nv_bfloat16 h4[4], l4[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    h4[u] = __float2bfloat16_rn(xv[u]);
-                    l4[u] = __float2bfloat16_rn(xv[u] - __bfloat162float(h4[u]));
-                }
-                *(uint2 *)(hi + at) = *(const uint2 *)h4;
-                *(uint2 *)(lo + at) = *(const uint2 *)l4;
-            }
+            trial_penalty_split(x, e, ch.base4, NQ, KP, hi, lo, acc[0], acc[1]);
         }
         block_write<2>(acc, part_rec(part, c));
     }
@@ -559,7 +535,6 @@ __global__ void k_ls_decide(SiteState *ss, const double *__restrict__ f_data, co
         if (s.hist < p.m) s.hist++;
         s.f = ft;
         s.gnorm2 = gn2;
-        s.neg_g = 0;
         s.iters++;
         if (sqrt(gn2) <= p.gtol) s.status = SITE_CONVERGED;
         else if (s.iters >= p.max_iter) s.status = SITE_FAILED;
@@ -574,8 +549,13 @@ __global__ void k_ls_decide(SiteState *ss, const double *__restrict__ f_data, co
 }
 
 // commit the accepted trial points of this round: s = theta_t - theta,
-// y = g_t - g into the ring slot, theta <- theta_t, g <- g_t
-__global__ void __launch_bounds__(LB_THREADS)
+// y = g_t - g into the ring slot, theta <- theta_t, g <- g_t.  The same pass
+// forms what the next direction needs: s_n.g_new and y_n.g_old (slots
+// LB_SLOT_SG, LB_SLOT_YG) and, for a site that iterates on, S'y_n and Y'y_n
+// over the stored pairs (slots 0..2M-1; the new pair's own entries from
+// registers).
+template <int M>
+__global__ void __launch_bounds__(LB_THREADS, 2)
 k_commit(const SiteState *ss, float *__restrict__ theta, float *__restrict__ g,
          const float *__restrict__ theta_t, const float *__restrict__ g_t,
          float *__restrict__ S, float *__restrict__ Y, const SiteInfo *si, const ChunkInfo *ci,
@@ -584,28 +564,50 @@ k_commit(const SiteState *ss, float *__restrict__ theta, float *__restrict__ g,
     const int round = *round_ptr;
     for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
         const Chunk ch = chunk_at(si, ci, c);
-        const SiteState &s = ss[ch.site];
-        if (s.commit_round != round) continue;
-        const size_t slot = (size_t)s.commit_slot;
+        const SiteState &st = ss[ch.site];
+        if (st.commit_round != round) continue;
+        const int n = st.commit_slot;
+        const bool dots = st.status == SITE_READY;
+        bool old[M];  // stored pairs other than the new one
+#pragma unroll
+        for (int j = 0; j < M; ++j) old[j] = dots && j != n && slot_valid(j, st.head, st.hist, M);
         float4 *th4 = (float4 *)theta + ch.base4;
         float4 *g4 = (float4 *)g + ch.base4;
         const float4 *tt4 = (const float4 *)theta_t + ch.base4;
         const float4 *gt4 = (const float4 *)g_t + ch.base4;
-        float4 *s4 = (float4 *)S + slot * vec4 + ch.base4;
-        float4 *y4 = (float4 *)Y + slot * vec4 + ch.base4;
-        DF acc[2];
+        const float4 *S4 = (const float4 *)S + ch.base4;
+        const float4 *Y4 = (const float4 *)Y + ch.base4;
+        float4 *s4 = (float4 *)S + (size_t)n * vec4 + ch.base4;
+        float4 *y4 = (float4 *)Y + (size_t)n * vec4 + ch.base4;
+        DF acc[2 * M], sgyg[2];
         for (size_t e = ch.e0 + threadIdx.x; e < ch.e1; e += LB_THREADS) {
             const float4 tn = tt4[e], to = th4[e], gn = gt4[e], go = g4[e];
+            float4 sj[M], yj[M];
+#pragma unroll
+            for (int j = 0; j < M; ++j) {
+                sj[j] = old[j] ? S4[(size_t)j * vec4 + e] : f4z();
+                yj[j] = old[j] ? Y4[(size_t)j * vec4 + e] : f4z();
+            }
             const float4 sv = make_float4(tn.x - to.x, tn.y - to.y, tn.z - to.z, tn.w - to.w);
             const float4 yv = make_float4(gn.x - go.x, gn.y - go.y, gn.z - go.z, gn.w - go.w);
             s4[e] = sv;
             y4[e] = yv;
             th4[e] = tn;
             g4[e] = gn;
-            df_dot4(acc[0], sv, gn);  // s_n . g_new
-            df_dot4(acc[1], yv, go);  // y_n . g_old
+            df_dot4(sgyg[0], sv, gn);  // s_n . g_new
+            df_dot4(sgyg[1], yv, go);  // y_n . g_old
+            if (dots) {
+#pragma unroll
+                for (int j = 0; j < M; ++j) {
+                    const float4 a = (j == n) ? sv : sj[j];
+                    const float4 b = (j == n) ? yv : yj[j];
+                    df_dot4(acc[j], a, yv);
+                    df_dot4(acc[M + j], b, yv);
+                }
+            }
         }
-        block_write<2>(acc, part_rec(part, c) + LB_SLOT_SG);
+        if (dots) block_write<2 * M>(acc, part_rec(part, c));
+        block_write<2>(sgyg, part_rec(part, c) + LB_SLOT_SG);
     }
 }
 
@@ -648,69 +650,48 @@ cudaError_t launch_lbfgs_init(SiteState *ss, const double *f, const float *g, co
 }
 
 template <int M>
-static void dir_dots_m(SiteState *ss, const float *S, const float *Y, const LbLayout &L,
-                       double *part, cudaStream_t st)
-{
-    k_dir_dots<M><<<lb_grid(k_dir_dots<M>, L.nchunks), LB_THREADS, 0, st>>>(
-        ss, S, Y, L.si, L.ci, L.nchunks, L.vec4, part);
-    k_dir_solve<M><<<L.nsites, 32, 0, st>>>(ss, part, L.si);
-}
-
-template <int M>
 static void dir_apply_m(SiteState *ss, const float *g, float *dir, const float *S,
-                        const float *Y, const LbLayout &L, double *part, cudaStream_t st)
+                        const float *Y, const float *theta, float *theta_t, __nv_bfloat16 *hi,
+                        __nv_bfloat16 *lo, const LbLayout &L, double *part, cudaStream_t st)
 {
+    k_dir_solve<M><<<L.nsites, 32, 0, st>>>(ss, part, L.si);
     k_dir_apply<M><<<lb_grid(k_dir_apply<M>, L.nchunks), LB_THREADS, 0, st>>>(
-        ss, g, S, Y, dir, L.si, L.ci, L.nchunks, L.vec4, part);
+        ss, g, S, Y, dir, theta, theta_t, hi, lo, L.si, L.ci, L.nchunks, L.vec4, part);
 }
 
-cudaError_t launch_lbfgs_dir_dots(SiteState *ss, const float *S_hist, const float *Y_hist,
-                                  const LbLayout &L, const SolveParams &p, double *part,
-                                  cudaStream_t st)
+cudaError_t launch_lbfgs_direction(SiteState *ss, const float *g, float *dir,
+                                   const float *S_hist, const float *Y_hist, const float *theta,
+                                   float *theta_t, __nv_bfloat16 *hi, __nv_bfloat16 *lo,
+                                   const LbLayout &L, const SolveParams &p, double *part,
+                                   cudaStream_t st)
 {
+#define PLM_DIR(MM)                                                                          \
+    case MM:                                                                                 \
+        dir_apply_m<MM>(ss, g, dir, S_hist, Y_hist, theta, theta_t, hi, lo, L, part, st);   \
+        break;
     switch (p.m) {
-    case 1: dir_dots_m<1>(ss, S_hist, Y_hist, L, part, st); break;
-    case 2: dir_dots_m<2>(ss, S_hist, Y_hist, L, part, st); break;
-    case 3: dir_dots_m<3>(ss, S_hist, Y_hist, L, part, st); break;
-    case 4: dir_dots_m<4>(ss, S_hist, Y_hist, L, part, st); break;
-    case 5: dir_dots_m<5>(ss, S_hist, Y_hist, L, part, st); break;
-    case 6: dir_dots_m<6>(ss, S_hist, Y_hist, L, part, st); break;
-    case 7: dir_dots_m<7>(ss, S_hist, Y_hist, L, part, st); break;
-    case 8: dir_dots_m<8>(ss, S_hist, Y_hist, L, part, st); break;
+        PLM_DIR(1)
+        PLM_DIR(2)
+        PLM_DIR(3)
+        PLM_DIR(4)
+        PLM_DIR(5)
+        PLM_DIR(6)
+        PLM_DIR(7)
+        PLM_DIR(8)
     default: return cudaErrorInvalidValue;
     }
-    count_launches(2);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_lbfgs_dir_apply(SiteState *ss, const float *g, float *dir,
-                                   const float *S_hist, const float *Y_hist, const LbLayout &L,
-                                   const SolveParams &p, double *part, cudaStream_t st)
-{
-    switch (p.m) {
-    case 1: dir_apply_m<1>(ss, g, dir, S_hist, Y_hist, L, part, st); break;
-    case 2: dir_apply_m<2>(ss, g, dir, S_hist, Y_hist, L, part, st); break;
-    case 3: dir_apply_m<3>(ss, g, dir, S_hist, Y_hist, L, part, st); break;
-    case 4: dir_apply_m<4>(ss, g, dir, S_hist, Y_hist, L, part, st); break;
-    case 5: dir_apply_m<5>(ss, g, dir, S_hist, Y_hist, L, part, st); break;
-    case 6: dir_apply_m<6>(ss, g, dir, S_hist, Y_hist, L, part, st); break;
-    case 7: dir_apply_m<7>(ss, g, dir, S_hist, Y_hist, L, part, st); break;
-    case 8: dir_apply_m<8>(ss, g, dir, S_hist, Y_hist, L, part, st); break;
-    default: return cudaErrorInvalidValue;
-    }
+#undef PLM_DIR
     k_dir_finish<<<L.nsites, 32, 0, st>>>(ss, part, L.si);
-    count_launches(2);
+    count_launches(3);
     return cudaGetLastError();
 }
 
-cudaError_t launch_lbfgs_trial(SiteState *ss, const float *theta, const float *g, float *dir,
+cudaError_t launch_lbfgs_trial(SiteState *ss, const float *theta, const float *dir,
                                float *theta_t, __nv_bfloat16 *hi, __nv_bfloat16 *lo,
-                               const LbLayout &L, const SolveParams &p, double *part,
-                               cudaStream_t st)
+                               const LbLayout &L, double *part, cudaStream_t st)
 {
-    (void)p;
-    k_trial<<<lb_grid(k_trial, L.nchunks), LB_THREADS, 0, st>>>(ss, theta, g, dir, theta_t, hi,
-                                                                  lo, L.si, L.ci, L.nchunks, part);
+    k_trial<<<lb_grid(k_trial, L.nchunks), LB_THREADS, 0, st>>>(ss, theta, dir, theta_t, hi, lo,
+                                                                  L.si, L.ci, L.nchunks, part);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -729,11 +710,27 @@ cudaError_t launch_lbfgs_linesearch(SiteState *ss, const double *f_data, const f
 
 cudaError_t launch_lbfgs_commit(const SiteState *ss, float *theta, float *g,
                                 const float *theta_t, const float *g_t, float *S_hist,
-                                float *Y_hist, const LbLayout &L, double *part,
-                                const int *round_ptr, cudaStream_t st)
+                                float *Y_hist, const LbLayout &L, const SolveParams &p,
+                                double *part, const int *round_ptr, cudaStream_t st)
 {
-    k_commit<<<lb_grid(k_commit, L.nchunks), LB_THREADS, 0, st>>>(
-        ss, theta, g, theta_t, g_t, S_hist, Y_hist, L.si, L.ci, L.nchunks, L.vec4, round_ptr, part);
+#define PLM_COMMIT(MM)                                                                       \
+    case MM:                                                                                 \
+        k_commit<MM><<<lb_grid(k_commit<MM>, L.nchunks), LB_THREADS, 0, st>>>(               \
+            ss, theta, g, theta_t, g_t, S_hist, Y_hist, L.si, L.ci, L.nchunks, L.vec4,       \
+            round_ptr, part);                                                                \
+        break;
+    switch (p.m) {
+        PLM_COMMIT(1)
+        PLM_COMMIT(2)
+        PLM_COMMIT(3)
+        PLM_COMMIT(4)
+        PLM_COMMIT(5)
+        PLM_COMMIT(6)
+        PLM_COMMIT(7)
+        PLM_COMMIT(8)
+    default: return cudaErrorInvalidValue;
+    }
+#undef PLM_COMMIT
     count_launches(1);
     return cudaGetLastError();
 }

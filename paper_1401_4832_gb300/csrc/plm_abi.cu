@@ -648,10 +648,10 @@ plm_status solve_core(plm_ctx *ctx, Problem &P, const plm_opts &o, std::vector<S
     // solve needs about max over sites of that site's evaluations rounds.
     // The round runs eagerly or is replayed from one CUDA graph.
     // algorithmic bytes of the passes of one round, from the site states at
-    // its start (profiling only: each pass streams the elements of the sites
-    // it acts on, once per vector it reads or writes)
+    // its start and after it (profiling only: each pass streams the elements
+    // of the sites it acts on, once per vector it reads or writes)
     struct RoundBytes {
-        double dots = 0, apply = 0, trial = 0, ls = 0;
+        double dir = 0, trial = 0, ls = 0;
     } rb;
     std::vector<SiteState> snap;
     std::vector<double> site_bytes;  // 4 x streamed elements of each site
@@ -670,12 +670,12 @@ plm_status solve_core(plm_ctx *ctx, Problem &P, const plm_opts &o, std::vector<S
             const SiteState &x = snap[r];
             const double e = site_bytes[r];
             if (x.status == SITE_READY) {
-                rb.dots += 2.0 * x.hist * e;          // S_j, Y_j (y_n among them)
-                rb.apply += (2.0 * x.hist + 2.0) * e;  // g, S_j, Y_j in; d out
-            }
-            if (x.status == SITE_READY || x.status == SITE_SEARCHING) {
+                // g, S_j, Y_j, theta in; d, theta_t (+ hi, lo) out
+                rb.dir += (2.0 * x.hist + 4.0 + split_b) * e;
+                rb.ls += 2.0 * e;  // g_t, d in
+            } else if (x.status == SITE_SEARCHING) {
                 rb.trial += (3.0 + split_b) * e;  // theta, d in; theta_t (+ hi, lo) out
-                rb.ls += 2.0 * e;                 // g_t, d in
+                rb.ls += 2.0 * e;
             }
         }
         return PLM_OK;
@@ -688,21 +688,17 @@ plm_status solve_core(plm_ctx *ctx, Problem &P, const plm_opts &o, std::vector<S
         }
         CK(launch_round_begin(round_ptr, (int *)cnt, st));
         {
-            ProfScope ps(ctx, "lbfgs_dir_dots", rb.dots);
-            CK(launch_lbfgs_dir_dots((SiteState *)sst, (const float *)Sh, (const float *)Yh, P.L,
-                                     p, (double *)part, st));
-        }
-        {
-            ProfScope ps(ctx, "lbfgs_dir_apply", rb.apply);
-            CK(launch_lbfgs_dir_apply((SiteState *)sst, (const float *)g, (float *)dir,
-                                      (const float *)Sh, (const float *)Yh, P.L, p,
-                                      (double *)part, st));
+            ProfScope ps(ctx, "lbfgs_direction", rb.dir);
+            CK(launch_lbfgs_direction((SiteState *)sst, (const float *)g, (float *)dir,
+                                      (const float *)Sh, (const float *)Yh, (const float *)theta,
+                                      (float *)theta_t, (__nv_bfloat16 *)hi, (__nv_bfloat16 *)lo,
+                                      P.L, p, (double *)part, st));
         }
         {
             ProfScope ps(ctx, "lbfgs_trial", rb.trial);
-            CK(launch_lbfgs_trial((SiteState *)sst, (const float *)theta, (const float *)g,
-                                  (float *)dir, (float *)theta_t, (__nv_bfloat16 *)hi,
-                                  (__nv_bfloat16 *)lo, P.L, p, (double *)part, st));
+            CK(launch_lbfgs_trial((SiteState *)sst, (const float *)theta, (const float *)dir,
+                                  (float *)theta_t, (__nv_bfloat16 *)hi, (__nv_bfloat16 *)lo, P.L,
+                                  (double *)part, st));
         }
         CK(launch_active_flags((const SiteState *)sst, P.nsites, (uint8_t *)active, st));
         plm_status s2 = evaluate(ctx, o.prec, P, (const float *)w, (const float *)theta_t,
@@ -720,7 +716,7 @@ plm_status solve_core(plm_ctx *ctx, Problem &P, const plm_opts &o, std::vector<S
             ProfScope ps(ctx, "lbfgs_commit");
             CK(launch_lbfgs_commit((const SiteState *)sst, (float *)theta, (float *)g,
                                    (const float *)theta_t, (const float *)g_t, (float *)Sh,
-                                   (float *)Yh, P.L, (double *)part, round_ptr, st));
+                                   (float *)Yh, P.L, p, (double *)part, round_ptr, st));
         }
         if (ctx->prof) commit_rec = (int)ctx->prof_records.size() - 1;
         CK(cudaMemcpyAsync(hc, cnt, 5 * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -770,9 +766,13 @@ plm_status solve_core(plm_ctx *ctx, Problem &P, const plm_opts &o, std::vector<S
             int rd_now = 0;
             CK(cudaMemcpyAsync(&rd_now, round_ptr, sizeof(int), cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
+            // theta_t, theta, g_t, g in; s, y, theta, g out; and the stored
+            // pairs other than the new one for a site that iterates on
             double cb = 0.0;
             for (int r = 0; r < P.nsites; ++r)
-                if (snap[r].commit_round == rd_now) cb += 8.0 * site_bytes[r];
+                if (snap[r].commit_round == rd_now)
+                    cb += (8.0 + (snap[r].status == SITE_READY ? 2.0 * (snap[r].hist - 1) : 0.0)) *
+                          site_bytes[r];
             ctx->prof_records[commit_rec].bytes = cb;
         }
         if (hc[4])

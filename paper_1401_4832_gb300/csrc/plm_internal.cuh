@@ -86,7 +86,6 @@ struct SiteState {
     int trials;
     int iters;
     int hist, head;  // stored pairs, next ring slot
-    int neg_g;       // 1: the computed direction was not a descent direction; use -g
     int commit_round;  // line-search round whose trial point is committed (-1: none)
     int commit_slot;
     int pad_;
@@ -182,20 +181,19 @@ cudaError_t launch_lbfgs_init(SiteState *ss, const double *f, const float *g,
                               const LbLayout &L, const SolveParams &p, double *part,
                               cudaStream_t st);
 // direction d = -H g (compact representation) and line-search set-up
-// (in two passes: dots = S'y_n, Y'y_n and the small solve; apply = d and
-// the line-search set-up; sites not READY are skipped)
-cudaError_t launch_lbfgs_dir_dots(SiteState *ss, const float *S_hist, const float *Y_hist,
-                                  const LbLayout &L, const SolveParams &p, double *part,
-                                  cudaStream_t st);
-cudaError_t launch_lbfgs_dir_apply(SiteState *ss, const float *g, float *dir,
-                                   const float *S_hist, const float *Y_hist,
+// direction d = -H g of every READY site (compact representation, from the
+// S'y_n and Y'y_n the commit pass left in the partial records), the first
+// trial point theta_t = theta + alpha d of its line search (and the bf16
+// split), and the line-search set-up; sites not READY are skipped
+cudaError_t launch_lbfgs_direction(SiteState *ss, const float *g, float *dir,
+                                   const float *S_hist, const float *Y_hist, const float *theta,
+                                   float *theta_t, __nv_bfloat16 *hi, __nv_bfloat16 *lo,
                                    const LbLayout &L, const SolveParams &p, double *part,
                                    cudaStream_t st);
-cudaError_t launch_lbfgs_trial(SiteState *ss, const float *theta,
-                               const float *g, float *dir, float *theta_t,
-                               __nv_bfloat16 *hi, __nv_bfloat16 *lo,
-                               const LbLayout &L, const SolveParams &p, double *part,
-                               cudaStream_t st);
+// later trial points of the searches in progress
+cudaError_t launch_lbfgs_trial(SiteState *ss, const float *theta, const float *dir,
+                               float *theta_t, __nv_bfloat16 *hi, __nv_bfloat16 *lo,
+                               const LbLayout &L, double *part, cudaStream_t st);
 // consumes f_data[site] (data part of the objective at theta_t) and g_t; the
 // decision is taken per site.  counters[0] += #sites still searching,
 // counters[1] += #sites that became ready for a new direction.
@@ -204,11 +202,11 @@ cudaError_t launch_lbfgs_linesearch(SiteState *ss, const double *f_data, const f
                                     double *part, const int *round_ptr, int *counters,
                                     cudaStream_t st);
 // commits the steps accepted in this round: S, Y ring slots, theta <- theta_t,
-// g <- g_t
+// g <- g_t, and the inner products the next direction needs
 cudaError_t launch_lbfgs_commit(const SiteState *ss, float *theta, float *g,
                                 const float *theta_t, const float *g_t, float *S_hist,
-                                float *Y_hist, const LbLayout &L, double *part,
-                                const int *round_ptr, cudaStream_t st);
+                                float *Y_hist, const LbLayout &L, const SolveParams &p,
+                                double *part, const int *round_ptr, cudaStream_t st);
 // start of a line-search round: ++*round_ptr, counters[0] = 0
 cudaError_t launch_round_begin(int *round_ptr, int *counters, cudaStream_t st);
 // active[site] = 1 if the site is in a line search (its trial point needs an
