@@ -209,9 +209,19 @@ __device__ __forceinline__ void trial_penalty_split(const float4 x, size_t e, si
 // the small FP64 algebra of the compact form, one warp per site (the site's
 // matrices are staged in shared memory)
 template <int M>
-__global__ void k_dir_solve(SiteState *ss, const double *part, const SiteInfo *si)
+__global__ void k_dir_solve(SiteState *ss, const double *part, const SiteInfo *si,
+                            int *round_ptr, int *counters)
 {
     const int r = blockIdx.x;
+    if (r == 0 && threadIdx.x == 0) {
+        // start of a round: advance the round counter; keep the number of
+        // searches that continue from the last round (the trial pass exits
+        // at once when there are none) and clear this round's counts
+        *round_ptr += 1;
+        counters[2] = counters[0];
+        counters[0] = 0;
+        counters[1] = 0;
+    }
     SiteState &s = ss[r];
     if (s.status != SITE_READY) return;
     __shared__ double tot[2 * M + 2];
@@ -364,33 +374,38 @@ k_dir_apply(const SiteState *ss, const float *__restrict__ g, const float *__res
 // (rounding in FP32) drops the history: the site stays READY and takes the
 // steepest-descent direction in the next round (its trial point of this
 // round is not evaluated).
-__global__ void k_dir_finish(SiteState *ss, const double *part, const SiteInfo *si)
+__global__ void k_dir_finish(SiteState *ss, const double *part, const SiteInfo *si,
+                             uint8_t *active)
 {
     const int r = blockIdx.x;
     SiteState &s = ss[r];
-    if (s.status != SITE_READY) return;
-    const double dg0 = chunk_sum(part, si[r], 2);
-    if (threadIdx.x != 0) return;
-    if (!(dg0 < 0.0)) {
-        if (s.hist == 0) s.status = SITE_FAILED;  // -g itself is not a descent direction
-        s.hist = 0;
-        s.head = 0;
-        return;
+    if (s.status == SITE_READY) {
+        const double dg0 = chunk_sum(part, si[r], 2);
+        if (threadIdx.x == 0) {
+            if (!(dg0 < 0.0)) {
+                if (s.hist == 0) s.status = SITE_FAILED;  // -g itself is not a descent direction
+                s.hist = 0;
+                s.head = 0;
+            } else {
+                s.f0 = s.f;
+                s.dg0 = dg0;
+                s.a_prev = 0.0;
+                s.f_prev = s.f;
+                s.dg_prev = dg0;
+                s.a_lo = 0.0;
+                s.f_lo = s.f;
+                s.dg_lo = dg0;
+                s.a_hi = 0.0;
+                s.f_hi = 0.0;
+                s.dg_hi = 0.0;
+                s.phase = 0;
+                s.trials = 0;
+                s.status = SITE_SEARCHING;
+            }
+        }
     }
-    s.f0 = s.f;
-    s.dg0 = dg0;
-    s.a_prev = 0.0;
-    s.f_prev = s.f;
-    s.dg_prev = dg0;
-    s.a_lo = 0.0;
-    s.f_lo = s.f;
-    s.dg_lo = dg0;
-    s.a_hi = 0.0;
-    s.f_hi = 0.0;
-    s.dg_hi = 0.0;
-    s.phase = 0;
-    s.trials = 0;
-    s.status = SITE_SEARCHING;
+    // the sites this round evaluates
+    if (threadIdx.x == 0) active[r] = s.status == SITE_SEARCHING ? 1 : 0;
 }
 
 // ------------------------------------------------------------ line search
@@ -401,8 +416,9 @@ __global__ void __launch_bounds__(LB_THREADS)
 k_trial(const SiteState *ss, const float *__restrict__ theta, const float *__restrict__ dir,
         float *__restrict__ theta_t, __nv_bfloat16 *__restrict__ hi,
         __nv_bfloat16 *__restrict__ lo, const SiteInfo *si, const ChunkInfo *ci, int nchunks,
-        double *part)
+        double *part, const int *counters)
 {
+    if (counters[2] == 0) return;  // no search continues from the last round
     for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
         const Chunk ch = chunk_at(si, ci, c);
         const SiteState &s = ss[ch.site];
@@ -652,9 +668,10 @@ cudaError_t launch_lbfgs_init(SiteState *ss, const double *f, const float *g, co
 template <int M>
 static void dir_apply_m(SiteState *ss, const float *g, float *dir, const float *S,
                         const float *Y, const float *theta, float *theta_t, __nv_bfloat16 *hi,
-                        __nv_bfloat16 *lo, const LbLayout &L, double *part, cudaStream_t st)
+                        __nv_bfloat16 *lo, const LbLayout &L, double *part, int *round_ptr,
+                        int *counters, cudaStream_t st)
 {
-    k_dir_solve<M><<<L.nsites, 32, 0, st>>>(ss, part, L.si);
+    k_dir_solve<M><<<L.nsites, 32, 0, st>>>(ss, part, L.si, round_ptr, counters);
     k_dir_apply<M><<<lb_grid(k_dir_apply<M>, L.nchunks), LB_THREADS, 0, st>>>(
         ss, g, S, Y, dir, theta, theta_t, hi, lo, L.si, L.ci, L.nchunks, L.vec4, part);
 }
@@ -663,11 +680,13 @@ cudaError_t launch_lbfgs_direction(SiteState *ss, const float *g, float *dir,
                                    const float *S_hist, const float *Y_hist, const float *theta,
                                    float *theta_t, __nv_bfloat16 *hi, __nv_bfloat16 *lo,
                                    const LbLayout &L, const SolveParams &p, double *part,
+                                   int *round_ptr, int *counters, uint8_t *active,
                                    cudaStream_t st)
 {
 #define PLM_DIR(MM)                                                                          \
     case MM:                                                                                 \
-        dir_apply_m<MM>(ss, g, dir, S_hist, Y_hist, theta, theta_t, hi, lo, L, part, st);   \
+        dir_apply_m<MM>(ss, g, dir, S_hist, Y_hist, theta, theta_t, hi, lo, L, part,        \
+                        round_ptr, counters, st);                                            \
         break;
     switch (p.m) {
         PLM_DIR(1)
@@ -681,17 +700,18 @@ cudaError_t launch_lbfgs_direction(SiteState *ss, const float *g, float *dir,
     default: return cudaErrorInvalidValue;
     }
 #undef PLM_DIR
-    k_dir_finish<<<L.nsites, 32, 0, st>>>(ss, part, L.si);
+    k_dir_finish<<<L.nsites, 32, 0, st>>>(ss, part, L.si, active);
     count_launches(3);
     return cudaGetLastError();
 }
 
 cudaError_t launch_lbfgs_trial(SiteState *ss, const float *theta, const float *dir,
                                float *theta_t, __nv_bfloat16 *hi, __nv_bfloat16 *lo,
-                               const LbLayout &L, double *part, cudaStream_t st)
+                               const LbLayout &L, double *part, const int *counters,
+                               cudaStream_t st)
 {
-    k_trial<<<lb_grid(k_trial, L.nchunks), LB_THREADS, 0, st>>>(ss, theta, dir, theta_t, hi, lo,
-                                                                  L.si, L.ci, L.nchunks, part);
+    k_trial<<<lb_grid(k_trial, L.nchunks), LB_THREADS, 0, st>>>(
+        ss, theta, dir, theta_t, hi, lo, L.si, L.ci, L.nchunks, part, counters);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -731,37 +751,6 @@ cudaError_t launch_lbfgs_commit(const SiteState *ss, float *theta, float *g,
     default: return cudaErrorInvalidValue;
     }
 #undef PLM_COMMIT
-    count_launches(1);
-    return cudaGetLastError();
-}
-
-namespace {
-__global__ void k_round_inc(int *round_ptr, int *counters)
-{
-    *round_ptr += 1;
-    counters[0] = 0;  // sites still searching after this round
-    counters[1] = 0;  // sites that accept a step in this round and iterate on
-}
-}  // namespace
-
-namespace {
-__global__ void k_active(const SiteState *ss, int nsites, uint8_t *active)
-{
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r < nsites) active[r] = ss[r].status == SITE_SEARCHING ? 1 : 0;
-}
-}  // namespace
-
-cudaError_t launch_active_flags(const SiteState *ss, int nsites, uint8_t *active, cudaStream_t st)
-{
-    k_active<<<(nsites + 255) / 256, 256, 0, st>>>(ss, nsites, active);
-    count_launches(1);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_round_begin(int *round_ptr, int *counters, cudaStream_t st)
-{
-    k_round_inc<<<1, 1, 0, st>>>(round_ptr, counters);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -686,21 +686,21 @@ plm_status solve_core(plm_ctx *ctx, Problem &P, const plm_opts &o, std::vector<S
             plm_status s2 = count_round();
             if (s2) return s2;
         }
-        CK(launch_round_begin(round_ptr, (int *)cnt, st));
         {
+            // also starts the round (counter, counts) and sets the active flags
             ProfScope ps(ctx, "lbfgs_direction", rb.dir);
             CK(launch_lbfgs_direction((SiteState *)sst, (const float *)g, (float *)dir,
                                       (const float *)Sh, (const float *)Yh, (const float *)theta,
                                       (float *)theta_t, (__nv_bfloat16 *)hi, (__nv_bfloat16 *)lo,
-                                      P.L, p, (double *)part, st));
+                                      P.L, p, (double *)part, round_ptr, (int *)cnt,
+                                      (uint8_t *)active, st));
         }
         {
             ProfScope ps(ctx, "lbfgs_trial", rb.trial);
             CK(launch_lbfgs_trial((SiteState *)sst, (const float *)theta, (const float *)dir,
                                   (float *)theta_t, (__nv_bfloat16 *)hi, (__nv_bfloat16 *)lo, P.L,
-                                  (double *)part, st));
+                                  (double *)part, (const int *)cnt, st));
         }
-        CK(launch_active_flags((const SiteState *)sst, P.nsites, (uint8_t *)active, st));
         plm_status s2 = evaluate(ctx, o.prec, P, (const float *)w, (const float *)theta_t,
                                  (const __nv_bfloat16 *)hi, (const __nv_bfloat16 *)lo, p.lambda_h,
                                  p.lambda_Jp, (double *)fdat, (float *)g_t, tc_err,

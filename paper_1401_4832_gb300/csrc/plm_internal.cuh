@@ -189,11 +189,13 @@ cudaError_t launch_lbfgs_direction(SiteState *ss, const float *g, float *dir,
                                    const float *S_hist, const float *Y_hist, const float *theta,
                                    float *theta_t, __nv_bfloat16 *hi, __nv_bfloat16 *lo,
                                    const LbLayout &L, const SolveParams &p, double *part,
+                                   int *round_ptr, int *counters, uint8_t *active,
                                    cudaStream_t st);
 // later trial points of the searches in progress
 cudaError_t launch_lbfgs_trial(SiteState *ss, const float *theta, const float *dir,
                                float *theta_t, __nv_bfloat16 *hi, __nv_bfloat16 *lo,
-                               const LbLayout &L, double *part, cudaStream_t st);
+                               const LbLayout &L, double *part, const int *counters,
+                               cudaStream_t st);
 // consumes f_data[site] (data part of the objective at theta_t) and g_t; the
 // decision is taken per site.  counters[0] += #sites still searching,
 // counters[1] += #sites that became ready for a new direction.
@@ -207,12 +209,6 @@ cudaError_t launch_lbfgs_commit(const SiteState *ss, float *theta, float *g,
                                 const float *theta_t, const float *g_t, float *S_hist,
                                 float *Y_hist, const LbLayout &L, const SolveParams &p,
                                 double *part, const int *round_ptr, cudaStream_t st);
-// start of a line-search round: ++*round_ptr, counters[0] = 0
-cudaError_t launch_round_begin(int *round_ptr, int *counters, cudaStream_t st);
-// active[site] = 1 if the site is in a line search (its trial point needs an
-// evaluation), else 0; the evaluation kernels skip tiles without active sites
-cudaError_t launch_active_flags(const SiteState *ss, int nsites, uint8_t *active,
-                                cudaStream_t st);
 
 // ---- scores (k_scores.cu) ----
 cudaError_t launch_fn(const float *J, int N, int combine, double *fn,
