@@ -45,7 +45,7 @@ namespace plm {
 
 namespace {
 
-constexpr int LB_THREADS = 256;
+constexpr int LB_THREADS = 128;
 
 // sum K per-thread double-float values over the block (fixed order) and
 // write them as FP64: a butterfly of error-free FP32 pair additions inside
@@ -129,10 +129,10 @@ __device__ __forceinline__ float4 f4z() { return make_float4(0.f, 0.f, 0.f, 0.f)
 
 // ------------------------------------------------------------ start
 __global__ void __launch_bounds__(LB_THREADS)
-k_init_dots(const float *__restrict__ g, const SiteInfo *si, const ChunkInfo *ci, int nchunks,
+k_init_dots(const float *__restrict__ g, const SiteInfo *si, const ChunkInfo *ci, int c0, int c1,
             double *part)
 {
-    for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    for (int c = c0 + blockIdx.x; c < c1; c += gridDim.x) {
         const Chunk ch = chunk_at(si, ci, c);
         const float4 *g4 = (const float4 *)g + ch.base4;
         DF acc[1];
@@ -145,9 +145,9 @@ k_init_dots(const float *__restrict__ g, const SiteInfo *si, const ChunkInfo *ci
 }
 
 __global__ void k_init_finish(SiteState *ss, const double *__restrict__ f, const double *part,
-                              const SiteInfo *si, SolveParams p)
+                              const SiteInfo *si, int s0, SolveParams p)
 {
-    const int r = blockIdx.x;
+    const int r = s0 + blockIdx.x;
     const double gg = chunk_sum(part, si[r], 0);
     if (threadIdx.x != 0) return;
     SiteState &s = ss[r];
@@ -209,11 +209,11 @@ __device__ __forceinline__ void trial_penalty_split(const float4 x, size_t e, si
 // the small FP64 algebra of the compact form, one warp per site (the site's
 // matrices are staged in shared memory)
 template <int M>
-__global__ void k_dir_solve(SiteState *ss, const double *part, const SiteInfo *si,
+__global__ void k_dir_solve(SiteState *ss, const double *part, const SiteInfo *si, int s0,
                             int *round_ptr, int *counters)
 {
-    const int r = blockIdx.x;
-    if (r == 0 && threadIdx.x == 0) {
+    const int r = s0 + blockIdx.x;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
         // start of a round: advance the round counter; keep the number of
         // searches that continue from the last round (the trial pass exits
         // at once when there are none) and clear this round's counts
@@ -317,10 +317,10 @@ __global__ void __launch_bounds__(LB_THREADS, 3)
 k_dir_apply(const SiteState *ss, const float *__restrict__ g, const float *__restrict__ S,
             const float *__restrict__ Y, float *__restrict__ dir, const float *__restrict__ theta,
             float *__restrict__ theta_t, __nv_bfloat16 *__restrict__ hi,
-            __nv_bfloat16 *__restrict__ lo, const SiteInfo *si, const ChunkInfo *ci, int nchunks,
+            __nv_bfloat16 *__restrict__ lo, const SiteInfo *si, const ChunkInfo *ci, int c0, int c1,
             long long vec4, double *part)
 {
-    for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    for (int c = c0 + blockIdx.x; c < c1; c += gridDim.x) {
         const Chunk ch = chunk_at(si, ci, c);
         const SiteState &s = ss[ch.site];
         if (s.status != SITE_READY) continue;
@@ -374,10 +374,10 @@ k_dir_apply(const SiteState *ss, const float *__restrict__ g, const float *__res
 // (rounding in FP32) drops the history: the site stays READY and takes the
 // steepest-descent direction in the next round (its trial point of this
 // round is not evaluated).
-__global__ void k_dir_finish(SiteState *ss, const double *part, const SiteInfo *si,
+__global__ void k_dir_finish(SiteState *ss, const double *part, const SiteInfo *si, int s0,
                              uint8_t *active)
 {
-    const int r = blockIdx.x;
+    const int r = s0 + blockIdx.x;
     SiteState &s = ss[r];
     if (s.status == SITE_READY) {
         const double dg0 = chunk_sum(part, si[r], 2);
@@ -415,11 +415,11 @@ __global__ void k_dir_finish(SiteState *ss, const double *part, const SiteInfo *
 __global__ void __launch_bounds__(LB_THREADS)
 k_trial(const SiteState *ss, const float *__restrict__ theta, const float *__restrict__ dir,
         float *__restrict__ theta_t, __nv_bfloat16 *__restrict__ hi,
-        __nv_bfloat16 *__restrict__ lo, const SiteInfo *si, const ChunkInfo *ci, int nchunks,
+        __nv_bfloat16 *__restrict__ lo, const SiteInfo *si, const ChunkInfo *ci, int c0, int c1,
         double *part, const int *counters)
 {
     if (counters[2] == 0) return;  // no search continues from the last round
-    for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    for (int c = c0 + blockIdx.x; c < c1; c += gridDim.x) {
         const Chunk ch = chunk_at(si, ci, c);
         const SiteState &s = ss[ch.site];
         if (s.status != SITE_SEARCHING || s.trials == 0) continue;
@@ -443,9 +443,9 @@ k_trial(const SiteState *ss, const float *__restrict__ theta, const float *__res
 // partial g_t . d and ||g_t||^2 (slots 2 and 3; slots 0, 1 hold the penalty)
 __global__ void __launch_bounds__(LB_THREADS)
 k_ls_dots(const SiteState *ss, const float *__restrict__ g_t, const float *__restrict__ dir,
-          const SiteInfo *si, const ChunkInfo *ci, int nchunks, double *part)
+          const SiteInfo *si, const ChunkInfo *ci, int c0, int c1, double *part)
 {
-    for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    for (int c = c0 + blockIdx.x; c < c1; c += gridDim.x) {
         const Chunk ch = chunk_at(si, ci, c);
         const SiteState &s = ss[ch.site];
         if (s.status != SITE_SEARCHING) continue;
@@ -491,11 +491,11 @@ __device__ double safe_interp(double lo, double flo, double dlo, double hi, doub
 enum { LS_CONTINUE = 0, LS_ACCEPT = 1, LS_FAIL = 2 };
 
 __global__ void k_ls_decide(SiteState *ss, const double *__restrict__ f_data, const double *part,
-                            const SiteInfo *si, SolveParams p, const int *round_ptr,
+                            const SiteInfo *si, int s0, SolveParams p, const int *round_ptr,
                             int *counters)
 {
     const int round = *round_ptr;
-    const int r = blockIdx.x;
+    const int r = s0 + blockIdx.x;
     SiteState &s = ss[r];
     if (s.status != SITE_SEARCHING) return;
     __shared__ double t4[4];
@@ -575,10 +575,10 @@ __global__ void __launch_bounds__(LB_THREADS, 2)
 k_commit(const SiteState *ss, float *__restrict__ theta, float *__restrict__ g,
          const float *__restrict__ theta_t, const float *__restrict__ g_t,
          float *__restrict__ S, float *__restrict__ Y, const SiteInfo *si, const ChunkInfo *ci,
-         int nchunks, long long vec4, const int *round_ptr, double *part)
+         int c0, int c1, long long vec4, const int *round_ptr, double *part)
 {
     const int round = *round_ptr;
-    for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    for (int c = c0 + blockIdx.x; c < c1; c += gridDim.x) {
         const Chunk ch = chunk_at(si, ci, c);
         const SiteState &st = ss[ch.site];
         if (st.commit_round != round) continue;
@@ -653,14 +653,33 @@ int lb_grid(Kern k, int nchunks)
     return nchunks < slots ? (nchunks > 0 ? nchunks : 1) : slots;
 }
 
+// end of a round inside a device-side loop: count the round and continue
+// while a site is searching or about to iterate, no tensor-core wait timed
+// out and the round cap is not reached
+__global__ void k_round_cond(cudaGraphConditionalHandle h, int *counters, int max_rounds)
+{
+    const int rounds = ++counters[9];
+    const bool more =
+        (counters[0] + counters[1] > 0) && counters[4] == 0 && rounds < max_rounds;
+    cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
 }  // namespace
+
+cudaError_t launch_round_cond(cudaGraphConditionalHandle h, int *counters, int max_rounds,
+                              cudaStream_t st)
+{
+    k_round_cond<<<1, 1, 0, st>>>(h, counters, max_rounds);
+    count_launches(1);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_lbfgs_init(SiteState *ss, const double *f, const float *g, const LbLayout &L,
                               const SolveParams &p, double *part, cudaStream_t st)
 {
-    k_init_dots<<<lb_grid(k_init_dots, L.nchunks), LB_THREADS, 0, st>>>(g, L.si, L.ci, L.nchunks,
+    k_init_dots<<<lb_grid(k_init_dots, L.c1 - L.c0), LB_THREADS, 0, st>>>(g, L.si, L.ci, L.c0, L.c1,
                                                                       part);
-    k_init_finish<<<L.nsites, 32, 0, st>>>(ss, f, part, L.si, p);
+    k_init_finish<<<L.nsites, 32, 0, st>>>(ss, f, part, L.si, L.s0, p);
     count_launches(2);
     return cudaGetLastError();
 }
@@ -671,9 +690,9 @@ static void dir_apply_m(SiteState *ss, const float *g, float *dir, const float *
                         __nv_bfloat16 *lo, const LbLayout &L, double *part, int *round_ptr,
                         int *counters, cudaStream_t st)
 {
-    k_dir_solve<M><<<L.nsites, 32, 0, st>>>(ss, part, L.si, round_ptr, counters);
-    k_dir_apply<M><<<lb_grid(k_dir_apply<M>, L.nchunks), LB_THREADS, 0, st>>>(
-        ss, g, S, Y, dir, theta, theta_t, hi, lo, L.si, L.ci, L.nchunks, L.vec4, part);
+    k_dir_solve<M><<<L.nsites, 32, 0, st>>>(ss, part, L.si, L.s0, round_ptr, counters);
+    k_dir_apply<M><<<lb_grid(k_dir_apply<M>, L.c1 - L.c0), LB_THREADS, 0, st>>>(
+        ss, g, S, Y, dir, theta, theta_t, hi, lo, L.si, L.ci, L.c0, L.c1, L.vec4, part);
 }
 
 cudaError_t launch_lbfgs_direction(SiteState *ss, const float *g, float *dir,
@@ -700,7 +719,7 @@ cudaError_t launch_lbfgs_direction(SiteState *ss, const float *g, float *dir,
     default: return cudaErrorInvalidValue;
     }
 #undef PLM_DIR
-    k_dir_finish<<<L.nsites, 32, 0, st>>>(ss, part, L.si, active);
+    k_dir_finish<<<L.nsites, 32, 0, st>>>(ss, part, L.si, L.s0, active);
     count_launches(3);
     return cudaGetLastError();
 }
@@ -710,8 +729,8 @@ cudaError_t launch_lbfgs_trial(SiteState *ss, const float *theta, const float *d
                                const LbLayout &L, double *part, const int *counters,
                                cudaStream_t st)
 {
-    k_trial<<<lb_grid(k_trial, L.nchunks), LB_THREADS, 0, st>>>(
-        ss, theta, dir, theta_t, hi, lo, L.si, L.ci, L.nchunks, part, counters);
+    k_trial<<<lb_grid(k_trial, L.c1 - L.c0), LB_THREADS, 0, st>>>(
+        ss, theta, dir, theta_t, hi, lo, L.si, L.ci, L.c0, L.c1, part, counters);
     count_launches(1);
     return cudaGetLastError();
 }
@@ -721,9 +740,9 @@ cudaError_t launch_lbfgs_linesearch(SiteState *ss, const double *f_data, const f
                                     double *part, const int *round_ptr, int *counters,
                                     cudaStream_t st)
 {
-    k_ls_dots<<<lb_grid(k_ls_dots, L.nchunks), LB_THREADS, 0, st>>>(ss, g_t, dir, L.si, L.ci,
-                                                                      L.nchunks, part);
-    k_ls_decide<<<L.nsites, 32, 0, st>>>(ss, f_data, part, L.si, p, round_ptr, counters);
+    k_ls_dots<<<lb_grid(k_ls_dots, L.c1 - L.c0), LB_THREADS, 0, st>>>(ss, g_t, dir, L.si, L.ci,
+                                                                        L.c0, L.c1, part);
+    k_ls_decide<<<L.nsites, 32, 0, st>>>(ss, f_data, part, L.si, L.s0, p, round_ptr, counters);
     count_launches(2);
     return cudaGetLastError();
 }
@@ -735,8 +754,8 @@ cudaError_t launch_lbfgs_commit(const SiteState *ss, float *theta, float *g,
 {
 #define PLM_COMMIT(MM)                                                                       \
     case MM:                                                                                 \
-        k_commit<MM><<<lb_grid(k_commit<MM>, L.nchunks), LB_THREADS, 0, st>>>(               \
-            ss, theta, g, theta_t, g_t, S_hist, Y_hist, L.si, L.ci, L.nchunks, L.vec4,       \
+        k_commit<MM><<<lb_grid(k_commit<MM>, L.c1 - L.c0), LB_THREADS, 0, st>>>(         \
+            ss, theta, g, theta_t, g_t, S_hist, Y_hist, L.si, L.ci, L.c0, L.c1, L.vec4,     \
             round_ptr, part);                                                                \
         break;
     switch (p.m) {

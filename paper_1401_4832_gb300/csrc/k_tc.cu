@@ -866,6 +866,7 @@ __global__ void k_tc_finish(const __grid_constant__ TcBatch b)
     const FamDesc &F = b.f[blockIdx.x];
     const int nbt = F.BP / TC_M;
     for (int r = threadIdx.x; r < F.N; r += blockDim.x) {
+        if (F.active && !F.active[r]) continue;  // not evaluated: keep its value
         double t = 0.0;
         for (int y = 0; y < nbt; ++y) t += F.partial[(size_t)y * F.N + r];
         F.f_data[r] = -t / F.beff;

@@ -33,6 +33,7 @@ struct ProfRecord {
 struct plm_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
+    cudaStream_t aux = nullptr;  // second stream of the pipelined solve (created on first use)
     std::string err;
     std::map<std::string, DevBuf> bufs;
     int *host_counters = nullptr;  // pinned
@@ -267,6 +268,7 @@ struct Problem {
     int maxB = 0, maxN = 0;
     size_t tc_scratch = 0;
     LbLayout L{};
+    std::vector<int> site_chunk0;  // first chunk of each site (host copy of the tables)
     std::vector<TcBatch> tcb;  // the families in launches of at most MAX_FAM
     bool tc_ready = false;
     TcConfig tc_cfg;
@@ -326,6 +328,9 @@ plm_status build_lbfgs_tables(plm_ctx *ctx, Problem &P)
             si.push_back(x);
         }
     }
+    P.site_chunk0.resize(si.size() + 1);
+    for (size_t r = 0; r < si.size(); ++r) P.site_chunk0[r] = si[r].chunk0;
+    P.site_chunk0[si.size()] = (int)ci.size();
     void *dsi, *dci;
     CK(ws(ctx, "lb_site_info", si.size() * sizeof(SiteInfo), &dsi));
     CK(ws(ctx, "lb_chunk_info", ci.size() * sizeof(ChunkInfo), &dci));
@@ -336,8 +341,10 @@ plm_status build_lbfgs_tables(plm_ctx *ctx, Problem &P)
     P.nchunks = (int)ci.size();
     P.L.si = (const SiteInfo *)dsi;
     P.L.ci = (const ChunkInfo *)dci;
+    P.L.s0 = 0;
     P.L.nsites = P.nsites;
-    P.L.nchunks = P.nchunks;
+    P.L.c0 = 0;
+    P.L.c1 = P.nchunks;
     P.L.vec4 = (long long)(P.total / 4);
     return PLM_OK;
 }
@@ -463,9 +470,9 @@ plm_status autotune_tc(plm_ctx *ctx, Problem &P, int *tc_err)
 plm_status evaluate(plm_ctx *ctx, plm_precision prec, Problem &P, const float *w,
                     const float *theta, const __nv_bfloat16 *hi, const __nv_bfloat16 *lo,
                     double lambda_h, double lambda_Jp, double *f_data, float *G, int *tc_err,
-                    const uint8_t *active = nullptr)
+                    const uint8_t *active = nullptr, cudaStream_t on = nullptr)
 {
-    cudaStream_t st = ctx->stream;
+    cudaStream_t st = on ? on : ctx->stream;
     if (prec == PLM_FP32_EXACT) {
         void *L, *D, *part;
         size_t lmax = 0, pmax = 0;
@@ -599,10 +606,10 @@ plm_status solve_core(plm_ctx *ctx, Problem &P, const plm_opts &o, std::vector<S
     CK(ws(ctx, "Y_hist", tb * o.lbfgs_m, &Yh));
     CK(ws(ctx, "site_state", (size_t)P.nsites * sizeof(SiteState), &sst));
     CK(ws(ctx, "fdata", (size_t)P.nsites * sizeof(double), &fdat));
-    CK(ws(ctx, "counters", 16 * sizeof(int), &cnt));
+    CK(ws(ctx, "counters", 32 * sizeof(int), &cnt));  // 16 per lane (see below)
     CK(ws(ctx, "lb_part", (size_t)P.nchunks * LB_PART * sizeof(double), &part));
     void *active;
-    CK(ws(ctx, "active", (size_t)P.nsites, &active));
+    CK(ws(ctx, "active", 2 * (size_t)P.nsites, &active));  // one flag array per lane
     if (o.prec == PLM_SPLIT_BF16) {
         CK(ws(ctx, "theta_hi", P.total * 2, &hi));
         CK(ws(ctx, "theta_lo", P.total * 2, &lo));
@@ -628,7 +635,8 @@ plm_status solve_core(plm_ctx *ctx, Problem &P, const plm_opts &o, std::vector<S
     }
     int evals = 0;
     int *tc_err = (int *)cnt + 4;  // tensor-core timeout word, read back with the counters
-    CK(cudaMemsetAsync(cnt, 0, 16 * sizeof(int), st));
+    CK(cudaMemsetAsync(cnt, 0, 32 * sizeof(int), st));
+    CK(cudaMemsetAsync(active, 0, 2 * (size_t)P.nsites, st));
     s = evaluate(ctx, o.prec, P, (const float *)w, (const float *)theta,
                  (const __nv_bfloat16 *)hi, (const __nv_bfloat16 *)lo, p.lambda_h, p.lambda_Jp,
                  (double *)fdat, (float *)g, tc_err);
@@ -637,19 +645,67 @@ plm_status solve_core(plm_ctx *ctx, Problem &P, const plm_opts &o, std::vector<S
     CK(launch_lbfgs_init((SiteState *)sst, (const double *)fdat, (const float *)g, P.L, p,
                          (double *)part, st));
 
-    int *hc = ctx->host_counters;
-    int *round_ptr = (int *)cnt + 8;  // device round counter (commit matching)
-    // One round advances every live site by one evaluation: sites whose last
-    // trial was accepted (READY) first form their next direction, then every
-    // searching site takes its trial point, all trial points are evaluated
-    // together and each site's line search decides.  A site never waits for
-    // the line searches of other sites, and its iterates do not depend on
-    // them (each site's objective involves only its own row block), so the
-    // solve needs about max over sites of that site's evaluations rounds.
-    // The round runs eagerly or is replayed from one CUDA graph.
+    // ---- the rounds.  One round advances every live site of a lane by one
+    // evaluation: sites whose last trial was accepted (READY) first form
+    // their next direction and first trial point, searching sites take their
+    // next trial point, all trial points of the lane are evaluated together
+    // and each site's line search decides.  A site never waits for the line
+    // searches of other sites, and its iterates do not depend on them (each
+    // site's objective involves only its own row block), so a lane needs
+    // about max over its sites of that site's evaluations rounds.
+    //
+    // With one family on the tensor-core path the sites are split into two
+    // lanes at a boundary shared by the logits site groups and the
+    // 128-row gradient tiles.  Each lane has its own counters, round number
+    // and active flags, its own stream and CUDA graph; lane 1's graph is
+    // rotated by half a round (evaluate, decide, commit, then the next
+    // direction), so one lane's tensor-core evaluation runs while the other
+    // lane streams its L-BFGS vectors.  Every other case runs one lane.
+    struct Lane {
+        LbLayout L;
+        int *cnt;          // 16 ints: [0] searching, [1] ready, [2] continuing, [4] tc error, [8] round
+        uint8_t *active;   // evaluation flags (nsites; only this lane's sites set)
+        int *hc;           // pinned host copy of cnt[0..4]
+        cudaStream_t st;
+        cudaGraphExec_t graph = nullptr;
+        bool rotated = false, done = false;
+        int rounds = 0;
+    };
+    const bool use_graph = o.use_graph && st != nullptr && !ctx->prof;
+    int split = 0;  // first site of lane 1 (0: one lane)
+    if (use_graph && nf == 1 && o.prec == PLM_SPLIT_BF16 && P.tc_tuned) {
+        int unit = 16;  // 16 sites = 384 rows = three gradient row tiles
+        while (unit % P.tc_cfg.lg_sites) unit += 16;
+        const int N = P.fam[0].d.N;
+        const int h = (N / 2 + unit / 2) / unit * unit;
+        if (h >= unit && N - h >= unit) split = h;
+    }
+    std::vector<Lane> lanes(split ? 2 : 1);
+    if (split && !ctx->aux) {
+        cudaError_t e = cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking);
+        if (e) return cuda_fail(ctx, e, "cudaStreamCreateWithFlags");
+    }
+    for (size_t k = 0; k < lanes.size(); ++k) {
+        Lane &ln = lanes[k];
+        ln.L = P.L;
+        if (split) {
+            const int s_lo = k == 0 ? 0 : split, s_hi = k == 0 ? split : P.nsites;
+            ln.L.s0 = s_lo;
+            ln.L.nsites = s_hi - s_lo;
+            ln.L.c0 = k == 0 ? 0 : P.site_chunk0[split];
+            ln.L.c1 = k == 0 ? P.site_chunk0[split] : P.nchunks;
+        }
+        ln.cnt = (int *)cnt + 16 * k;
+        ln.active = (uint8_t *)active + (size_t)P.nsites * k;
+        ln.hc = ctx->host_counters + 32 * k;
+        ln.st = k == 0 ? st : ctx->aux;
+        ln.rotated = k == 1;
+    }
+
     // algorithmic bytes of the passes of one round, from the site states at
-    // its start and after it (profiling only: each pass streams the elements
-    // of the sites it acts on, once per vector it reads or writes)
+    // its start and after it (profiling only, one lane: each pass streams
+    // the elements of the sites it acts on, once per vector it reads or
+    // writes)
     struct RoundBytes {
         double dir = 0, trial = 0, ls = 0;
     } rb;
@@ -681,7 +737,8 @@ plm_status solve_core(plm_ctx *ctx, Problem &P, const plm_opts &o, std::vector<S
         return PLM_OK;
     };
     int commit_rec = -1;  // profile record of this round's commit pass
-    auto round_step = [&]() -> plm_status {
+    // the three phases of a round
+    auto phase_dir = [&](Lane &ln) -> plm_status {
         if (ctx->prof) {
             plm_status s2 = count_round();
             if (s2) return s2;
@@ -692,93 +749,174 @@ plm_status solve_core(plm_ctx *ctx, Problem &P, const plm_opts &o, std::vector<S
             CK(launch_lbfgs_direction((SiteState *)sst, (const float *)g, (float *)dir,
                                       (const float *)Sh, (const float *)Yh, (const float *)theta,
                                       (float *)theta_t, (__nv_bfloat16 *)hi, (__nv_bfloat16 *)lo,
-                                      P.L, p, (double *)part, round_ptr, (int *)cnt,
-                                      (uint8_t *)active, st));
+                                      ln.L, p, (double *)part, ln.cnt + 8, ln.cnt, ln.active,
+                                      ln.st));
         }
         {
             ProfScope ps(ctx, "lbfgs_trial", rb.trial);
             CK(launch_lbfgs_trial((SiteState *)sst, (const float *)theta, (const float *)dir,
-                                  (float *)theta_t, (__nv_bfloat16 *)hi, (__nv_bfloat16 *)lo, P.L,
-                                  (double *)part, (const int *)cnt, st));
+                                  (float *)theta_t, (__nv_bfloat16 *)hi, (__nv_bfloat16 *)lo,
+                                  ln.L, (double *)part, (const int *)ln.cnt, ln.st));
         }
-        plm_status s2 = evaluate(ctx, o.prec, P, (const float *)w, (const float *)theta_t,
-                                 (const __nv_bfloat16 *)hi, (const __nv_bfloat16 *)lo, p.lambda_h,
-                                 p.lambda_Jp, (double *)fdat, (float *)g_t, tc_err,
-                                 (const uint8_t *)active);
-        if (s2) return s2;
+        return PLM_OK;
+    };
+    auto phase_eval = [&](Lane &ln) -> plm_status {
+        return evaluate(ctx, o.prec, P, (const float *)w, (const float *)theta_t,
+                        (const __nv_bfloat16 *)hi, (const __nv_bfloat16 *)lo, p.lambda_h,
+                        p.lambda_Jp, (double *)fdat, (float *)g_t, ln.cnt + 4, ln.active, ln.st);
+    };
+    auto phase_post = [&](Lane &ln, bool copy_counts) -> plm_status {
         {
             ProfScope ps(ctx, "lbfgs_linesearch", rb.ls);
             CK(launch_lbfgs_linesearch((SiteState *)sst, (const double *)fdat, (const float *)g_t,
-                                       (const float *)dir, P.L, p, (double *)part, round_ptr,
-                                       (int *)cnt, st));
+                                       (const float *)dir, ln.L, p, (double *)part, ln.cnt + 8,
+                                       ln.cnt, ln.st));
         }
         {
             ProfScope ps(ctx, "lbfgs_commit");
             CK(launch_lbfgs_commit((const SiteState *)sst, (float *)theta, (float *)g,
                                    (const float *)theta_t, (const float *)g_t, (float *)Sh,
-                                   (float *)Yh, P.L, p, (double *)part, round_ptr, st));
+                                   (float *)Yh, ln.L, p, (double *)part, ln.cnt + 8, ln.st));
         }
         if (ctx->prof) commit_rec = (int)ctx->prof_records.size() - 1;
-        CK(cudaMemcpyAsync(hc, cnt, 5 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        if (copy_counts)
+            CK(cudaMemcpyAsync(ln.hc, ln.cnt, 5 * sizeof(int), cudaMemcpyDeviceToHost, ln.st));
         return PLM_OK;
     };
-    cudaGraphExec_t g_round = nullptr;
-    const bool use_graph = o.use_graph && st != nullptr && !ctx->prof;
-    int graph_kernels = 0;  // kernels one replay of the round graph launches
-    if (use_graph) {
-        cudaGraph_t gr;
-        const long long before = g_launches.load();
-        CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-        plm_status s2 = round_step();
-        cudaError_t e = cudaStreamEndCapture(st, &gr);
-        // capture records the launches without running them: count replays instead
-        graph_kernels = (int)(g_launches.load() - before);
-        count_launches(-graph_kernels);
-        if (s2) return s2;
-        if (e) return cuda_fail(ctx, e, "cudaStreamEndCapture");
-        e = cudaGraphInstantiate(&g_round, gr, 0);
-        cudaGraphDestroy(gr);
-        if (e) return cuda_fail(ctx, e, "cudaGraphInstantiate");
-    }
-    struct GraphGuard {
-        cudaGraphExec_t a;
-        ~GraphGuard()
-        {
-            if (a) cudaGraphExecDestroy(a);
-        }
-    } guard{g_round};
     // every site stops within max_iter iterations of at most max_ls trials
     const long long max_rounds = (long long)o.max_iter * o.max_ls + 1;
-    for (long long rd = 0; rd < max_rounds; ++rd) {
-        if (use_graph) {
-            CK(cudaGraphLaunch(g_round, st));
-            count_launches(graph_kernels);
+    const int max_rounds_i = (int)std::min<long long>(max_rounds, 1 << 30);
+    // one round; inside a device loop it ends by setting the loop condition
+    // instead of copying the counts to the host
+    auto round_step = [&](Lane &ln, cudaGraphConditionalHandle cond, bool in_loop) -> plm_status {
+        plm_status s2;
+        if (ln.rotated) {
+            if ((s2 = phase_eval(ln)) || (s2 = phase_post(ln, !in_loop))) return s2;
+            if (in_loop) CK(launch_round_cond(cond, ln.cnt, max_rounds_i, ln.st));
+            if ((s2 = phase_dir(ln))) return s2;
         } else {
-            s = round_step();
-            if (s) return s;
+            if ((s2 = phase_dir(ln)) || (s2 = phase_eval(ln)) || (s2 = phase_post(ln, !in_loop)))
+                return s2;
+            if (in_loop) CK(launch_round_cond(cond, ln.cnt, max_rounds_i, ln.st));
         }
-        evals++;
-        CK(cudaStreamSynchronize(st));
-        if (ctx->prof && commit_rec >= 0) {
-            // committed sites: theta_t, theta, g_t, g in; S, Y, theta, g out
-            CK(cudaMemcpyAsync(snap.data(), sst, snap.size() * sizeof(SiteState),
-                               cudaMemcpyDeviceToHost, st));
-            int rd_now = 0;
-            CK(cudaMemcpyAsync(&rd_now, round_ptr, sizeof(int), cudaMemcpyDeviceToHost, st));
-            CK(cudaStreamSynchronize(st));
-            // theta_t, theta, g_t, g in; s, y, theta, g out; and the stored
-            // pairs other than the new one for a site that iterates on
-            double cb = 0.0;
-            for (int r = 0; r < P.nsites; ++r)
-                if (snap[r].commit_round == rd_now)
-                    cb += (8.0 + (snap[r].status == SITE_READY ? 2.0 * (snap[r].hist - 1) : 0.0)) *
-                          site_bytes[r];
-            ctx->prof_records[commit_rec].bytes = cb;
+        return PLM_OK;
+    };
+    struct GraphGuard {
+        std::vector<Lane> *l;
+        ~GraphGuard()
+        {
+            for (auto &ln : *l)
+                if (ln.graph) cudaGraphExecDestroy(ln.graph);
         }
-        if (hc[4])
-            return fail(ctx, PLM_ETIMEOUT, "tensor-core pipeline wait timed out (code 0x%x)",
-                        hc[4]);
-        if (hc[0] == 0 && hc[1] == 0) break;  // no site searching or about to iterate
+    } guard{&lanes};
+    cudaEvent_t fork = nullptr, join = nullptr;
+    struct EventGuard {
+        cudaEvent_t *a, *b;
+        ~EventGuard()
+        {
+            if (*a) cudaEventDestroy(*a);
+            if (*b) cudaEventDestroy(*b);
+        }
+    } eguard{&fork, &join};
+    if (split) {
+        // lane 1 starts after everything queued so far on the caller's stream
+        CK(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
+        CK(cudaEventRecord(fork, st));
+        CK(cudaStreamWaitEvent(ctx->aux, fork, 0));
+        // the first half round of the rotated lane
+        s = phase_dir(lanes[1]);
+        if (s) return s;
+    }
+    if (use_graph) {
+        // each lane's rounds run as one CUDA graph: a while node whose body
+        // is the round, the loop condition set on the device at the end of
+        // each round, so no round waits for the host
+        int body_kernels = 0;
+        for (auto &ln : lanes) {
+            cudaGraph_t top;
+            CK(cudaGraphCreate(&top, 0));
+            struct TopGuard {
+                cudaGraph_t g;
+                ~TopGuard() { cudaGraphDestroy(g); }
+            } tg{top};
+            cudaGraphConditionalHandle cond;
+            CK(cudaGraphConditionalHandleCreate(&cond, top, 1, cudaGraphCondAssignDefault));
+            cudaGraphNodeParams np = {};
+            np.type = cudaGraphNodeTypeConditional;
+            np.conditional.handle = cond;
+            np.conditional.type = cudaGraphCondTypeWhile;
+            np.conditional.size = 1;
+            cudaGraphNode_t node;
+            CK(cudaGraphAddNode(&node, top, nullptr, nullptr, 0, &np));
+            cudaGraph_t body = np.conditional.phGraph_out[0];
+            const long long before = g_launches.load();
+            CK(cudaStreamBeginCaptureToGraph(ln.st, body, nullptr, nullptr, 0,
+                                             cudaStreamCaptureModeThreadLocal));
+            plm_status s2 = round_step(ln, cond, true);
+            cudaGraph_t captured;
+            cudaError_t e = cudaStreamEndCapture(ln.st, &captured);
+            // capture records the launches without running them: counted per round below
+            body_kernels = (int)(g_launches.load() - before);
+            count_launches(-body_kernels);
+            if (s2) return s2;
+            if (e) return cuda_fail(ctx, e, "cudaStreamEndCapture");
+            e = cudaGraphInstantiate(&ln.graph, top, 0);
+            if (e) return cuda_fail(ctx, e, "cudaGraphInstantiate");
+        }
+        for (auto &ln : lanes) CK(cudaGraphLaunch(ln.graph, ln.st));
+        for (auto &ln : lanes) {
+            CK(cudaMemcpyAsync(ln.hc, ln.cnt, 10 * sizeof(int), cudaMemcpyDeviceToHost, ln.st));
+            CK(cudaStreamSynchronize(ln.st));
+            ln.rounds = ln.hc[9];
+            count_launches(body_kernels * ln.rounds);
+            if (ln.hc[4])
+                return fail(ctx, PLM_ETIMEOUT, "tensor-core pipeline wait timed out (code 0x%x)",
+                            ln.hc[4]);
+        }
+    } else {
+        for (long long rd = 0; rd < max_rounds; ++rd) {
+            for (auto &ln : lanes) {
+                if (ln.done) continue;
+                s = round_step(ln, 0, false);
+                if (s) return s;
+                ln.rounds++;
+            }
+            for (auto &ln : lanes) CK(cudaStreamSynchronize(ln.st));
+            if (ctx->prof && commit_rec >= 0) {
+                // committed sites: theta_t, theta, g_t, g in; s, y, theta, g out; and
+                // the stored pairs other than the new one for a site that iterates on
+                CK(cudaMemcpyAsync(snap.data(), sst, snap.size() * sizeof(SiteState),
+                                   cudaMemcpyDeviceToHost, st));
+                int rd_now = 0;
+                CK(cudaMemcpyAsync(&rd_now, lanes[0].cnt + 8, sizeof(int),
+                                   cudaMemcpyDeviceToHost, st));
+                CK(cudaStreamSynchronize(st));
+                double cb = 0.0;
+                for (int r = 0; r < P.nsites; ++r)
+                    if (snap[r].commit_round == rd_now)
+                        cb += (8.0 + (snap[r].status == SITE_READY ? 2.0 * (snap[r].hist - 1)
+                                                                    : 0.0)) *
+                              site_bytes[r];
+                ctx->prof_records[commit_rec].bytes = cb;
+            }
+            bool all_done = true;
+            for (auto &ln : lanes) {
+                if (ln.hc[4])
+                    return fail(ctx, PLM_ETIMEOUT,
+                                "tensor-core pipeline wait timed out (code 0x%x)", ln.hc[4]);
+                // no site searching or about to iterate
+                if (!ln.done && ln.hc[0] == 0 && ln.hc[1] == 0) ln.done = true;
+                all_done = all_done && ln.done;
+            }
+            if (all_done) break;
+        }
+    }
+    for (auto &ln : lanes) evals = std::max(evals, 1 + ln.rounds);
+    if (split) {
+        // the caller's stream resumes after lane 1
+        CK(cudaEventRecord(join, ctx->aux));
+        CK(cudaStreamWaitEvent(st, join, 0));
     }
 
     for (size_t f = 0; f < nf; ++f)
@@ -875,6 +1013,10 @@ plm_status plm_destroy(plm_ctx *c)
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
+    if (c->aux) {
+        cudaStreamSynchronize(c->aux);
+        cudaStreamDestroy(c->aux);
+    }
     for (auto &kv : c->bufs)
         if (kv.second.p) cudaFree(kv.second.p);
     if (c->host_counters) cudaFreeHost(c->host_counters);

@@ -170,10 +170,14 @@ struct ChunkInfo {
     int e0, e1;  // float4 range inside the site segment
 };
 
+// the sites a launch works on: sites s0 .. s0 + nsites - 1 and their chunks
+// c0 .. c1 - 1 (site and chunk indices are global: the tables describe the
+// whole problem)
 struct LbLayout {
     const SiteInfo *si;
     const ChunkInfo *ci;
-    int nsites, nchunks;
+    int s0, nsites;
+    int c0, c1;
     long long vec4;  // float4 stride between history slots (arena size / 4)
 };
 
@@ -209,6 +213,12 @@ cudaError_t launch_lbfgs_commit(const SiteState *ss, float *theta, float *g,
                                 const float *theta_t, const float *g_t, float *S_hist,
                                 float *Y_hist, const LbLayout &L, const SolveParams &p,
                                 double *part, const int *round_ptr, cudaStream_t st);
+
+// closes a round of a device-side loop (CUDA graph while node): counters[9]
+// counts the rounds; the loop goes on while counters[0] + counters[1] > 0,
+// counters[4] (tensor-core error) is 0 and fewer than max_rounds ran
+cudaError_t launch_round_cond(cudaGraphConditionalHandle h, int *counters, int max_rounds,
+                              cudaStream_t st);
 
 // ---- scores (k_scores.cu) ----
 cudaError_t launch_fn(const float *J, int N, int combine, double *fn,
