@@ -673,12 +673,24 @@ plm_status solve_core(plm_ctx *ctx, Problem &P, const plm_opts &o, std::vector<S
     };
     const bool use_graph = o.use_graph && st != nullptr && !ctx->prof;
     int split = 0;  // first site of lane 1 (0: one lane)
-    if (use_graph && nf == 1 && o.prec == PLM_SPLIT_BF16 && P.tc_tuned) {
-        int unit = 16;  // 16 sites = 384 rows = three gradient row tiles
-        while (unit % P.tc_cfg.lg_sites) unit += 16;
-        const int N = P.fam[0].d.N;
-        const int h = (N / 2 + unit / 2) / unit * unit;
-        if (h >= unit && N - h >= unit) split = h;
+    if (use_graph && o.prec == PLM_SPLIT_BF16 && P.tc_tuned) {
+        if (nf == 1) {
+            int unit = 16;  // 16 sites = 384 rows = three gradient row tiles
+            while (unit % P.tc_cfg.lg_sites) unit += 16;
+            const int N = P.fam[0].d.N;
+            const int h = (N / 2 + unit / 2) / unit * unit;
+            if (h >= unit && N - h >= unit) split = h;
+        } else {
+            // whole families per lane (no tile straddles a family), the
+            // boundary that best balances the evaluation work B_f N_f^2
+            std::vector<double> cum(nf + 1, 0.0);
+            for (size_t f = 0; f < nf; ++f)
+                cum[f + 1] = cum[f] + (double)P.fam[f].d.B * P.fam[f].d.N * P.fam[f].d.N;
+            size_t best = 1;
+            for (size_t k = 1; k < nf; ++k)
+                if (std::fabs(2 * cum[k] - cum[nf]) < std::fabs(2 * cum[best] - cum[nf])) best = k;
+            split = P.fam[best].site0;
+        }
     }
     std::vector<Lane> lanes(split ? 2 : 1);
     if (split && !ctx->aux) {
