@@ -77,6 +77,14 @@ def _load():
         lib.orc_apc.restype = None
         lib.orc_topL.argtypes = [P, I, I, I, P]
         lib.orc_topL.restype = I
+        lib.orc_sym_nparams.argtypes = [I, I]
+        lib.orc_sym_nparams.restype = ctypes.c_size_t
+        lib.orc_sym_expand.argtypes = [P, I, I, P, P]
+        lib.orc_sym_expand.restype = None
+        lib.orc_sym_objgrad.argtypes = [P, P, D, I, I, I, P, D, D, P]
+        lib.orc_sym_objgrad.restype = D
+        lib.orc_solve_symmetric.argtypes = [P, P, D, I, I, I, D, D, D, I, I, P, P, P, P, P]
+        lib.orc_solve_symmetric.restype = I
         _lib = lib
         return lib
 
@@ -249,6 +257,73 @@ def plmdca(S, x=0.8, lambda_h=0.01, lambda_J=0.01, gtol=1e-9, m=5,
     B, N = S.shape
     mcount, w, w32, beff = reweight(S, x)
     h, J, info = solve(S, w, beff, lambda_h, lambda_J, gtol, m, max_iter)
+    fn, cfn = scores(J)
+    top = topL(cfn, N if L is None else L, min_sep)
+    return dict(m=mcount, w=w, w32=w32, beff=beff, h=h, J=J, info=info,
+                fn=fn, cfn=cfn, top=top)
+
+
+# ---------------------------------------------------------------- symmetric
+def sym_nparams(N, q=Q):
+    """Parameters of the symmetric problem: N q fields + one q x q block per
+    pair i < j (Sec. 6: N q (1 + (N - 1) q / 2))."""
+    return int(_load().orc_sym_nparams(N, q))
+
+
+def sym_expand(x, N, q=Q):
+    """x = [h | J_ij (i < j, pair order (0,1), (0,2), ...)] -> per-site
+    layout (h[N,q], J[N,q,N,q]) with J[j,l,i,k] = J[i,k,j,l] (both copies)."""
+    x = np.ascontiguousarray(x, np.float64)
+    h = np.zeros((N, q))
+    J = np.zeros((N, q, N, q))
+    _load().orc_sym_expand(_ptr(x), N, q, _ptr(h), _ptr(J))
+    return h, J
+
+
+def sym_objgrad(S, w, beff, x, lambda_h=0.01, lambda_J=0.01, grad=True, q=Q):
+    """l_pseudo + R_l2 (Eqs. npll_1, l2reg) at x and its gradient in x."""
+    S = _msa(S)
+    B, N = S.shape
+    w = np.ascontiguousarray(w, np.float64)
+    x = np.ascontiguousarray(x, np.float64)
+    g = np.zeros_like(x) if grad else None
+    f = _load().orc_sym_objgrad(_ptr(S), _ptr(w), float(beff), B, N, q, _ptr(x),
+                                float(lambda_h), float(lambda_J),
+                                _ptr(g) if grad else None)
+    return (f, g) if grad else f
+
+
+def solve_symmetric(S, w, beff, lambda_h=0.01, lambda_J=0.01, gtol=1e-7, m=5,
+                    max_iter=20000, q=Q):
+    """Symmetric plmDCA (Eq. npll_1 + Eq. l2reg) from the origin by the same
+    L-BFGS as the site problems.  Returns ``(h, J, info)`` with J in the
+    per-site layout (both copies of every block) and info = dict(iters,
+    status, f, gnorm, nevals)."""
+    S = _msa(S)
+    B, N = S.shape
+    w = np.ascontiguousarray(w, np.float64)
+    x = np.zeros(sym_nparams(N, q))
+    f = ctypes.c_double()
+    gn = ctypes.c_double()
+    ne = ctypes.c_int()
+    st = ctypes.c_int()
+    it = _load().orc_solve_symmetric(_ptr(S), _ptr(w), float(beff), B, N, q,
+                                     float(lambda_h), float(lambda_J), float(gtol),
+                                     int(m), int(max_iter), _ptr(x), ctypes.byref(f),
+                                     ctypes.byref(gn), ctypes.byref(ne), ctypes.byref(st))
+    h, J = sym_expand(x, N, q)
+    return h, J, dict(iters=it, status=st.value, f=f.value, gnorm=gn.value,
+                      nevals=ne.value, x=x)
+
+
+def plmdca_symmetric(S, x=0.8, lambda_h=0.01, lambda_J=0.01, gtol=1e-7, m=5,
+                     max_iter=20000, L=None, min_sep=5):
+    """Reweighting, the symmetric minimisation and the same scoring (the
+    two estimates of a block coincide, so the average is the block)."""
+    S = _msa(S)
+    B, N = S.shape
+    mcount, w, w32, beff = reweight(S, x)
+    h, J, info = solve_symmetric(S, w, beff, lambda_h, lambda_J, gtol, m, max_iter)
     fn, cfn = scores(J)
     top = topL(cfn, N if L is None else L, min_sep)
     return dict(m=mcount, w=w, w32=w32, beff=beff, h=h, J=J, info=info,

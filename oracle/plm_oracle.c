@@ -224,11 +224,14 @@ typedef struct {
     int B, N, q, r;
     double lambda_h, lambda_Jp;
     int nevals;
+    /* objective and gradient at theta; NULL = the site objective g_r^(reg) */
+    double (*fg)(void *self, const double *theta, double *grad);
 } orc_site_problem;
 
 static double site_fg(orc_site_problem *p, const double *theta, double *grad)
 {
     p->nevals++;
+    if (p->fg) return p->fg(p, theta, grad);
     return orc_site_objgrad(p->S, p->w, p->beff, p->B, p->N, p->q, p->r,
                             theta, theta + p->q, p->lambda_h, p->lambda_Jp,
                             grad, grad + p->q);
@@ -335,14 +338,28 @@ static int wolfe_search(orc_site_problem *p, size_t n, const double *x,
 /* theta: in = start point (the paper starts at the origin), out = minimiser.
  * Returns the number of iterations taken; *status_out is ORC_OK when the
  * gradient norm reached gtol and ORC_ENOTCONV otherwise. */
+static int lbfgs_run(orc_site_problem *pp, size_t n, double gtol, int mem, int max_iter,
+                     double *theta, double *f_out, double *gnorm_out, int *nevals_out,
+                     int *status_out);
+
 int orc_lbfgs_site(const int8_t *S, const double *w, double beff, int B, int N,
                    int q, int r, double lambda_h, double lambda_Jp,
                    double gtol, int mem, int max_iter, double *theta,
                    double *f_out, double *gnorm_out, int *nevals_out,
                    int *status_out)
 {
-    orc_site_problem p = {S, w, beff, B, N, q, r, lambda_h, lambda_Jp, 0};
+    orc_site_problem p = {S, w, beff, B, N, q, r, lambda_h, lambda_Jp, 0, NULL};
     const size_t n = (size_t)q + (size_t)q * N * q;
+    return lbfgs_run(&p, n, gtol, mem, max_iter, theta, f_out, gnorm_out, nevals_out,
+                     status_out);
+}
+
+/* the L-BFGS iteration described above, for any objective (pp->fg) */
+static int lbfgs_run(orc_site_problem *pp, size_t n, double gtol, int mem, int max_iter,
+                     double *theta, double *f_out, double *gnorm_out, int *nevals_out,
+                     int *status_out)
+{
+    orc_site_problem *p = pp;
     double *g = (double *)malloc(sizeof(double) * n);
     double *d = (double *)malloc(sizeof(double) * n);
     double *xn = (double *)malloc(sizeof(double) * n);
@@ -354,7 +371,7 @@ int orc_lbfgs_site(const int8_t *S, const double *w, double beff, int B, int N,
     int hist = 0, head = 0; /* number of stored pairs, next slot */
     int status = ORC_ENOTCONV, it = 0;
 
-    double f = site_fg(&p, theta, g);
+    double f = site_fg(p, theta, g);
     double gnorm = sqrt(dot(g, g, n));
     for (it = 0; it < max_iter; ++it) {
         if (gnorm <= gtol) { status = ORC_OK; break; }
@@ -380,7 +397,7 @@ int orc_lbfgs_site(const int8_t *S, const double *w, double beff, int B, int N,
 
         double alpha1 = (it == 0 && hist == 0) ? 1.0 / gnorm : 1.0;
         double fn, alpha;
-        if (wolfe_search(&p, n, theta, f, g, d, alpha1, xn, &fn, gn, &alpha) != 0) {
+        if (wolfe_search(p, n, theta, f, g, d, alpha1, xn, &fn, gn, &alpha) != 0) {
             status = ORC_ENOTCONV;
             break;
         }
@@ -404,7 +421,7 @@ int orc_lbfgs_site(const int8_t *S, const double *w, double beff, int B, int N,
     if (it >= max_iter && gnorm <= gtol) status = ORC_OK;
     if (f_out) *f_out = f;
     if (gnorm_out) *gnorm_out = gnorm;
-    if (nevals_out) *nevals_out = p.nevals;
+    if (nevals_out) *nevals_out = p->nevals;
     if (status_out) *status_out = status;
     free(g); free(d); free(xn); free(gn); free(sh); free(yh); free(rho); free(alph);
     return it;
@@ -441,6 +458,116 @@ void orc_solve_sites(const int8_t *S, const double *w, double beff, int B,
         if (nevals) nevals[t] = ne;
         free(theta);
     }
+}
+
+/* ------------------------------------------------------------------------
+ * Symmetric pseudolikelihood maximisation (Sec. 3, Eq. npll_1, with the l2
+ * penalty of Eq. l2reg): one minimisation of
+ *     l_pseudo(h, J) + R_l2(h, J),   l_pseudo = sum_r g_r(h_r, J_r),
+ *     R_l2 = lambda_h sum_i ||h_i||^2 + lambda_J sum_{i<j} ||J_ij||^2,
+ * where site r's conditional uses J_ri(s,k) = J_ir(k,s) for i < r, i.e. one
+ * coupling block per pair shared by both sites.
+ * Parameter vector x = [h (N*q) | J_ij for i < j in the order (0,1), (0,2),
+ * ..., (0,N-1), (1,2), ... (q*q each, J_ij[k][l] with k the state of i)].
+ * The objective is evaluated through the per-site g_r written above: with
+ * lambda' = lambda_J / 2 each block's penalty is counted once from each of
+ * its two sites, so sum_r g_r^(reg) = l_pseudo + R_l2 (the remark after
+ * Eq. g_reg), and the gradient of a shared block is the sum of its two
+ * per-site gradients, the second transposed.
+ * ---------------------------------------------------------------------- */
+static size_t pair_index(int i, int j, int N) /* i < j */
+{
+    return (size_t)i * N - (size_t)i * (i + 1) / 2 + (size_t)(j - i - 1);
+}
+
+size_t orc_sym_nparams(int N, int q)
+{
+    return (size_t)N * q + (size_t)N * (N - 1) / 2 * q * q;
+}
+
+/* expand x into the per-site layout h[N][q], J[N][q][N][q] (both copies) */
+void orc_sym_expand(const double *x, int N, int q, double *h, double *J)
+{
+    memcpy(h, x, sizeof(double) * N * q);
+    const double *xJ = x + (size_t)N * q;
+    memset(J, 0, sizeof(double) * (size_t)N * q * N * q);
+    for (int i = 0; i < N; ++i)
+        for (int j = i + 1; j < N; ++j) {
+            const double *blk = xJ + pair_index(i, j, N) * q * q;
+            for (int k = 0; k < q; ++k)
+                for (int l = 0; l < q; ++l) {
+                    J[(((size_t)i * q + k) * N + j) * q + l] = blk[k * q + l]; /* J_ij(k,l) */
+                    J[(((size_t)j * q + l) * N + i) * q + k] = blk[k * q + l]; /* J_ji(l,k) */
+                }
+        }
+}
+
+/* l_pseudo + R_l2 at x; gx (may be NULL) gets its gradient */
+double orc_sym_objgrad(const int8_t *S, const double *w, double beff, int B, int N,
+                       int q, const double *x, double lambda_h, double lambda_J,
+                       double *gx)
+{
+    const size_t Jlen = (size_t)N * q * N * q;
+    double *h = (double *)malloc(sizeof(double) * N * q);
+    double *J = (double *)malloc(sizeof(double) * Jlen);
+    double *f = (double *)malloc(sizeof(double) * N);
+    double *gh = gx ? (double *)malloc(sizeof(double) * N * q) : NULL;
+    double *gJ = gx ? (double *)malloc(sizeof(double) * Jlen) : NULL;
+    orc_sym_expand(x, N, q, h, J);
+    orc_objgrad_all(S, w, beff, B, N, q, h, J, lambda_h, lambda_J, f, gh, gJ);
+    double total = 0.0;
+    for (int r = 0; r < N; ++r) total += f[r];
+    if (gx) {
+        memcpy(gx, gh, sizeof(double) * N * q);
+        double *gxJ = gx + (size_t)N * q;
+        for (int i = 0; i < N; ++i)
+            for (int j = i + 1; j < N; ++j) {
+                double *blk = gxJ + pair_index(i, j, N) * q * q;
+                for (int k = 0; k < q; ++k)
+                    for (int l = 0; l < q; ++l)
+                        blk[k * q + l] = gJ[(((size_t)i * q + k) * N + j) * q + l] +
+                                         gJ[(((size_t)j * q + l) * N + i) * q + k];
+            }
+    }
+    free(h); free(J); free(f); free(gh); free(gJ);
+    return total;
+}
+
+typedef struct {
+    orc_site_problem base; /* first member: the L-BFGS driver passes its address */
+    double lambda_J;
+} orc_sym_problem;
+
+static double sym_fg(void *self, const double *x, double *grad)
+{
+    orc_sym_problem *p = (orc_sym_problem *)self;
+    return orc_sym_objgrad(p->base.S, p->base.w, p->base.beff, p->base.B, p->base.N,
+                           p->base.q, x, p->base.lambda_h, p->lambda_J, grad);
+}
+
+/* minimise l_pseudo + R_l2 from the origin with the same L-BFGS as the site
+ * problems (memory mem, strong Wolfe, stop at ||grad||_2 <= gtol, the
+ * gradient in the parameters x); x gets the minimiser */
+int orc_solve_symmetric(const int8_t *S, const double *w, double beff, int B, int N, int q,
+                        double lambda_h, double lambda_J, double gtol, int mem, int max_iter,
+                        double *x, double *f_out, double *gnorm_out, int *nevals_out,
+                        int *status_out)
+{
+    orc_sym_problem p;
+    memset(&p, 0, sizeof p);
+    p.base.S = S;
+    p.base.w = w;
+    p.base.beff = beff;
+    p.base.B = B;
+    p.base.N = N;
+    p.base.q = q;
+    p.base.lambda_h = lambda_h;
+    p.base.fg = sym_fg;
+    p.lambda_J = lambda_J;
+    const size_t n = orc_sym_nparams(N, q);
+    memset(x, 0, sizeof(double) * n); /* origin */
+    return lbfgs_run(&p.base, n, gtol, mem, max_iter, x, f_out, gnorm_out, nevals_out,
+                     status_out);
 }
 
 /* ------------------------------------------------------------------------

@@ -35,12 +35,25 @@ MUTANTS = {
         ("if (i == r) continue;\n                        gJ_r[((size_t)s * N + i) * q + seq[i]] += d;",
          "gJ_r[((size_t)s * N + i) * q + seq[i]] += d;"),
     "weights not normalised by B_eff": ("return -loglik / beff + lambda_h", "return -loglik / B + lambda_h"),
+    # symmetric plmDCA (caught by the symmetric pins)
+    "symmetric mirror copy not transposed":
+        ("J[(((size_t)j * q + l) * N + i) * q + k] = blk[k * q + l]; /* J_ji(l,k) */",
+         "J[(((size_t)j * q + k) * N + i) * q + l] = blk[k * q + l];", "sym"),
+    "symmetric block gradient of the second site not transposed":
+        ("gJ[(((size_t)j * q + l) * N + i) * q + k];",
+         "gJ[(((size_t)j * q + k) * N + i) * q + l];", "sym"),
+    "symmetric block gradient from one site only":
+        ("blk[k * q + l] = gJ[(((size_t)i * q + k) * N + j) * q + l] +",
+         "blk[k * q + l] = gJ[(((size_t)i * q + k) * N + j) * q + l] + 0.0 *", "sym"),
 }
+
+PIN_FILES = {"pins": "test_oracle_pins.py", "sym": "test_oracle_symmetric.py"}
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
 def test_pins_catch_mutant(name, tmp_path):
-    old, new = MUTANTS[name]
+    old, new = MUTANTS[name][:2]
+    pins = PIN_FILES[MUTANTS[name][2] if len(MUTANTS[name]) > 2 else "pins"]
     src = open(SRC).read()
     assert src.count(old) >= 1, f"mutation anchor not found: {name}"
     mutated = src.replace(old, new, 1)
@@ -51,6 +64,6 @@ def test_pins_catch_mutant(name, tmp_path):
                     "-o", str(lib), str(cfile), "-lm"], check=True)
     env = dict(os.environ, ORACLE_LIB=str(lib), OMP_NUM_THREADS="2")
     res = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q",
-                          os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                          os.path.join(ROOT, "tests", pins)],
                          cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert res.returncode != 0, f"pins did not catch: {name}\n{res.stdout[-2000:]}"
