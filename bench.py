@@ -42,10 +42,12 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32-cmp", action="store_true",
                     help="skip timing the plain FP32 path beside the split-bf16 one")
-    ap.add_argument("--workload", default="family", choices=["family", "batch", "scale", "eval"],
+    ap.add_argument("--workload", default="family",
+                    choices=["family", "batch", "scale", "eval", "symmetric"],
                     help="family: the benchmark line; batch (64 families), scale "
-                         "(N=500, B=50000) and eval (full objective+gradient evaluations "
-                         "of the family at a random point): separate measurements")
+                         "(N=500, B=50000), eval (full objective+gradient evaluations "
+                         "of the family at a random point) and symmetric (symmetric "
+                         "plmDCA on the family): separate measurements")
     ap.add_argument("--cpu-sites", type=int, default=0,
                     help="sites per CPU-oracle sample (0 = one per host core, at most 16)")
     return ap.parse_args()
@@ -268,8 +270,49 @@ def run_eval(args):
     ctx.close()
 
 
+def run_symmetric(args):
+    """Symmetric plmDCA (one minimisation, tied blocks) on the family
+    workload beside the asymmetric solve: seconds, descent steps and the
+    overlap of the two contact lists (the paper compares the two, Sec. 6)."""
+    import torch
+    from paper_1401_4832_gb300 import api, synth
+    fam = synth.protein_family()
+    S = torch.from_numpy(fam.msa).cuda()
+    stream = torch.cuda.Stream()
+    ctx = api.Context(0, stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    prec = "split_bf16" if args.prec == "auto" else args.prec
+    out = {}
+    tops = {}
+    with torch.cuda.stream(stream):
+        for name, fn in (("asymmetric", api.plm_solve), ("symmetric", api.plm_solve_symmetric)):
+            times = []
+            for k in range(args.warmup + args.steps):
+                flush.zero_()
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                h, J, rep = fn(ctx, S, gtol=args.gtol, prec=prec)
+                fnm, cfn, top = api.fn_apc_scores(ctx, J)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if k >= args.warmup:
+                    times.append(e0.elapsed_time(e1) / 1000.0)
+            tops[name] = set(map(tuple, top.cpu().numpy().tolist()))
+            out[name] = {"s": statistics.mean(times), "iters": rep["iters"],
+                         "evals": rep["evals"], "gnorm_max": rep["gnorm_max"],
+                         "converged": rep["n_converged"] == fam.N}
+    out["top_N_overlap"] = len(tops["asymmetric"] & tops["symmetric"]) / max(1, len(tops["symmetric"]))
+    print(json.dumps({"workload": "symmetric vs asymmetric: " + WORKLOAD, "precision": prec,
+                      "gtol": args.gtol, "results": out}), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse_args()
+    if args.workload == "symmetric":
+        return run_symmetric(args)
     if args.workload == "eval":
         return run_eval(args)
     if args.workload == "batch":

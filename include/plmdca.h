@@ -173,6 +173,24 @@ typedef struct {
 plm_status plm_solve_batch(plm_ctx *ctx, const plm_family *fams, int nfam,
                            int q, const plm_opts *opts, plm_report *reports);
 
+/* Symmetric pseudolikelihood maximisation (Sec. 3, Eq. npll_1, with the l2
+ * penalty of Eq. l2reg: lambda_h sum ||h_i||^2 + lambda_J sum_{i<j}
+ * ||J_ij||^2, lambda_J used as given): one minimisation of l_pseudo + R_l2
+ * over the fields and one coupling block per pair, shared by both sites
+ * (J_ri = J_ir^T), instead of the N separate problems of plm_solve.
+ * Reweighting as in plm_solve; one L-BFGS problem from the origin (memory,
+ * line search, max_iter from opts) over the site-contiguous layout
+ * restricted to J_ri = J_ir^T, with the gradient projected onto that
+ * subspace; stops when the norm of that projected gradient is <= gtol.
+ * Same arguments and output layouts as plm_solve; J_out holds both copies
+ * of every block (J[j][l][i][k] = J[i][k][j][l]).  The report's site
+ * counts all take the one problem's outcome (n_converged = N when it
+ * converged).  Returns PLM_ENOTCONV (outputs valid) when it stopped before
+ * gtol, PLM_ETIMEOUT if a device wait ran out. */
+plm_status plm_solve_symmetric(plm_ctx *ctx, const int8_t *msa, int B, int N, int q,
+                               const plm_opts *opts, float *h_out, float *J_out,
+                               plm_report *report);
+
 /* Steps 4-6 of the rundown: Ising gauge of every estimate (Eq.
  * gauge_change2), combination of J^i_ij with J^j_ij = (J^j_ji)^T (Eq.
  * average2; combine = 1 / 2 selects the elementwise min / max alternatives

@@ -100,6 +100,9 @@ def load():
         lib.plm_solve_batch.argtypes = [P, ctypes.POINTER(plm_family), I, I,
                                         ctypes.POINTER(plm_opts), ctypes.POINTER(plm_report)]
         lib.plm_solve_batch.restype = I
+        lib.plm_solve_symmetric.argtypes = [P, P, I, I, I, ctypes.POINTER(plm_opts), P, P,
+                                            ctypes.POINTER(plm_report)]
+        lib.plm_solve_symmetric.restype = I
         lib.fn_apc_scores.argtypes = [P, P, I, I, I, P, P, P, I, I]
         lib.fn_apc_scores.restype = I
         lib.plm_kernel_launches.argtypes = []

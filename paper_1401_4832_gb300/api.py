@@ -162,6 +162,25 @@ def plm_solve(ctx: Context, msa, raise_on_notconv: bool = False, **opts):
     return h, J, d
 
 
+def plm_solve_symmetric(ctx: Context, msa, raise_on_notconv: bool = False, **opts):
+    """Symmetric plmDCA (Eq. npll_1 with the penalty of Eq. l2reg): one
+    minimisation with a single coupling block per pair.  Returns (h[N,q],
+    J[N,q,N,q] with J[j,:,i,:] = J[i,:,j,:]^T, report dict incl. 'status')."""
+    msa = _as_input(msa, np.int8)
+    B, N = msa.shape
+    o = default_opts(**opts)
+    h = _like(msa, (N, Q), np.float32)
+    J = _like(msa, (N, Q, N, Q), np.float32)
+    rep = N_.plm_report()
+    st = ctx.lib.plm_solve_symmetric(ctx.handle, _ptr(msa), B, N, Q, ctypes.byref(o),
+                                     _ptr(h), _ptr(J), ctypes.byref(rep))
+    if st != N_.PLM_OK and (st != N_.PLM_ENOTCONV or raise_on_notconv):
+        ctx.check(st)
+    d = rep.as_dict()
+    d["status"] = N_.STATUS_NAMES.get(st, st)
+    return h, J, d
+
+
 def plm_solve_batch(ctx: Context, msas, raise_on_notconv: bool = False, **opts):
     """plm_solve for many families at once (one batched L-BFGS, one launch
     per evaluation kernel for all families).  Returns a list of

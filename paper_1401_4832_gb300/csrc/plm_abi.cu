@@ -274,6 +274,10 @@ struct Problem {
     TcConfig tc_cfg;
     bool tc_tuned = false;
     bool autotune = true;
+    // symmetric plmDCA (one family): one L-BFGS problem over the whole arena
+    bool symmetric = false;
+    int lb_sites = 0;              // L-BFGS problems: nsites, or 1 when symmetric
+    std::vector<int> lb_len4;      // streamed float4 of each L-BFGS problem
 };
 
 void layout_problem(Problem &P)
@@ -302,7 +306,29 @@ plm_status build_lbfgs_tables(plm_ctx *ctx, Problem &P)
 {
     std::vector<SiteInfo> si;
     std::vector<ChunkInfo> ci;
-    for (size_t f = 0; f < P.fam.size(); ++f) {
+    if (P.symmetric) {
+        // one problem: every row of the family (padding rows stay zero)
+        const Fam &F = P.fam[0];
+        const int len4 = (int)(F.d.theta_elems() / 4);
+        SiteInfo x;
+        x.off4 = (long long)(F.off / 4);
+        x.len4 = len4;
+        x.KP = F.d.KP;
+        x.NQ = F.d.N * Q;
+        x.chunk0 = 0;
+        x.nchunks = (len4 + LB_CHUNK4 - 1) / LB_CHUNK4;
+        x.family = 0;
+        x.r = 0;
+        for (int c = 0; c < x.nchunks; ++c) {
+            ChunkInfo y;
+            y.site = 0;
+            y.e0 = c * LB_CHUNK4;
+            y.e1 = std::min(len4, (c + 1) * LB_CHUNK4);
+            ci.push_back(y);
+        }
+        si.push_back(x);
+    }
+    for (size_t f = 0; f < P.fam.size() && !P.symmetric; ++f) {
         const Fam &F = P.fam[f];
         // the q state rows of the site; its padding rows (Q..QP-1) stay zero in
         // theta and are never streamed
@@ -330,6 +356,9 @@ plm_status build_lbfgs_tables(plm_ctx *ctx, Problem &P)
     }
     P.site_chunk0.resize(si.size() + 1);
     for (size_t r = 0; r < si.size(); ++r) P.site_chunk0[r] = si[r].chunk0;
+    P.lb_sites = (int)si.size();
+    P.lb_len4.resize(si.size());
+    for (size_t r = 0; r < si.size(); ++r) P.lb_len4[r] = si[r].len4;
     P.site_chunk0[si.size()] = (int)ci.size();
     void *dsi, *dci;
     CK(ws(ctx, "lb_site_info", si.size() * sizeof(SiteInfo), &dsi));
@@ -342,7 +371,7 @@ plm_status build_lbfgs_tables(plm_ctx *ctx, Problem &P)
     P.L.si = (const SiteInfo *)dsi;
     P.L.ci = (const ChunkInfo *)dci;
     P.L.s0 = 0;
-    P.L.nsites = P.nsites;
+    P.L.nsites = P.lb_sites;
     P.L.c0 = 0;
     P.L.c1 = P.nchunks;
     P.L.vec4 = (long long)(P.total / 4);
@@ -604,8 +633,10 @@ plm_status solve_core(plm_ctx *ctx, Problem &P, const plm_opts &o, std::vector<S
     CK(ws(ctx, "dir", tb, &dir));
     CK(ws(ctx, "S_hist", tb * o.lbfgs_m, &Sh));
     CK(ws(ctx, "Y_hist", tb * o.lbfgs_m, &Yh));
-    CK(ws(ctx, "site_state", (size_t)P.nsites * sizeof(SiteState), &sst));
-    CK(ws(ctx, "fdata", (size_t)P.nsites * sizeof(double), &fdat));
+    CK(ws(ctx, "site_state", (size_t)P.lb_sites * sizeof(SiteState), &sst));
+    // per-site data terms, and (symmetric) their sum in the last slot
+    CK(ws(ctx, "fdata", (size_t)(P.nsites + 1) * sizeof(double), &fdat));
+    double *f_lb = (double *)fdat + (P.symmetric ? P.nsites : 0);  // what the line search reads
     CK(ws(ctx, "counters", 32 * sizeof(int), &cnt));  // 16 per lane (see below)
     CK(ws(ctx, "lb_part", (size_t)P.nchunks * LB_PART * sizeof(double), &part));
     void *active;
@@ -641,9 +672,13 @@ plm_status solve_core(plm_ctx *ctx, Problem &P, const plm_opts &o, std::vector<S
                  (const __nv_bfloat16 *)hi, (const __nv_bfloat16 *)lo, p.lambda_h, p.lambda_Jp,
                  (double *)fdat, (float *)g, tc_err);
     if (s) return s;
+    if (P.symmetric) {
+        // the symmetric problem's gradient and objective (data part)
+        CK(launch_sym_project((float *)g, P.fam[0].d, st));
+        CK(launch_sum_sites((const double *)fdat, P.nsites, f_lb, st));
+    }
     evals++;
-    CK(launch_lbfgs_init((SiteState *)sst, (const double *)fdat, (const float *)g, P.L, p,
-                         (double *)part, st));
+    CK(launch_lbfgs_init((SiteState *)sst, f_lb, (const float *)g, P.L, p, (double *)part, st));
 
     // ---- the rounds.  One round advances every live site of a lane by one
     // evaluation: sites whose last trial was accepted (READY) first form
@@ -673,7 +708,7 @@ plm_status solve_core(plm_ctx *ctx, Problem &P, const plm_opts &o, std::vector<S
     };
     const bool use_graph = o.use_graph && st != nullptr && !ctx->prof;
     int split = 0;  // first site of lane 1 (0: one lane)
-    if (use_graph && o.prec == PLM_SPLIT_BF16 && P.tc_tuned) {
+    if (use_graph && o.prec == PLM_SPLIT_BF16 && P.tc_tuned && !P.symmetric) {
         if (nf == 1) {
             int unit = 16;  // 16 sites = 384 rows = three gradient row tiles
             while (unit % P.tc_cfg.lg_sites) unit += 16;
@@ -701,7 +736,7 @@ plm_status solve_core(plm_ctx *ctx, Problem &P, const plm_opts &o, std::vector<S
         Lane &ln = lanes[k];
         ln.L = P.L;
         if (split) {
-            const int s_lo = k == 0 ? 0 : split, s_hi = k == 0 ? split : P.nsites;
+            const int s_lo = k == 0 ? 0 : split, s_hi = k == 0 ? split : P.lb_sites;
             ln.L.s0 = s_lo;
             ln.L.nsites = s_hi - s_lo;
             ln.L.c0 = k == 0 ? 0 : P.site_chunk0[split];
@@ -724,9 +759,8 @@ plm_status solve_core(plm_ctx *ctx, Problem &P, const plm_opts &o, std::vector<S
     std::vector<SiteState> snap;
     std::vector<double> site_bytes;  // 4 x streamed elements of each site
     if (ctx->prof) {
-        snap.resize(P.nsites);
-        for (const auto &F : P.fam)
-            for (int r = 0; r < F.d.N; ++r) site_bytes.push_back(4.0 * Q * F.d.KP);
+        snap.resize(P.lb_sites);
+        for (int r = 0; r < P.lb_sites; ++r) site_bytes.push_back(16.0 * P.lb_len4[r]);
     }
     const double split_b = o.prec == PLM_SPLIT_BF16 ? 1.0 : 0.0;  // hi + lo: 2 + 2 B an element
     auto count_round = [&]() -> plm_status {
@@ -734,7 +768,7 @@ plm_status solve_core(plm_ctx *ctx, Problem &P, const plm_opts &o, std::vector<S
                            cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         rb = RoundBytes{};
-        for (int r = 0; r < P.nsites; ++r) {
+        for (int r = 0; r < P.lb_sites; ++r) {
             const SiteState &x = snap[r];
             const double e = site_bytes[r];
             if (x.status == SITE_READY) {
@@ -773,14 +807,21 @@ plm_status solve_core(plm_ctx *ctx, Problem &P, const plm_opts &o, std::vector<S
         return PLM_OK;
     };
     auto phase_eval = [&](Lane &ln) -> plm_status {
-        return evaluate(ctx, o.prec, P, (const float *)w, (const float *)theta_t,
-                        (const __nv_bfloat16 *)hi, (const __nv_bfloat16 *)lo, p.lambda_h,
-                        p.lambda_Jp, (double *)fdat, (float *)g_t, ln.cnt + 4, ln.active, ln.st);
+        plm_status s2 = evaluate(ctx, o.prec, P, (const float *)w, (const float *)theta_t,
+                                 (const __nv_bfloat16 *)hi, (const __nv_bfloat16 *)lo,
+                                 p.lambda_h, p.lambda_Jp, (double *)fdat, (float *)g_t,
+                                 ln.cnt + 4, P.symmetric ? nullptr : ln.active, ln.st);
+        if (s2) return s2;
+        if (P.symmetric) {
+            CK(launch_sym_project((float *)g_t, P.fam[0].d, ln.st));
+            CK(launch_sum_sites((const double *)fdat, P.nsites, f_lb, ln.st));
+        }
+        return PLM_OK;
     };
     auto phase_post = [&](Lane &ln, bool copy_counts) -> plm_status {
         {
             ProfScope ps(ctx, "lbfgs_linesearch", rb.ls);
-            CK(launch_lbfgs_linesearch((SiteState *)sst, (const double *)fdat, (const float *)g_t,
+            CK(launch_lbfgs_linesearch((SiteState *)sst, f_lb, (const float *)g_t,
                                        (const float *)dir, ln.L, p, (double *)part, ln.cnt + 8,
                                        ln.cnt, ln.st));
         }
@@ -905,7 +946,7 @@ plm_status solve_core(plm_ctx *ctx, Problem &P, const plm_opts &o, std::vector<S
                                    cudaMemcpyDeviceToHost, st));
                 CK(cudaStreamSynchronize(st));
                 double cb = 0.0;
-                for (int r = 0; r < P.nsites; ++r)
+                for (int r = 0; r < P.lb_sites; ++r)
                     if (snap[r].commit_round == rd_now)
                         cb += (8.0 + (snap[r].status == SITE_READY ? 2.0 * (snap[r].hist - 1)
                                                                     : 0.0)) *
@@ -934,8 +975,8 @@ plm_status solve_core(plm_ctx *ctx, Problem &P, const plm_opts &o, std::vector<S
     for (size_t f = 0; f < nf; ++f)
         CK(launch_unpack_theta((const float *)theta + P.fam[f].off, P.fam[f].d, out[f].h,
                                out[f].J, st));
-    std::vector<SiteState> host(P.nsites);
-    CK(cudaMemcpyAsync(host.data(), sst, (size_t)P.nsites * sizeof(SiteState),
+    std::vector<SiteState> host(P.lb_sites);
+    CK(cudaMemcpyAsync(host.data(), sst, (size_t)P.lb_sites * sizeof(SiteState),
                        cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     const double secs =
@@ -947,6 +988,18 @@ plm_status solve_core(plm_ctx *ctx, Problem &P, const plm_opts &o, std::vector<S
         rep.evals = evals;
         rep.beff = P.fam[f].beff;
         rep.seconds = secs;
+        if (P.symmetric) {
+            // one problem: every site shares its outcome
+            const SiteState &x = host[0];
+            rep.iters = x.iters;
+            rep.f_total = x.f;
+            rep.gnorm_max = std::sqrt(x.gnorm2);
+            const int N = P.fam[f].d.N;
+            if (x.status == SITE_CONVERGED) rep.n_converged = N;
+            else if (x.status == SITE_NOISE) rep.n_noise = N;
+            else rep.n_failed = N;
+            continue;
+        }
         for (int r = 0; r < P.fam[f].d.N; ++r) {
             const SiteState &x = host[P.fam[f].site0 + r];
             rep.iters = std::max(rep.iters, x.iters);
@@ -1224,8 +1277,30 @@ plm_status plm_solve(plm_ctx *ctx, const int8_t *msa, int B, int N, int q,
     return plm_solve_batch(ctx, &fam, 1, q, opts, report);
 }
 
+static plm_status solve_families(plm_ctx *ctx, const plm_family *fams, int nfam, int q,
+                                 const plm_opts *opts, plm_report *reports, bool symmetric);
+
 plm_status plm_solve_batch(plm_ctx *ctx, const plm_family *fams, int nfam, int q,
                            const plm_opts *opts, plm_report *reports)
+{
+    return solve_families(ctx, fams, nfam, q, opts, reports, false);
+}
+
+plm_status plm_solve_symmetric(plm_ctx *ctx, const int8_t *msa, int B, int N, int q,
+                               const plm_opts *opts, float *h_out, float *J_out,
+                               plm_report *report)
+{
+    plm_family fam;
+    fam.msa = msa;
+    fam.B = B;
+    fam.N = N;
+    fam.h_out = h_out;
+    fam.J_out = J_out;
+    return solve_families(ctx, &fam, 1, q, opts, report, true);
+}
+
+static plm_status solve_families(plm_ctx *ctx, const plm_family *fams, int nfam, int q,
+                                 const plm_opts *opts, plm_report *reports, bool symmetric)
 {
     if (!ctx) return PLM_EINVAL;
     if (!fams || nfam < 1) return fail(ctx, PLM_EINVAL, "need at least one family");
@@ -1241,6 +1316,7 @@ plm_status plm_solve_batch(plm_ctx *ctx, const plm_family *fams, int nfam, int q
     if (s) return s;
     CK(cudaSetDevice(ctx->device));
     Problem P;
+    P.symmetric = symmetric;
     std::vector<SolveOut> out(nfam);
     std::vector<Staged> hs(nfam), Js(nfam);
     char name[64];

@@ -220,6 +220,13 @@ cudaError_t launch_lbfgs_commit(const SiteState *ss, float *theta, float *g,
 cudaError_t launch_round_cond(cudaGraphConditionalHandle h, int *counters, int max_rounds,
                               cudaStream_t st);
 
+// ---- symmetric plmDCA (k_symmetric.cu) ----
+// G <- its projection on the layouts with J_ri = J_ir^T: both mirror
+// entries replaced by their mean (fields, padding, diagonal untouched)
+cudaError_t launch_sym_project(float *G, const Dims &d, cudaStream_t st);
+// *out = sum_{r < n} f[r], in site order, FP64
+cudaError_t launch_sum_sites(const double *f, int n, double *out, cudaStream_t st);
+
 // ---- scores (k_scores.cu) ----
 cudaError_t launch_fn(const float *J, int N, int combine, double *fn,
                       cudaStream_t st);
