@@ -77,6 +77,12 @@ def _load():
         lib.orc_apc.restype = None
         lib.orc_topL.argtypes = [P, I, I, I, P]
         lib.orc_topL.restype = I
+        lib.orc_site_freqs.argtypes = [P, P, D, I, I, I, P]
+        lib.orc_site_freqs.restype = None
+        lib.orc_score_matrix.argtypes = [P, I, I, I, I, D, I, P, P]
+        lib.orc_score_matrix.restype = None
+        lib.orc_asc.argtypes = [P, I, P]
+        lib.orc_asc.restype = None
         lib.orc_sym_nparams.argtypes = [I, I]
         lib.orc_sym_nparams.restype = ctypes.c_size_t
         lib.orc_sym_expand.argtypes = [P, I, I, P, P]
@@ -237,6 +243,42 @@ def apc(fn):
     cfn = np.zeros((N, N))
     _load().orc_apc(_ptr(fn), N, _ptr(cfn))
     return cfn
+
+
+def site_freqs(S, w, beff, q=Q):
+    """Reweighted single-site frequencies f_i(k), ``[N, q]``."""
+    S = _msa(S)
+    B, N = S.shape
+    w = np.ascontiguousarray(w, np.float64)
+    f = np.zeros((N, q))
+    _load().orc_site_freqs(_ptr(S), _ptr(w), float(beff), B, N, q, _ptr(f))
+    return f
+
+
+SCORE_KINDS = {"fro": 0, "lp": 1, "burkoff": 2}
+
+
+def score_matrix(J, kind="fro", p=2.0, exclude_gap=False, freq=None, combine="mean"):
+    """Sec. 6 score alternatives on the combined Ising-gauged blocks:
+    Frobenius, general l_p norm, Burkoff's D_ij (needs ``freq`` [N, q]);
+    ``exclude_gap`` leaves state 0 out of the norm sums."""
+    J = np.ascontiguousarray(J, np.float64)
+    N, q = J.shape[0], J.shape[1]
+    out = np.zeros((N, N))
+    fr = None if freq is None else np.ascontiguousarray(freq, np.float64)
+    _load().orc_score_matrix(_ptr(J), N, q, COMBINE[combine], SCORE_KINDS[kind], float(p),
+                             int(bool(exclude_gap)), _ptr(fr) if fr is not None else None,
+                             _ptr(out))
+    return out
+
+
+def asc(fn):
+    """Average sum correction (Eq. corr_normsum)."""
+    fn = np.ascontiguousarray(fn, np.float64)
+    N = fn.shape[0]
+    out = np.zeros((N, N))
+    _load().orc_asc(_ptr(fn), N, _ptr(out))
+    return out
 
 
 def topL(score, L, min_sep=5):

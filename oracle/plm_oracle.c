@@ -685,6 +685,115 @@ void orc_scores(const double *J, int N, int q, int combine, double *fn,
     orc_apc(fn, N, cfn);
 }
 
+/* ------------------------------------------------------------------------
+ * The score alternatives of Sec. 6.
+ *
+ * Reweighted single-site frequencies (Sec. 3.1 weights):
+ *     f_i(k) = (1/B_eff) sum_b w_b [S_bi = k]
+ * ---------------------------------------------------------------------- */
+void orc_site_freqs(const int8_t *S, const double *w, double beff, int B, int N, int q,
+                    double *f)
+{
+    memset(f, 0, sizeof(double) * N * q);
+    for (int b = 0; b < B; ++b)
+        for (int i = 0; i < N; ++i) f[(size_t)i * q + S[(size_t)b * N + i]] += w[b];
+    for (int e = 0; e < N * q; ++e) f[e] /= beff;
+}
+
+/* Score of every pair from the combined Ising-gauged block v (the same block
+ * orc_fn takes the Frobenius norm of):
+ *   kind 0  Frobenius norm (Eq. frob_normtrans2)
+ *   kind 1  the general l_p norm (sum_{k,l} |v(k,l)|^p)^(1/p) of Sec. 6 (i)
+ *           (absolute values: the l_p norm of the block's entries)
+ *   kind 2  Burkoff's score (Sec. 6 (ii), Eqs. burkoffscore1-2):
+ *           P(k,l) = f_i(k) f_j(l) e^{v(k,l)} / Z, Z normalising P over k,l,
+ *           D_ij = sum_{k,l} P(k,l) ln(P(k,l) / (f_i(k) f_j(l))),
+ *           terms with P = 0 (a state never seen) taken as 0
+ * exclude_gap (kinds 0, 1): the gap state 0 is left out of the sum
+ * (Sec. 6 (iii)).  score is [N][N], symmetric, zero on the diagonal. */
+void orc_score_matrix(const double *J, int N, int q, int combine, int kind, double p,
+                      int exclude_gap, const double *freq, double *score)
+{
+    const size_t Jr_len = (size_t)q * N * q;
+    memset(score, 0, sizeof(double) * N * N);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int i = 0; i < N; ++i) {
+        double *bi = (double *)malloc(sizeof(double) * q * q);
+        double *bj = (double *)malloc(sizeof(double) * q * q);
+        double *gi = (double *)malloc(sizeof(double) * q * q);
+        double *gj = (double *)malloc(sizeof(double) * q * q);
+        double *v = (double *)malloc(sizeof(double) * q * q);
+        for (int j = i + 1; j < N; ++j) {
+            for (int k = 0; k < q; ++k)
+                for (int l = 0; l < q; ++l) {
+                    bi[k * q + l] = J[(size_t)i * Jr_len + ((size_t)k * N + j) * q + l];
+                    bj[k * q + l] = J[(size_t)j * Jr_len + ((size_t)l * N + i) * q + k];
+                }
+            orc_ising_gauge_block(bi, q, gi);
+            orc_ising_gauge_block(bj, q, gj);
+            for (int e = 0; e < q * q; ++e) {
+                if (combine == 1) v[e] = gi[e] < gj[e] ? gi[e] : gj[e];
+                else if (combine == 2) v[e] = gi[e] > gj[e] ? gi[e] : gj[e];
+                else v[e] = 0.5 * (gi[e] + gj[e]);
+            }
+            double out = 0.0;
+            if (kind == 2) {
+                const double *fi = freq + (size_t)i * q, *fj = freq + (size_t)j * q;
+                double Z = 0.0;
+                for (int k = 0; k < q; ++k)
+                    for (int l = 0; l < q; ++l) Z += fi[k] * fj[l] * exp(v[k * q + l]);
+                for (int k = 0; k < q; ++k)
+                    for (int l = 0; l < q; ++l) {
+                        double P = fi[k] * fj[l] * exp(v[k * q + l]) / Z;
+                        if (P > 0.0) out += P * log(P / (fi[k] * fj[l]));
+                    }
+            } else {
+                double acc = 0.0;
+                for (int k = 0; k < q; ++k)
+                    for (int l = 0; l < q; ++l) {
+                        if (exclude_gap && (k == 0 || l == 0)) continue;
+                        double a = fabs(v[k * q + l]);
+                        acc += kind == 1 ? pow(a, p) : a * a;
+                    }
+                out = kind == 1 ? pow(acc, 1.0 / p) : sqrt(acc);
+            }
+            score[(size_t)i * N + j] = out;
+            score[(size_t)j * N + i] = out;
+        }
+        free(bi); free(bj); free(gi); free(gj); free(v);
+    }
+}
+
+/* Average sum correction (Sec. 6 (iv), Eq. corr_normsum):
+ *   S_ij = FN_ij - FN_:j - FN_i: + FN_::
+ * with the same off-diagonal means as the APC (orc_apc). */
+void orc_asc(const double *fn, int N, double *out)
+{
+    double *row = (double *)malloc(sizeof(double) * N);
+    double *col = (double *)malloc(sizeof(double) * N);
+    double tot = 0.0;
+    for (int i = 0; i < N; ++i) {
+        double s = 0.0;
+        for (int j = 0; j < N; ++j)
+            if (j != i) s += fn[(size_t)i * N + j];
+        row[i] = s / (N - 1);
+        tot += s;
+    }
+    for (int j = 0; j < N; ++j) {
+        double s = 0.0;
+        for (int i = 0; i < N; ++i)
+            if (i != j) s += fn[(size_t)i * N + j];
+        col[j] = s / (N - 1);
+    }
+    tot /= (double)N * (N - 1);
+    for (int i = 0; i < N; ++i)
+        for (int j = 0; j < N; ++j)
+            out[(size_t)i * N + j] =
+                (i == j) ? 0.0 : fn[(size_t)i * N + j] - col[j] - row[i] + tot;
+    free(row);
+    free(col);
+}
+
 /* Top-L contact list: pairs i<j with j - i >= min_sep ranked by score
  * descending, ties broken by (i, j) ascending.  Returns the number written
  * (min(L, #eligible pairs)); ij is [L][2]. */

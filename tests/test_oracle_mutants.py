@@ -45,9 +45,22 @@ MUTANTS = {
     "symmetric block gradient from one site only":
         ("blk[k * q + l] = gJ[(((size_t)i * q + k) * N + j) * q + l] +",
          "blk[k * q + l] = gJ[(((size_t)i * q + k) * N + j) * q + l] + 0.0 *", "sym"),
+    # score alternatives (caught by the score pins)
+    "l_p norm without absolute values":
+        ("double a = fabs(v[k * q + l]);", "double a = v[k * q + l];", "scores"),
+    "gap exclusion on rows only":
+        ("if (exclude_gap && (k == 0 || l == 0)) continue;",
+         "if (exclude_gap && k == 0) continue;", "scores"),
+    "Burkoff log ratio without the column frequency":
+        ("if (P > 0.0) out += P * log(P / (fi[k] * fj[l]));",
+         "if (P > 0.0) out += P * log(P / fi[k]);", "scores"),
+    "average sum correction with the grand mean subtracted":
+        ("fn[(size_t)i * N + j] - col[j] - row[i] + tot;",
+         "fn[(size_t)i * N + j] - col[j] - row[i] - tot;", "scores"),
 }
 
-PIN_FILES = {"pins": "test_oracle_pins.py", "sym": "test_oracle_symmetric.py"}
+PIN_FILES = {"pins": "test_oracle_pins.py", "sym": "test_oracle_symmetric.py",
+             "scores": "test_oracle_scores.py"}
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
