@@ -210,6 +210,51 @@ plm_status fn_apc_scores(plm_ctx *ctx, const float *J, int N, int q,
                          int combine, double *fn_out, double *cfn_out,
                          int32_t *topL_out, int L, int min_sep);
 
+/* The score alternatives of Sec. 6, on the same combined Ising-gauged
+ * blocks as fn_apc_scores:
+ *   norm        PLM_NORM_FROBENIUS (Eq. frob_normtrans2, the default),
+ *               PLM_NORM_LP: the general l_p norm (sum |J(k,l)|^p)^(1/p)
+ *               (Sec. 6 (i); absolute values), exponent p > 0,
+ *               PLM_NORM_BURKOFF: Burkoff's D_ij (Sec. 6 (ii), Eqs.
+ *               burkoffscore1-2) from the site frequencies freq;
+ *   exclude_gap the gap state 0 left out of the norm (Sec. 6 (iii); norms
+ *               only);
+ *   correction  PLM_CORR_APC (Eq. corr_norm2, the default), PLM_CORR_ASC:
+ *               average sum correction S_ij = FN_ij - FN_:j - FN_i: + FN_::
+ *               (Sec. 6 (iv), Eq. corr_normsum), PLM_CORR_NONE;
+ *   combine     as in fn_apc_scores. */
+enum { PLM_NORM_FROBENIUS = 0, PLM_NORM_LP = 1, PLM_NORM_BURKOFF = 2 };
+enum { PLM_CORR_APC = 0, PLM_CORR_ASC = 1, PLM_CORR_NONE = 2 };
+typedef struct {
+    int combine;      /* 0 mean, 1 min, 2 max */
+    int norm;         /* PLM_NORM_* */
+    double p;         /* l_p exponent */
+    int exclude_gap;  /* 0/1 */
+    int correction;   /* PLM_CORR_* */
+    int reserved[4];
+} plm_score_opts;
+
+/* Defaults: mean, Frobenius, p = 2, gap included, APC (= fn_apc_scores). */
+void plm_default_score_opts(plm_score_opts *opts);
+
+/* Scores with the chosen variant.  J, score_out, corr_out, topL_out as in
+ * fn_apc_scores (score_out = the uncorrected pair score, corr_out = the
+ * corrected one the top-L list ranks); freq [N][q] double: the site
+ * frequencies (msa_frequencies), required for PLM_NORM_BURKOFF, else
+ * unused (may be NULL).  opts NULL = defaults.  Errors: PLM_EINVAL for an
+ * unknown norm or correction, p <= 0, Burkoff without freq or with
+ * exclude_gap, and as fn_apc_scores. */
+plm_status plm_scores(plm_ctx *ctx, const float *J, int N, int q, const plm_score_opts *opts,
+                      const double *freq, double *score_out, double *corr_out,
+                      int32_t *topL_out, int L, int min_sep);
+
+/* Reweighted single-site frequencies f_i(k) = (1/B_eff) sum_b w_b [S_bi = k]
+ * (Sec. 3.1 weights; the f_i of Burkoff's score, Eq. burkoffscore2).
+ *   msa [B][N] int8, w [B] float (msa_reweight), beff > 0, f_out [N][q]
+ *   double.  Errors: PLM_EINVAL for shapes, states outside 0..q-1, beff <= 0. */
+plm_status msa_frequencies(plm_ctx *ctx, const int8_t *msa, const float *w, double beff, int B,
+                           int N, int q, double *f_out);
+
 /* msa_reweight_static -- the paper has no counterpart to this call.
  * The same reweighting as msa_reweight (identical m, w and B_eff), for
  * callers that cannot allocate memory when they need it: code running while

@@ -53,6 +53,16 @@ class plm_family(ctypes.Structure):
                 ("h_out", ctypes.c_void_p), ("J_out", ctypes.c_void_p)]
 
 
+class plm_score_opts(ctypes.Structure):
+    _fields_ = [("combine", ctypes.c_int), ("norm", ctypes.c_int), ("p", ctypes.c_double),
+                ("exclude_gap", ctypes.c_int), ("correction", ctypes.c_int),
+                ("reserved", ctypes.c_int * 4)]
+
+
+NORMS = {"fro": 0, "lp": 1, "burkoff": 2}
+CORRECTIONS = {"apc": 0, "asc": 1, "none": 2}
+
+
 class PlmError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -105,6 +115,12 @@ def load():
         lib.plm_solve_symmetric.restype = I
         lib.fn_apc_scores.argtypes = [P, P, I, I, I, P, P, P, I, I]
         lib.fn_apc_scores.restype = I
+        lib.plm_default_score_opts.argtypes = [ctypes.POINTER(plm_score_opts)]
+        lib.plm_default_score_opts.restype = None
+        lib.plm_scores.argtypes = [P, P, I, I, ctypes.POINTER(plm_score_opts), P, P, P, P, I, I]
+        lib.plm_scores.restype = I
+        lib.msa_frequencies.argtypes = [P, P, P, D, I, I, I, P]
+        lib.msa_frequencies.restype = I
         lib.plm_kernel_launches.argtypes = []
         lib.plm_kernel_launches.restype = ctypes.c_longlong
         lib.plm_profile.argtypes = [P, I]

@@ -227,6 +227,46 @@ def fn_apc_scores(ctx: Context, J, combine: str = "mean", L: int | None = None,
     return fn, cfn, top
 
 
+def msa_frequencies(ctx: Context, msa, w, beff: float):
+    """Reweighted single-site frequencies f_i(k), ``[N, q]`` float64."""
+    msa = _as_input(msa, np.int8)
+    B, N = msa.shape
+    w = _as_input(w, np.float32)
+    f = _like(msa, (N, Q), np.float64)
+    ctx.check(ctx.lib.msa_frequencies(ctx.handle, _ptr(msa), _ptr(w), float(beff), B, N, Q,
+                                      _ptr(f)))
+    return f
+
+
+def plm_scores(ctx: Context, J, norm: str = "fro", p: float = 2.0, exclude_gap: bool = False,
+               correction: str = "apc", combine: str = "mean", freq=None,
+               L: int | None = None, min_sep: int = 5):
+    """The Sec. 6 score alternatives: returns (score[N,N], corrected[N,N],
+    top[L,2]).  ``norm`` in fro / lp / burkoff (needs ``freq`` from
+    msa_frequencies), ``correction`` in apc / asc / none."""
+    J = _as_input(J, np.float32)
+    N = J.shape[0]
+    L = N if L is None else L
+    so = N_.plm_score_opts()
+    ctx.lib.plm_default_score_opts(ctypes.byref(so))
+    so.combine = {"mean": 0, "min": 1, "max": 2}[combine]
+    so.norm = N_.NORMS[norm]
+    so.p = float(p)
+    so.exclude_gap = int(bool(exclude_gap))
+    so.correction = N_.CORRECTIONS[correction]
+    if freq is not None:
+        if _is_torch(freq):
+            freq = freq.to(_torch().float64).contiguous()
+        else:
+            freq = np.ascontiguousarray(freq, np.float64)
+    sc = _like(J, (N, N), np.float64)
+    co = _like(J, (N, N), np.float64)
+    top = _like(J, (L, 2), np.int32)
+    ctx.check(ctx.lib.plm_scores(ctx.handle, _ptr(J), N, Q, ctypes.byref(so), _ptr(freq),
+                                 _ptr(sc), _ptr(co), _ptr(top), L, min_sep))
+    return sc, co, top
+
+
 def plmdca(ctx: Context, msa, L: int | None = None, min_sep: int = 5, **opts):
     """The whole rundown (steps 1-6) on the GPU."""
     h, J, rep = plm_solve(ctx, msa, **opts)

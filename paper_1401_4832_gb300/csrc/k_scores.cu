@@ -7,7 +7,11 @@
 // site j's estimate of the same coupling is J^j_ij(k,l) = J^j_ji(l,k) =
 // J[j][l][i][k], i.e. the transpose of site j's stored block.  One warp
 // handles one pair: both blocks are staged in shared memory in FP64, moved
-// to the Ising gauge, combined elementwise and reduced to the norm.
+// to the Ising gauge, combined elementwise and reduced to the pair's score:
+// the Frobenius norm, or one of the Sec. 6 alternatives -- the general l_p
+// norm, Burkoff's D_ij (Eqs. burkoffscore1-2), either norm without the gap
+// state -- and the correction is the APC or the average sum correction
+// (Eq. corr_normsum).
 #include "plm_device.cuh"
 #include "plm_internal.cuh"
 
@@ -18,7 +22,7 @@ namespace {
 constexpr int FN_WARPS = 4;
 
 __global__ void __launch_bounds__(32 * FN_WARPS)
-k_fn(const float *__restrict__ J, int N, int combine, double *__restrict__ fn)
+k_fn(const float *__restrict__ J, int N, int combine, ScoreKind sk, double *__restrict__ fn)
 {
     __shared__ double A[FN_WARPS][Q][Q + 1];
     __shared__ double Bt[FN_WARPS][Q][Q + 1];
@@ -53,21 +57,45 @@ k_fn(const float *__restrict__ J, int N, int combine, double *__restrict__ fn)
         double allA = warp_sum_d(lane < Q ? rowA : 0.0) / Q;
         double allB = warp_sum_d(lane < Q ? rowB : 0.0) / Q;
         __syncwarp();
-        double ss = 0.0;
+        // the combined gauged block, row k = lane, kept in place of A
         if (lane < Q) {
             const int k = lane;
             for (int l = 0; l < Q; ++l) {
                 double a = A[w][k][l] - mA[w][1][l] - mA[w][0][k] + allA;
                 double b = Bt[w][k][l] - mB[w][1][l] - mB[w][0][k] + allB;
-                double v = combine == 1 ? fmin(a, b) : combine == 2 ? fmax(a, b) : 0.5 * (a + b);
-                ss += v * v;
+                Bt[w][k][l] = combine == 1 ? fmin(a, b) : combine == 2 ? fmax(a, b) : 0.5 * (a + b);
             }
         }
-        ss = warp_sum_d(ss);
+        __syncwarp();
+        double out;
+        if (sk.kind == 2) {
+            // Burkoff: P = f_i(k) f_j(l) e^v / Z and ln(P / (f_i f_j)) = v - ln Z
+            const double *fi = sk.freq + (size_t)i * Q, *fj = sk.freq + (size_t)j * Q;
+            double z = 0.0;
+            if (lane < Q)
+                for (int l = 0; l < Q; ++l) z += fi[lane] * fj[l] * exp(Bt[w][lane][l]);
+            const double Z = warp_sum_d(z);
+            const double lz = log(Z);
+            double d = 0.0;
+            if (lane < Q)
+                for (int l = 0; l < Q; ++l) {
+                    const double P = fi[lane] * fj[l] * exp(Bt[w][lane][l]) / Z;
+                    if (P > 0.0) d += P * (Bt[w][lane][l] - lz);
+                }
+            out = warp_sum_d(d);
+        } else {
+            double ss = 0.0;
+            if (lane < Q && !(sk.exclude_gap && lane == 0))
+                for (int l = sk.exclude_gap ? 1 : 0; l < Q; ++l) {
+                    const double a = fabs(Bt[w][lane][l]);
+                    ss += sk.kind == 1 ? pow(a, sk.p) : a * a;
+                }
+            ss = warp_sum_d(ss);
+            out = sk.kind == 1 ? pow(ss, 1.0 / sk.p) : sqrt(ss);
+        }
         if (lane == 0) {
-            double v = sqrt(ss);
-            fn[(size_t)i * N + j] = v;
-            fn[(size_t)j * N + i] = v;
+            fn[(size_t)i * N + j] = out;
+            fn[(size_t)j * N + i] = out;
         }
         __syncwarp();
     }
@@ -94,16 +122,47 @@ __global__ void k_apc_total(double *__restrict__ row, int N)
     row[N] = tot / ((double)N * (N - 1));
 }
 
+// correction 0: APC (Eq. corr_norm2); 1: average sum correction (Eq.
+// corr_normsum); 2: none
 __global__ void k_apc_apply(const double *__restrict__ fn, int N,
                             const double *__restrict__ row,
-                            double *__restrict__ cfn)
+                            double *__restrict__ cfn, int correction)
 {
     size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (size_t)N * N) return;
     int i = (int)(idx / N), j = (int)(idx % N);
     double tot = row[N];
-    // all-zero FN makes the correction 0/0; it is taken as 0
-    cfn[idx] = (i == j) ? 0.0 : fn[idx] - (tot > 0.0 ? row[j] * row[i] / tot : 0.0);
+    double c;
+    if (correction == 1) c = row[j] + row[i] - tot;
+    else if (correction == 2) c = 0.0;
+    else c = tot > 0.0 ? row[j] * row[i] / tot : 0.0;  // all-zero FN: 0/0 taken as 0
+    cfn[idx] = (i == j) ? 0.0 : fn[idx] - c;
+}
+
+// f[i][k] = (1/B_eff) sum_b w_b [S_bi = k]: one block per position, a fixed
+// order of partial sums
+__global__ void k_site_freqs(const int8_t *__restrict__ msa, const float *__restrict__ w, int B,
+                             int N, double inv_beff, double *__restrict__ f)
+{
+    __shared__ double part[128][Q + 1];
+    const int i = blockIdx.x, t = threadIdx.x;
+    double acc[Q];
+#pragma unroll
+    for (int k = 0; k < Q; ++k) acc[k] = 0.0;
+    for (int b = t; b < B; b += 128) {
+        const int s = msa[(size_t)b * N + i];
+        const double wb = w[b];
+#pragma unroll
+        for (int k = 0; k < Q; ++k) acc[k] += (s == k) ? wb : 0.0;
+    }
+#pragma unroll
+    for (int k = 0; k < Q; ++k) part[t][k] = acc[k];
+    __syncthreads();
+    if (t < Q) {
+        double s = 0.0;
+        for (int u = 0; u < 128; ++u) s += part[u][t];
+        f[(size_t)i * Q + t] = s * inv_beff;
+    }
 }
 
 // ---- top-L selection ----------------------------------------------------
@@ -286,22 +345,30 @@ __global__ void k_sel_sort(const SelState *st, Cand *cand, int n2, int L, int N,
 }  // namespace
 
 cudaError_t launch_fn(const float *J, int N, int combine, double *fn,
-                      cudaStream_t st)
+                      cudaStream_t st, ScoreKind sk)
 {
-    k_fn<<<N, 32 * FN_WARPS, 0, st>>>(J, N, combine, fn);
+    k_fn<<<N, 32 * FN_WARPS, 0, st>>>(J, N, combine, sk, fn);
     count_launches(1);
     return cudaGetLastError();
 }
 
 // work: N + 1 doubles
 cudaError_t launch_apc(const double *fn, int N, double *cfn, double *work,
-                       cudaStream_t st)
+                       cudaStream_t st, int correction)
 {
     k_apc_rows<<<(N + 127) / 128, 128, 0, st>>>(fn, N, work);
     k_apc_total<<<1, 32, 0, st>>>(work, N);
     size_t nn = (size_t)N * N;
-    k_apc_apply<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(fn, N, work, cfn);
+    k_apc_apply<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(fn, N, work, cfn, correction);
     count_launches(3);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_site_freqs(const int8_t *msa, const float *w, int B, int N, double beff,
+                              double *f, cudaStream_t st)
+{
+    k_site_freqs<<<N, 128, 0, st>>>(msa, w, B, N, 1.0 / beff, f);
+    count_launches(1);
     return cudaGetLastError();
 }
 

@@ -1363,30 +1363,70 @@ plm_status fn_apc_scores(plm_ctx *ctx, const float *J, int N, int q,
                          int combine, double *fn_out, double *cfn_out,
                          int32_t *topL_out, int L, int min_sep)
 {
+    plm_score_opts so;
+    plm_default_score_opts(&so);
+    so.combine = combine;
+    return plm_scores(ctx, J, N, q, &so, nullptr, fn_out, cfn_out, topL_out, L, min_sep);
+}
+
+void plm_default_score_opts(plm_score_opts *so)
+{
+    if (!so) return;
+    memset(so, 0, sizeof *so);
+    so->combine = 0;
+    so->norm = PLM_NORM_FROBENIUS;
+    so->p = 2.0;
+    so->exclude_gap = 0;
+    so->correction = PLM_CORR_APC;
+}
+
+plm_status plm_scores(plm_ctx *ctx, const float *J, int N, int q, const plm_score_opts *opts,
+                      const double *freq, double *score_out, double *corr_out,
+                      int32_t *topL_out, int L, int min_sep)
+{
     if (!ctx) return PLM_EINVAL;
     if (q != Q) return fail(ctx, PLM_EINVAL, "q must be %d (got %d)", Q, q);
     if (N < 2) return fail(ctx, PLM_EINVAL, "N must be >= 2");
     if (!J) return fail(ctx, PLM_EINVAL, "J is NULL");
     if (L < 0 || min_sep < 1) return fail(ctx, PLM_EINVAL, "need L >= 0 and min_sep >= 1");
     if (L > 8192) return fail(ctx, PLM_EINVAL, "L must be <= 8192 (got %d)", L);
-    if (combine < 0 || combine > 2) return fail(ctx, PLM_EINVAL, "combine must be 0, 1 or 2");
+    plm_score_opts so;
+    if (opts) so = *opts;
+    else plm_default_score_opts(&so);
+    if (so.combine < 0 || so.combine > 2) return fail(ctx, PLM_EINVAL, "combine must be 0, 1 or 2");
+    if (so.norm < PLM_NORM_FROBENIUS || so.norm > PLM_NORM_BURKOFF)
+        return fail(ctx, PLM_EINVAL, "unknown norm %d", so.norm);
+    if (so.norm == PLM_NORM_LP && !(so.p > 0.0 && std::isfinite(so.p)))
+        return fail(ctx, PLM_EINVAL, "the l_p exponent must be > 0");
+    if (so.norm == PLM_NORM_BURKOFF && !freq)
+        return fail(ctx, PLM_EINVAL, "Burkoff's score needs the site frequencies");
+    if (so.norm == PLM_NORM_BURKOFF && so.exclude_gap)
+        return fail(ctx, PLM_EINVAL, "gap exclusion applies to the norms only");
+    if (so.correction < PLM_CORR_APC || so.correction > PLM_CORR_NONE)
+        return fail(ctx, PLM_EINVAL, "unknown correction %d", so.correction);
     CK(cudaSetDevice(ctx->device));
     cudaStream_t st = ctx->stream;
     const size_t NQ = (size_t)N * Q;
-    const void *J_d;
+    const void *J_d, *f_d = nullptr;
     CK(stage_in(ctx, "in_J", J, NQ * NQ * sizeof(float), &J_d));
+    if (so.norm == PLM_NORM_BURKOFF) CK(stage_in(ctx, "in_freq", freq, NQ * sizeof(double), &f_d));
     Staged fn_s, cfn_s, top_s;
-    CK(stage_out(ctx, "out_fn", fn_out, (size_t)N * N * sizeof(double), &fn_s));
-    CK(stage_out(ctx, "out_cfn", cfn_out, (size_t)N * N * sizeof(double), &cfn_s));
+    CK(stage_out(ctx, "out_fn", score_out, (size_t)N * N * sizeof(double), &fn_s));
+    CK(stage_out(ctx, "out_cfn", corr_out, (size_t)N * N * sizeof(double), &cfn_s));
     CK(stage_out(ctx, "out_top", topL_out, (size_t)L * 2 * sizeof(int32_t), &top_s));
     void *fn = fn_s.dev, *cfn = cfn_s.dev, *work;
     if (!fn) CK(ws(ctx, "fn", (size_t)N * N * sizeof(double), &fn));
     if (!cfn) CK(ws(ctx, "cfn", (size_t)N * N * sizeof(double), &cfn));
     CK(ws(ctx, "apc_work", ((size_t)N + 1) * sizeof(double), &work));
+    ScoreKind sk;
+    sk.kind = so.norm;
+    sk.p = so.p;
+    sk.exclude_gap = so.exclude_gap ? 1 : 0;
+    sk.freq = (const double *)f_d;
     {
         ProfScope ps(ctx, "fn_apc_topL");
-        CK(launch_fn((const float *)J_d, N, combine, (double *)fn, st));
-        CK(launch_apc((const double *)fn, N, (double *)cfn, (double *)work, st));
+        CK(launch_fn((const float *)J_d, N, so.combine, (double *)fn, st, sk));
+        CK(launch_apc((const double *)fn, N, (double *)cfn, (double *)work, st, so.correction));
         if (top_s.dev) {
             void *tsc;
             CK(ws(ctx, "topL_scratch", topL_scratch_bytes(L), &tsc));
@@ -1397,6 +1437,29 @@ plm_status fn_apc_scores(plm_ctx *ctx, const float *J, int N, int q,
     CK(copy_back(ctx, cfn_s));
     CK(copy_back(ctx, top_s));
     if (fn_s.host || cfn_s.host || top_s.host) CK(cudaStreamSynchronize(st));
+    return PLM_OK;
+}
+
+plm_status msa_frequencies(plm_ctx *ctx, const int8_t *msa, const float *w, double beff, int B,
+                           int N, int q, double *f_out)
+{
+    if (!ctx) return PLM_EINVAL;
+    plm_status s = check_common(ctx, B, N, q);
+    if (s) return s;
+    if (!msa || !w || !f_out) return fail(ctx, PLM_EINVAL, "msa, w and f_out are required");
+    if (!(beff > 0.0)) return fail(ctx, PLM_EINVAL, "beff must be > 0");
+    CK(cudaSetDevice(ctx->device));
+    const void *msa_d, *w_d;
+    CK(stage_in(ctx, "in_msa", msa, (size_t)B * N, &msa_d));
+    s = check_msa(ctx, (const int8_t *)msa_d, B, N);
+    if (s) return s;
+    CK(stage_in(ctx, "in_w", w, (size_t)B * sizeof(float), &w_d));
+    Staged f_s;
+    CK(stage_out(ctx, "out_freq", f_out, (size_t)N * Q * sizeof(double), &f_s));
+    CK(launch_site_freqs((const int8_t *)msa_d, (const float *)w_d, B, N, beff,
+                         (double *)f_s.dev, ctx->stream));
+    CK(copy_back(ctx, f_s));
+    if (f_s.host) CK(cudaStreamSynchronize(ctx->stream));
     return PLM_OK;
 }
 

@@ -228,10 +228,23 @@ cudaError_t launch_sym_project(float *G, const Dims &d, cudaStream_t st);
 cudaError_t launch_sum_sites(const double *f, int n, double *out, cudaStream_t st);
 
 // ---- scores (k_scores.cu) ----
+// the pair score: kind 0 Frobenius norm, 1 general l_p norm (exponent p),
+// 2 Burkoff's D_ij (freq: [N][Q] site frequencies); exclude_gap leaves
+// state 0 out of the norms
+struct ScoreKind {
+    int kind = 0;
+    double p = 2.0;
+    int exclude_gap = 0;
+    const double *freq = nullptr;
+};
 cudaError_t launch_fn(const float *J, int N, int combine, double *fn,
-                      cudaStream_t st);
+                      cudaStream_t st, ScoreKind sk = ScoreKind());
+// correction 0: APC, 1: average sum correction, 2: none
 cudaError_t launch_apc(const double *fn, int N, double *cfn, double *work,
-                       cudaStream_t st);
+                       cudaStream_t st, int correction = 0);
+// f[i][k] = (1/B_eff) sum_b w_b [S_bi = k]
+cudaError_t launch_site_freqs(const int8_t *msa, const float *w, int B, int N, double beff,
+                              double *f, cudaStream_t st);
 // top-L pairs (j - i >= min_sep) by score descending, ties (i, j) ascending;
 // L <= 8192; rows beyond the number of eligible pairs are -1
 size_t topL_scratch_bytes(int L);

@@ -1,0 +1,87 @@
+"""GPU score alternatives (Sec. 6) and site frequencies against the oracle.
+
+The GPU computes the scores in FP64 from the same float32 couplings the
+oracle reads (cast to double), so they agree to rounding (rtol 1e-9); the
+top-L lists must be identical.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1401_4832_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+Q = 21
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1401_4832_gb300 import api
+    c = api.Context(0)
+    yield c
+    c.close()
+
+
+def _J(N, seed):
+    rng = np.random.default_rng(seed)
+    J = rng.normal(0, 0.2, (N, Q, N, Q)).astype(np.float32)
+    for r in range(N):
+        J[r, :, r, :] = 0
+    return J
+
+
+def test_site_frequencies_match_oracle(ctx):
+    from paper_1401_4832_gb300 import api
+    S = synth.add_clusters(synth.small_random(37, 1003, 6, gap_p=0.2), 0.3, 6, max_redraw=0.1)
+    m, w, w32, beff = oracle.reweight(S, 0.8)
+    f = api.msa_frequencies(ctx, torch.from_numpy(S).cuda(), torch.from_numpy(w32).cuda(), beff)
+    fo = oracle.site_freqs(S, w32.astype(np.float64), beff)
+    assert np.allclose(f.cpu().numpy(), fo, rtol=1e-12, atol=1e-15)
+
+
+VARIANTS = [
+    dict(norm="lp", p=1.0), dict(norm="lp", p=3.0), dict(norm="lp", p=0.5),
+    dict(norm="fro", exclude_gap=True), dict(norm="lp", p=1.0, exclude_gap=True),
+    dict(norm="fro", correction="asc"), dict(norm="fro", correction="none"),
+    dict(norm="lp", p=1.5, combine="min"), dict(norm="fro", combine="max", correction="asc"),
+    dict(norm="burkoff"), dict(norm="burkoff", correction="asc"),
+]
+
+
+@pytest.mark.parametrize("v", VARIANTS, ids=lambda v: "-".join(f"{k}={x}" for k, x in v.items()))
+def test_score_variant_matches_oracle(ctx, v):
+    from paper_1401_4832_gb300 import api
+    N = 29
+    J = _J(N, 3)
+    S = synth.small_random(N, 400, 8, gap_p=0.15)
+    m, w, w32, beff = oracle.reweight(S, 0.8)
+    freq = oracle.site_freqs(S, w, beff)
+    kw = dict(v)
+    kind = {"fro": "fro", "lp": "lp", "burkoff": "burkoff"}[kw.get("norm", "fro")]
+    sc_o = oracle.score_matrix(J.astype(np.float64), kind, kw.get("p", 2.0),
+                               kw.get("exclude_gap", False),
+                               freq if kind == "burkoff" else None, kw.get("combine", "mean"))
+    corr = kw.get("correction", "apc")
+    co_o = oracle.apc(sc_o) if corr == "apc" else oracle.asc(sc_o) if corr == "asc" else sc_o
+    if corr == "none":
+        np.fill_diagonal(co_o, 0.0)
+    sc, co, top = api.plm_scores(ctx, torch.from_numpy(J).cuda(),
+                                 freq=torch.from_numpy(freq).cuda() if kind == "burkoff" else None,
+                                 **kw)
+    assert np.allclose(sc.cpu().numpy(), sc_o, rtol=1e-9, atol=1e-13)
+    assert np.allclose(co.cpu().numpy(), co_o, rtol=1e-9, atol=1e-12)
+    assert np.array_equal(top.cpu().numpy(), oracle.topL(co_o, N))
+
+
+def test_score_variant_errors(ctx):
+    from paper_1401_4832_gb300 import api, _native
+    J = torch.from_numpy(_J(6, 1)).cuda()
+    with pytest.raises(_native.PlmError):
+        api.plm_scores(ctx, J, norm="burkoff")  # no frequencies
+    with pytest.raises(_native.PlmError):
+        api.plm_scores(ctx, J, norm="lp", p=0.0)
+    f = torch.full((6, Q), 1.0 / Q, dtype=torch.float64, device="cuda")
+    with pytest.raises(_native.PlmError):
+        api.plm_scores(ctx, J, norm="burkoff", freq=f, exclude_gap=True)
