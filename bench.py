@@ -43,7 +43,7 @@ def parse_args():
     ap.add_argument("--no-fp32-cmp", action="store_true",
                     help="skip timing the plain FP32 path beside the split-bf16 one")
     ap.add_argument("--workload", default="family",
-                    choices=["family", "batch", "scale", "eval", "symmetric"],
+                    choices=["family", "batch", "scale", "eval", "symmetric", "scores"],
                     help="family: the benchmark line; batch (64 families), scale "
                          "(N=500, B=50000), eval (full objective+gradient evaluations "
                          "of the family at a random point) and symmetric (symmetric "
@@ -309,8 +309,47 @@ def run_symmetric(args):
     ctx.close()
 
 
+def run_scores(args):
+    """Every score variant of Sec. 6 on the family's solved couplings: device
+    time per call (gauge + combination + score + correction + top-N)."""
+    import torch
+    from paper_1401_4832_gb300 import api, synth
+    fam = synth.protein_family()
+    S = torch.from_numpy(fam.msa).cuda()
+    stream = torch.cuda.Stream()
+    ctx = api.Context(0, stream)
+    out = {}
+    with torch.cuda.stream(stream):
+        h, J, rep = api.plm_solve(ctx, S, gtol=args.gtol)
+        m, w, beff = api.msa_reweight(ctx, S)
+        freq = api.msa_frequencies(ctx, S, w, beff)
+        ref = set(map(tuple, api.fn_apc_scores(ctx, J)[2].cpu().numpy().tolist()))
+        variants = {"fro+apc": {}, "lp1+apc": dict(norm="lp", p=1.0),
+                    "fro_nogap+apc": dict(exclude_gap=True), "fro+asc": dict(correction="asc"),
+                    "burkoff+apc": dict(norm="burkoff", freq=freq),
+                    "min+fro+apc": dict(combine="min")}
+        for name, kw in variants.items():
+            for _ in range(args.warmup):
+                api.plm_scores(ctx, J, **kw)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                sc, co, top = api.plm_scores(ctx, J, **kw)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            got = set(map(tuple, top.cpu().numpy().tolist()))
+            out[name] = {"ms_per_call": e0.elapsed_time(e1) / args.steps,
+                         "top_N_overlap_with_fro_apc": len(got & ref) / max(1, len(ref))}
+    print(json.dumps({"workload": "scores: " + WORKLOAD, "results": out}), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse_args()
+    if args.workload == "scores":
+        return run_scores(args)
     if args.workload == "symmetric":
         return run_symmetric(args)
     if args.workload == "eval":

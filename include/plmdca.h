@@ -248,6 +248,24 @@ plm_status plm_scores(plm_ctx *ctx, const float *J, int N, int q, const plm_scor
                       const double *freq, double *score_out, double *corr_out,
                       int32_t *topL_out, int L, int min_sep);
 
+/* An aligned protein family as the int8 MSA of the other calls (host code;
+ * no counterpart in the paper's equations: Sec. 4 describes the PFAM
+ * alignments it uses).  Insert states (lower-case letters, '.') are
+ * removed, as the paper does before DCA; match states map to 0 = gap ('-')
+ * and 1..20 = A C D E F G H I K L M N P Q R S T V W Y; O, U, B, Z, X read
+ * as the gap.
+ *   text, len  the file contents (host)
+ *   format     0 auto (Stockholm if the text starts with its header),
+ *              1 aligned FASTA / A2M, 2 Stockholm
+ *   msa_out    [B][N] int8 (host), or NULL to get B and N only
+ *   capacity   bytes available at msa_out
+ *   B_out, N_out  out: sequences and match columns
+ * ctx may be NULL.  Errors: PLM_EINVAL for an unknown format, characters
+ * outside the alphabet, sequences with different numbers of match
+ * columns, no sequences, or capacity < B N. */
+plm_status msa_parse(plm_ctx *ctx, const char *text, size_t len, int format, int8_t *msa_out,
+                     long long capacity, int *B_out, int *N_out);
+
 /* Reweighted single-site frequencies f_i(k) = (1/B_eff) sum_b w_b [S_bi = k]
  * (Sec. 3.1 weights; the f_i of Burkoff's score, Eq. burkoffscore2).
  *   msa [B][N] int8, w [B] float (msa_reweight), beff > 0, f_out [N][q]

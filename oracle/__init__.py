@@ -370,3 +370,55 @@ def plmdca_symmetric(S, x=0.8, lambda_h=0.01, lambda_J=0.01, gtol=1e-7, m=5,
     top = topL(cfn, N if L is None else L, min_sep)
     return dict(m=mcount, w=w, w32=w32, beff=beff, h=h, J=J, info=info,
                 fn=fn, cfn=cfn, top=top)
+
+
+# ---------------------------------------------------------------- MSA text
+ALPHABET = "ACDEFGHIKLMNPQRSTVWY"  # states 1..20; 0 is the gap
+
+
+def _state(c):
+    # Sec. 4: PFAM marks insert states with lower-case letters and '.',
+    # removed before DCA; '-' is a deletion (the gap state).  Reading of the
+    # appendix table: O, U and the ambiguity codes B, Z, X become the gap.
+    if c == "-" or c in "OUBZX":
+        return 0
+    if c == "." or c.islower():
+        return None
+    if c in ALPHABET:
+        return 1 + ALPHABET.index(c)
+    raise ValueError(f"unexpected character {c!r}")
+
+
+def parse_msa(text, fmt="auto"):
+    """Aligned FASTA/A2M or Stockholm text -> int8 MSA [B, N] (plain Python)."""
+    lines = text.splitlines()
+    if fmt == "auto":
+        first = next((ln for ln in lines if ln.strip()), "")
+        fmt = "stockholm" if first.startswith("# STOCKHOLM") else "fasta"
+    seqs = []
+    if fmt == "fasta":
+        for ln in lines:
+            if ln.startswith(">"):
+                seqs.append([])
+            elif ln.strip():
+                if not seqs:
+                    raise ValueError("sequence data before the first header")
+                seqs[-1].extend(ch for ch in ln if not ch.isspace())
+    else:
+        order, rows = [], {}
+        for ln in lines:
+            t = ln.strip()
+            if not t or t.startswith("#"):
+                continue
+            if t.startswith("//"):
+                break
+            name, _, rest = t.partition(" ")
+            if name not in rows:
+                rows[name] = []
+                order.append(name)
+            rows[name].extend(ch for ch in rest if not ch.isspace())
+        seqs = [rows[n] for n in order]
+    out = [[st for st in (_state(c) for c in s) if st is not None] for s in seqs]
+    if not out or any(len(r) != len(out[0]) for r in out) or not out[0]:
+        raise ValueError("sequences differ in match columns, or none")
+    return np.array(out, dtype=np.int8)

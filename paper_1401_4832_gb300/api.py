@@ -227,6 +227,37 @@ def fn_apc_scores(ctx: Context, J, combine: str = "mean", L: int | None = None,
     return fn, cfn, top
 
 
+FORMATS = {"auto": 0, "fasta": 1, "a2m": 1, "stockholm": 2}
+
+
+def msa_parse(text, fmt: str = "auto", ctx: Context | None = None) -> np.ndarray:
+    """An aligned family (FASTA/A2M or Stockholm text, str or bytes) as the
+    int8 MSA ``[B, N]``: insert states removed, 0 = gap, 1..20 = ACDEFGHIKLMNPQRSTVWY
+    (host code; no GPU needed)."""
+    lib = N_.load()
+    data = text.encode() if isinstance(text, str) else bytes(text)
+    B = ctypes.c_int()
+    N = ctypes.c_int()
+    h = ctx.handle if ctx is not None else None
+    st = lib.msa_parse(h, data, len(data), FORMATS[fmt], None, 0, ctypes.byref(B), ctypes.byref(N))
+    if st != N_.PLM_OK:
+        if ctx is not None:
+            ctx.check(st)
+        raise N_.PlmError(st, "msa_parse failed")
+    out = np.empty((B.value, N.value), np.int8)
+    st = lib.msa_parse(h, data, len(data), FORMATS[fmt], out.ctypes.data_as(ctypes.c_void_p),
+                       out.size, ctypes.byref(B), ctypes.byref(N))
+    if st != N_.PLM_OK:
+        raise N_.PlmError(st, "msa_parse failed")
+    return out
+
+
+def read_msa(path: str, fmt: str = "auto") -> np.ndarray:
+    """msa_parse of a file."""
+    with open(path, "rb") as fh:
+        return msa_parse(fh.read(), fmt)
+
+
 def msa_frequencies(ctx: Context, msa, w, beff: float):
     """Reweighted single-site frequencies f_i(k), ``[N, q]`` float64."""
     msa = _as_input(msa, np.int8)

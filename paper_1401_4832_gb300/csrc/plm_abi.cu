@@ -44,6 +44,10 @@ struct plm_ctx {
 };
 
 namespace plm {
+void set_error(plm_ctx *c, const char *msg)
+{
+    if (c) c->err = msg;
+}
 static std::atomic<long long> g_launches{0};
 void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 }  // namespace plm
