@@ -43,7 +43,8 @@ def parse_args():
     ap.add_argument("--no-fp32-cmp", action="store_true",
                     help="skip timing the plain FP32 path beside the split-bf16 one")
     ap.add_argument("--workload", default="family",
-                    choices=["family", "batch", "scale", "eval", "symmetric", "scores"],
+                    choices=["family", "batch", "scale", "eval", "symmetric", "scores",
+                             "frontend"],
                     help="family: the benchmark line; batch (64 families), scale "
                          "(N=500, B=50000), eval (full objective+gradient evaluations "
                          "of the family at a random point) and symmetric (symmetric "
@@ -346,8 +347,36 @@ def run_scores(args):
     ctx.close()
 
 
+def run_frontend(args):
+    """The MSA front end on the family written as A2M text with insert
+    states (host code): parse throughput, and the parsed MSA equal to the
+    family's."""
+    import numpy as np
+    from paper_1401_4832_gb300 import api, synth
+    fam = synth.protein_family()
+    rng = np.random.default_rng(0)
+    inv = "-ACDEFGHIKLMNPQRSTVWY"
+    lines = []
+    for b, row in enumerate(fam.msa):
+        s = "".join(inv[x] + ("a" if rng.random() < 0.05 else "") for x in row)
+        lines.append(f">seq{b}")
+        lines.extend(s[k:k + 60] for k in range(0, len(s), 60))
+    text = ("\n".join(lines) + "\n").encode()
+    for _ in range(args.warmup):
+        api.msa_parse(text)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        S = api.msa_parse(text)
+    dt = (time.perf_counter() - t0) / args.steps
+    print(json.dumps({"workload": "frontend: A2M text of " + WORKLOAD, "bytes": len(text),
+                      "s_per_parse": dt, "MB_per_s": len(text) / dt / 1e6,
+                      "equal_to_family": bool(np.array_equal(S, fam.msa))}), flush=True)
+
+
 def main():
     args = parse_args()
+    if args.workload == "frontend":
+        return run_frontend(args)
     if args.workload == "scores":
         return run_scores(args)
     if args.workload == "symmetric":
