@@ -28,10 +28,14 @@ k_fn(const float *__restrict__ J, int N, int combine, ScoreKind sk, double *__re
     __shared__ double Bt[FN_WARPS][Q][Q + 1];
     __shared__ double mA[FN_WARPS][2][Q], mB[FN_WARPS][2][Q];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int i = blockIdx.x;
+    // block (x, y): row i = y, pairs (i, j) for j = x FN_WARPS + w; every
+    // pair has its own warp
+    const int i = blockIdx.y;
     const size_t NQ = (size_t)N * Q;
-    if (lane == 0 && w == 0) fn[(size_t)i * N + i] = 0.0;
-    for (int j = i + 1 + w; j < N; j += FN_WARPS) {
+    if (lane == 0 && w == 0 && blockIdx.x == 0) fn[(size_t)i * N + i] = 0.0;
+    {
+        const int j = blockIdx.x * FN_WARPS + w;
+        if (j <= i || j >= N) return;
         if (lane < Q) {
             const float *ra = J + ((size_t)i * Q + lane) * NQ + (size_t)j * Q;  // J[i][lane][j][.]
             const float *rb = J + ((size_t)j * Q + lane) * NQ + (size_t)i * Q;  // J[j][lane][i][.]
@@ -347,7 +351,7 @@ __global__ void k_sel_sort(const SelState *st, Cand *cand, int n2, int L, int N,
 cudaError_t launch_fn(const float *J, int N, int combine, double *fn,
                       cudaStream_t st, ScoreKind sk)
 {
-    k_fn<<<N, 32 * FN_WARPS, 0, st>>>(J, N, combine, sk, fn);
+    k_fn<<<dim3((N + FN_WARPS - 1) / FN_WARPS, N), 32 * FN_WARPS, 0, st>>>(J, N, combine, sk, fn);
     count_launches(1);
     return cudaGetLastError();
 }

@@ -190,7 +190,7 @@ def test_solve_tiny_fp32_matches_oracle(ctx):
 # ---------------------------------------------------------------------------
 # scores
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("N", [2, 6, 37, 130])
+@pytest.mark.parametrize("N", [2, 6, 37, 128, 130])  # 128: the most pairs sorted whole; 130: radix select
 @pytest.mark.parametrize("combine", ["mean", "min", "max"])
 def test_scores_match_oracle(ctx, N, combine):
     rng = np.random.default_rng(N)
