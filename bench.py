@@ -492,18 +492,25 @@ def main():
                     "evals_per_solve": rep32["evals"], "gnorm_max": rep32["gnorm_max"],
                     "top_L_identical_to_split_bf16": same}
 
-    # end to end through the C ABI with host buffers (pinned MSA in, J/h/scores out)
+    # end to end through the public API with host buffers: the whole rundown
+    # (api.plmdca -> plmdca_run) from a pinned host MSA into pinned host
+    # outputs (h, J, FN, CFN, top-N); the copies happen inside the call
     msa_host = torch.from_numpy(fam.msa).pin_memory()
-    msa_np = msa_host.numpy()
+    pin = dict(h=torch.empty((N, 21), dtype=torch.float32).pin_memory(),
+               J=torch.empty((N, 21, N, 21), dtype=torch.float32).pin_memory(),
+               fn=torch.empty((N, N), dtype=torch.float64).pin_memory(),
+               cfn=torch.empty((N, N), dtype=torch.float64).pin_memory(),
+               top=torch.empty((N, 2), dtype=torch.int32).pin_memory())
     e2e_times = []
-    for _ in range(max(1, args.steps)):
-        torch.cuda.synchronize(device)
-        t0 = time.perf_counter()
-        h_h, J_h, _ = api.plm_solve(ctx, msa_np, **opts)
-        fn_h, cfn_h, top_h = api.fn_apc_scores(ctx, J_h)
-        e2e_times.append(time.perf_counter() - t0)
-    h2d = B * N + N * 21 * N * 21 * 4  # msa in; J back in for the scoring call
-    d2h = (N * 21 + (N * 21) ** 2) * 4 + 2 * N * N * 8 + N * 2 * 4
+    with torch.cuda.stream(stream):
+        for _ in range(max(1, args.steps)):
+            torch.cuda.synchronize(device)
+            t0 = time.perf_counter()
+            res = api.plmdca(ctx, msa_host, out=pin, **opts)
+            e2e_times.append(time.perf_counter() - t0)
+    e2e_top_same = bool(torch.equal(res["top"], top.cpu()))
+    h2d = B * N  # the MSA
+    d2h = sum(v.numel() * v.element_size() for v in pin.values())  # h, J, FN, CFN, top-N
 
     # per-kernel device times of one profiled solve (events on the library stream)
     import ctypes
@@ -555,7 +562,9 @@ def main():
             "sites_failed": reps[-1]["n_failed"], "gnorm_max": reps[-1]["gnorm_max"],
             "clocks": clocks,
             "e2e": {"value": statistics.mean(e2e_times), "unit": "s",
-                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "call": "api.plmdca (plmdca_run), pinned host buffers",
+                    "top_N_equal_to_device_run": e2e_top_same},
             "gpu_launches": launches,
             "roofline": roof,
             "kernels_profiled_ms": {k: v[1] for k, v in kern.items()},

@@ -248,6 +248,16 @@ plm_status plm_scores(plm_ctx *ctx, const float *J, int N, int q, const plm_scor
                       const double *freq, double *score_out, double *corr_out,
                       int32_t *topL_out, int L, int min_sep);
 
+/* The whole rundown (steps 1-6) in one call: plm_solve, then fn_apc_scores
+ * on the estimates while they are still on the device (one upload of the
+ * MSA and one download of each result when the buffers are on the host).
+ * Arguments as plm_solve and fn_apc_scores (L top pairs, min_sep; any
+ * output may be NULL except that the estimates are always computed).
+ * Returns PLM_ENOTCONV (outputs valid) as plm_solve does. */
+plm_status plmdca_run(plm_ctx *ctx, const int8_t *msa, int B, int N, int q,
+                      const plm_opts *opts, int L, int min_sep, float *h_out, float *J_out,
+                      double *fn_out, double *cfn_out, int32_t *topL_out, plm_report *report);
+
 /* An aligned protein family as the int8 MSA of the other calls (host code;
  * no counterpart in the paper's equations: Sec. 4 describes the PFAM
  * alignments it uses).  Insert states (lower-case letters, '.') are

@@ -119,6 +119,9 @@ def load():
         lib.plm_default_score_opts.restype = None
         lib.plm_scores.argtypes = [P, P, I, I, ctypes.POINTER(plm_score_opts), P, P, P, P, I, I]
         lib.plm_scores.restype = I
+        lib.plmdca_run.argtypes = [P, P, I, I, I, ctypes.POINTER(plm_opts), I, I, P, P, P, P, P,
+                                   ctypes.POINTER(plm_report)]
+        lib.plmdca_run.restype = I
         lib.msa_parse.argtypes = [P, ctypes.c_char_p, ctypes.c_size_t, I, P, ctypes.c_longlong,
                                   ctypes.POINTER(I), ctypes.POINTER(I)]
         lib.msa_parse.restype = I

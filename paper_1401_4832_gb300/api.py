@@ -298,8 +298,27 @@ def plm_scores(ctx: Context, J, norm: str = "fro", p: float = 2.0, exclude_gap: 
     return sc, co, top
 
 
-def plmdca(ctx: Context, msa, L: int | None = None, min_sep: int = 5, **opts):
-    """The whole rundown (steps 1-6) on the GPU."""
-    h, J, rep = plm_solve(ctx, msa, **opts)
-    fn, cfn, top = fn_apc_scores(ctx, J, L=L, min_sep=min_sep)
-    return dict(h=h, J=J, report=rep, fn=fn, cfn=cfn, top=top)
+def plmdca(ctx: Context, msa, L: int | None = None, min_sep: int = 5, out=None,
+           raise_on_notconv: bool = False, **opts):
+    """The whole rundown (steps 1-6) on the GPU in one library call
+    (``plmdca_run``): the estimates stay on the device between the solve and
+    the scores.  Outputs are allocated beside ``msa`` (CUDA tensors, or host
+    arrays), or written into ``out`` (a dict with h, J, fn, cfn, top, e.g.
+    pinned host tensors).  Returns dict(h, J, report, fn, cfn, top)."""
+    msa = _as_input(msa, np.int8)
+    B, N = msa.shape
+    L = N if L is None else L
+    o = default_opts(**opts)
+    if out is None:
+        out = dict(h=_like(msa, (N, Q), np.float32), J=_like(msa, (N, Q, N, Q), np.float32),
+                   fn=_like(msa, (N, N), np.float64), cfn=_like(msa, (N, N), np.float64),
+                   top=_like(msa, (L, 2), np.int32))
+    rep = N_.plm_report()
+    st = ctx.lib.plmdca_run(ctx.handle, _ptr(msa), B, N, Q, ctypes.byref(o), L, min_sep,
+                            _ptr(out["h"]), _ptr(out["J"]), _ptr(out["fn"]), _ptr(out["cfn"]),
+                            _ptr(out["top"]), ctypes.byref(rep))
+    if st != N_.PLM_OK and (st != N_.PLM_ENOTCONV or raise_on_notconv):
+        ctx.check(st)
+    d = rep.as_dict()
+    d["status"] = N_.STATUS_NAMES.get(st, st)
+    return dict(h=out["h"], J=out["J"], report=d, fn=out["fn"], cfn=out["cfn"], top=out["top"])

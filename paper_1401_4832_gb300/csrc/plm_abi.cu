@@ -1444,6 +1444,38 @@ plm_status plm_scores(plm_ctx *ctx, const float *J, int N, int q, const plm_scor
     return PLM_OK;
 }
 
+plm_status plmdca_run(plm_ctx *ctx, const int8_t *msa, int B, int N, int q,
+                      const plm_opts *opts, int L, int min_sep, float *h_out, float *J_out,
+                      double *fn_out, double *cfn_out, int32_t *topL_out, plm_report *report)
+{
+    if (!ctx) return PLM_EINVAL;
+    plm_status s = check_common(ctx, B, N, q);
+    if (s) return s;
+    CK(cudaSetDevice(ctx->device));
+    const size_t NQ = (size_t)N * Q;
+    // the couplings stay on the device between the solve and the scores
+    Staged hs, Js;
+    CK(stage_out(ctx, "run_h", h_out, NQ * sizeof(float), &hs));
+    CK(stage_out(ctx, "run_J", J_out, NQ * NQ * sizeof(float), &Js));
+    if (!hs.dev) CK(ws(ctx, "run_h", NQ * sizeof(float), &hs.dev));
+    if (!Js.dev) CK(ws(ctx, "run_J", NQ * NQ * sizeof(float), &Js.dev));
+    plm_family fam;
+    fam.msa = msa;
+    fam.B = B;
+    fam.N = N;
+    fam.h_out = (float *)hs.dev;
+    fam.J_out = (float *)Js.dev;
+    const plm_status st = solve_families(ctx, &fam, 1, q, opts, report, false);
+    if (st != PLM_OK && st != PLM_ENOTCONV) return st;
+    s = plm_scores(ctx, (const float *)Js.dev, N, q, nullptr, nullptr, fn_out, cfn_out, topL_out,
+                   L, min_sep);
+    if (s) return s;
+    CK(copy_back(ctx, hs));
+    CK(copy_back(ctx, Js));
+    if (hs.host || Js.host) CK(cudaStreamSynchronize(ctx->stream));
+    return st;
+}
+
 plm_status msa_frequencies(plm_ctx *ctx, const int8_t *msa, const float *w, double beff, int B,
                            int N, int q, double *f_out)
 {

@@ -90,3 +90,30 @@ def test_family_solve_matches_oracle(ctx, fam, ref, prec):
     cfn_err = float(np.max(np.abs(cfn_g.cpu().numpy() - ref["cfn"])))
     assert _top_equal_up_to_ties(top_g.cpu().numpy()[:len(top_o)], top_o, ref["cfn"],
                                  2 * cfn_err + 1e-12), cfn_err
+
+
+def test_plmdca_run_equals_solve_then_scores():
+    # the one-call rundown (plmdca_run) from host buffers (pinned and not)
+    # and from device buffers gives exactly the two-call result
+    from paper_1401_4832_gb300 import api
+    S = synth.tiny().msa
+    N = S.shape[1]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream), api.Context(0, stream) as ctx:
+        Sd = torch.from_numpy(S).cuda()
+        h, J, rep = api.plm_solve(ctx, Sd, gtol=1e-5)
+        fn, cfn, top = api.fn_apc_scores(ctx, J)
+        r_dev = api.plmdca(ctx, Sd, gtol=1e-5)
+        r_np = api.plmdca(ctx, S, gtol=1e-5)
+        pin = dict(h=torch.empty((N, 21)).pin_memory(), J=torch.empty((N, 21, N, 21)).pin_memory(),
+                   fn=torch.empty((N, N), dtype=torch.float64).pin_memory(),
+                   cfn=torch.empty((N, N), dtype=torch.float64).pin_memory(),
+                   top=torch.empty((N, 2), dtype=torch.int32).pin_memory())
+        r_pin = api.plmdca(ctx, torch.from_numpy(S).pin_memory(), out=pin, gtol=1e-5)
+        stream.synchronize()
+    for r in (r_dev, r_np, r_pin):
+        for k, ref in (("h", h), ("J", J), ("fn", fn), ("cfn", cfn), ("top", top)):
+            got = r[k]
+            got = got.cpu().numpy() if hasattr(got, "cpu") else got
+            assert np.array_equal(got, ref.cpu().numpy()), k
+        assert r["report"]["n_converged"] == N
