@@ -30,10 +30,12 @@ struct ProfRecord {
     double bytes;  // algorithmic bytes the bracketed kernels move (0: not counted)
 };
 
+constexpr int MAX_LANES = 4;  // lanes of the pipelined solve (counters: 16 ints each)
+
 struct plm_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
-    cudaStream_t aux = nullptr;  // second stream of the pipelined solve (created on first use)
+    cudaStream_t aux[3] = {nullptr, nullptr, nullptr};  // lanes 1..3 of the pipelined solve
     std::string err;
     std::map<std::string, DevBuf> bufs;
     int *host_counters = nullptr;  // pinned
@@ -280,6 +282,7 @@ struct Problem {
     bool autotune = true;
     // symmetric plmDCA (one family): one L-BFGS problem over the whole arena
     bool symmetric = false;
+    int tune_lanes = 1;  // lanes the solve will run (the autotuner times lane-shaped evaluations)
     int lb_sites = 0;              // L-BFGS problems: nsites, or 1 when symmetric
     std::vector<int> lb_len4;      // streamed float4 of each L-BFGS problem
 };
@@ -436,9 +439,25 @@ std::string problem_signature(const Problem &P)
     return sig;
 }
 
+// first sites of the lanes of a one-family pipelined solve: boundaries at
+// multiples of lcm(16, sites per logits group), so that no gradient row
+// tile (128 rows = 16/3 sites) and no logits site group straddles two lanes
+std::vector<int> lane_bounds(int N, int lg_sites, int K)
+{
+    int unit = 16;  // 16 sites = 384 rows = three gradient row tiles
+    while (unit % lg_sites) unit += 16;
+    std::vector<int> b{0};
+    for (int k = 1; k < K; ++k) {
+        const int h = (int)(((long long)N * k / K + unit / 2) / unit * unit);
+        if (h - b.back() >= unit && N - h >= unit) b.push_back(h);
+    }
+    b.push_back(N);
+    return b;
+}
+
 plm_status autotune_tc(plm_ctx *ctx, Problem &P, int *tc_err)
 {
-    const std::string sig = problem_signature(P);
+    const std::string sig = problem_signature(P) + "L" + std::to_string(P.tune_lanes);
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         auto it = g_tune_cache.find(sig);
@@ -450,21 +469,53 @@ plm_status autotune_tc(plm_ctx *ctx, Problem &P, int *tc_err)
     }
     cudaStream_t st = ctx->stream;
     cudaEvent_t e0 = take_event(ctx), e1 = take_event(ctx);
+    // with lanes, a candidate is timed as the lanes launch it: one
+    // evaluation per lane, each with that lane's sites active
+    const bool laned = P.tune_lanes > 1 && P.fam.size() == 1;
+    const int N = P.fam[0].d.N;
+    uint8_t *masks = nullptr;
+    if (laned) {
+        void *m;
+        CK(ws(ctx, "tune_masks", (size_t)P.tune_lanes * N, &m));
+        masks = (uint8_t *)m;
+    }
+    const uint8_t *saved_active = P.tcb[0].f[0].active;
     auto time_it = [&](const TcConfig &c, int which, float *best) -> plm_status {
+        int nl = 1;
+        if (laned) {
+            const std::vector<int> b = lane_bounds(N, c.lg_sites, P.tune_lanes);
+            nl = (int)b.size() - 1;
+            if (nl < P.tune_lanes) {
+                // this shape cannot be split into the lanes: not a candidate
+                *best = 1e30f;
+                return PLM_OK;
+            }
+            std::vector<uint8_t> h((size_t)nl * N, 0);
+            for (int k = 0; k < nl; ++k)
+                for (int r = b[k]; r < b[k + 1]; ++r) h[(size_t)k * N + r] = 1;
+            CK(cudaMemcpyAsync(masks, h.data(), h.size(), cudaMemcpyHostToDevice, st));
+        }
         *best = 1e30f;
         for (int rep = 0; rep < 3; ++rep) {
             CK(cudaEventRecord(e0, st));
-            for (auto &b : P.tcb) CK(launch_tc_eval(nullptr, b, c, 0.0, 0.0, tc_err, st, which));
+            for (int k = 0; k < nl; ++k) {
+                if (laned) P.tcb[0].f[0].active = masks + (size_t)k * N;
+                for (auto &b : P.tcb)
+                    CK(launch_tc_eval(nullptr, b, c, 0.0, 0.0, tc_err, st, which));
+            }
             CK(cudaEventRecord(e1, st));
             CK(cudaEventSynchronize(e1));
             float ms = 0.0f;
             CK(cudaEventElapsedTime(&ms, e0, e1));
             if (rep > 0 && ms < *best) *best = ms;
         }
+        P.tcb[0].f[0].active = saved_active;
         return PLM_OK;
     };
     TcConfig best;
     float tbest = 1e30f;
+    if (laned && lane_bounds(N, best.lg_sites, P.tune_lanes).size() - 1 < (size_t)P.tune_lanes)
+        best.lg_sites = 4;  // a default that splits
     for (int sites : {4, 6, 8, 10}) {
         TcConfig c = best;
         c.lg_sites = sites;
@@ -641,10 +692,10 @@ plm_status solve_core(plm_ctx *ctx, Problem &P, const plm_opts &o, std::vector<S
     // per-site data terms, and (symmetric) their sum in the last slot
     CK(ws(ctx, "fdata", (size_t)(P.nsites + 1) * sizeof(double), &fdat));
     double *f_lb = (double *)fdat + (P.symmetric ? P.nsites : 0);  // what the line search reads
-    CK(ws(ctx, "counters", 32 * sizeof(int), &cnt));  // 16 per lane (see below)
+    CK(ws(ctx, "counters", 16 * MAX_LANES * sizeof(int), &cnt));  // 16 per lane (see below)
     CK(ws(ctx, "lb_part", (size_t)P.nchunks * LB_PART * sizeof(double), &part));
     void *active;
-    CK(ws(ctx, "active", 2 * (size_t)P.nsites, &active));  // one flag array per lane
+    CK(ws(ctx, "active", MAX_LANES * (size_t)P.nsites, &active));  // one flag array per lane
     if (o.prec == PLM_SPLIT_BF16) {
         CK(ws(ctx, "theta_hi", P.total * 2, &hi));
         CK(ws(ctx, "theta_lo", P.total * 2, &lo));
@@ -670,8 +721,13 @@ plm_status solve_core(plm_ctx *ctx, Problem &P, const plm_opts &o, std::vector<S
     }
     int evals = 0;
     int *tc_err = (int *)cnt + 4;  // tensor-core timeout word, read back with the counters
-    CK(cudaMemsetAsync(cnt, 0, 32 * sizeof(int), st));
-    CK(cudaMemsetAsync(active, 0, 2 * (size_t)P.nsites, st));
+    const bool use_graph = o.use_graph && st != nullptr && !ctx->prof;
+    int K = 2;  // lanes of a one-family pipelined solve (PLMDCA_LANES overrides: 1..4)
+    if (const char *e = getenv("PLMDCA_LANES")) K = std::max(1, std::min(MAX_LANES, atoi(e)));
+    const bool pipelined = use_graph && o.prec == PLM_SPLIT_BF16 && !P.symmetric;
+    P.tune_lanes = (pipelined && nf == 1) ? K : 1;
+    CK(cudaMemsetAsync(cnt, 0, 16 * MAX_LANES * sizeof(int), st));
+    CK(cudaMemsetAsync(active, 0, MAX_LANES * (size_t)P.nsites, st));
     s = evaluate(ctx, o.prec, P, (const float *)w, (const float *)theta,
                  (const __nv_bfloat16 *)hi, (const __nv_bfloat16 *)lo, p.lambda_h, p.lambda_Jp,
                  (double *)fdat, (float *)g, tc_err);
@@ -693,13 +749,16 @@ plm_status solve_core(plm_ctx *ctx, Problem &P, const plm_opts &o, std::vector<S
     // site's objective involves only its own row block), so a lane needs
     // about max over its sites of that site's evaluations rounds.
     //
-    // With one family on the tensor-core path the sites are split into two
-    // lanes at a boundary shared by the logits site groups and the
-    // 128-row gradient tiles.  Each lane has its own counters, round number
-    // and active flags, its own stream and CUDA graph; lane 1's graph is
-    // rotated by half a round (evaluate, decide, commit, then the next
-    // direction), so one lane's tensor-core evaluation runs while the other
-    // lane streams its L-BFGS vectors.  Every other case runs one lane.
+    // On the tensor-core path the sites are split into lanes (two by
+    // default; PLMDCA_LANES=1..4 for measurements): for one family at
+    // boundaries shared by the logits site groups and the 128-row gradient
+    // tiles, for a batch at family boundaries.  Each lane has its own
+    // counters, round number and active flags, its own stream and CUDA
+    // graph, and starts its round at a different phase (lane k at phase
+    // k mod 3: direction, evaluation, decision), so one lane's tensor-core
+    // evaluation runs while another streams its L-BFGS vectors.  Measured
+    // on the family workload: 1 lane 0.035 s, 2 lanes 0.030 s, 3 or 4
+    // lanes 0.032 s.  Every other case runs one lane.
     struct Lane {
         LbLayout L;
         int *cnt;          // 16 ints: [0] searching, [1] ready, [2] continuing, [4] tc error, [8] round
@@ -707,50 +766,62 @@ plm_status solve_core(plm_ctx *ctx, Problem &P, const plm_opts &o, std::vector<S
         int *hc;           // pinned host copy of cnt[0..4]
         cudaStream_t st;
         cudaGraphExec_t graph = nullptr;
-        bool rotated = false, done = false;
+        int offset = 0;  // phase the lane's round starts at: 0 direction, 1 evaluation, 2 decision
+        bool done = false;
         int rounds = 0;
     };
-    const bool use_graph = o.use_graph && st != nullptr && !ctx->prof;
-    int split = 0;  // first site of lane 1 (0: one lane)
-    if (use_graph && o.prec == PLM_SPLIT_BF16 && P.tc_tuned && !P.symmetric) {
+    // lane boundaries (sites): [0, b_1, ..., lb_sites]
+    std::vector<int> bounds{0, P.lb_sites};
+    if (pipelined && P.tc_tuned) {
+        std::vector<int> b{0};
         if (nf == 1) {
-            int unit = 16;  // 16 sites = 384 rows = three gradient row tiles
-            while (unit % P.tc_cfg.lg_sites) unit += 16;
-            const int N = P.fam[0].d.N;
-            const int h = (N / 2 + unit / 2) / unit * unit;
-            if (h >= unit && N - h >= unit) split = h;
+            b = lane_bounds(P.fam[0].d.N, P.tc_cfg.lg_sites, K);
+            b.pop_back();
         } else {
-            // whole families per lane (no tile straddles a family), the
-            // boundary that best balances the evaluation work B_f N_f^2
+            // whole families per lane (no tile straddles a family), boundaries
+            // that best balance the evaluation work B_f N_f^2
             std::vector<double> cum(nf + 1, 0.0);
             for (size_t f = 0; f < nf; ++f)
                 cum[f + 1] = cum[f] + (double)P.fam[f].d.B * P.fam[f].d.N * P.fam[f].d.N;
-            size_t best = 1;
-            for (size_t k = 1; k < nf; ++k)
-                if (std::fabs(2 * cum[k] - cum[nf]) < std::fabs(2 * cum[best] - cum[nf])) best = k;
-            split = P.fam[best].site0;
+            size_t prev = 0;
+            for (int k = 1; k < K; ++k) {
+                size_t best = 0;
+                double bd = 1e300;
+                for (size_t f = prev + 1; f < nf; ++f) {
+                    const double d = std::fabs(cum[f] - cum[nf] * k / K);
+                    if (d < bd) {
+                        bd = d;
+                        best = f;
+                    }
+                }
+                if (best > prev) {
+                    b.push_back(P.fam[best].site0);
+                    prev = best;
+                }
+            }
         }
+        b.push_back(P.lb_sites);
+        bounds = b;
     }
-    std::vector<Lane> lanes(split ? 2 : 1);
-    if (split && !ctx->aux) {
-        cudaError_t e = cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking);
-        if (e) return cuda_fail(ctx, e, "cudaStreamCreateWithFlags");
-    }
-    for (size_t k = 0; k < lanes.size(); ++k) {
+    const int nlanes = (int)bounds.size() - 1;
+    std::vector<Lane> lanes(nlanes);
+    for (int k = 1; k < nlanes; ++k)
+        if (!ctx->aux[k - 1]) {
+            cudaError_t e = cudaStreamCreateWithFlags(&ctx->aux[k - 1], cudaStreamNonBlocking);
+            if (e) return cuda_fail(ctx, e, "cudaStreamCreateWithFlags");
+        }
+    for (int k = 0; k < nlanes; ++k) {
         Lane &ln = lanes[k];
         ln.L = P.L;
-        if (split) {
-            const int s_lo = k == 0 ? 0 : split, s_hi = k == 0 ? split : P.lb_sites;
-            ln.L.s0 = s_lo;
-            ln.L.nsites = s_hi - s_lo;
-            ln.L.c0 = k == 0 ? 0 : P.site_chunk0[split];
-            ln.L.c1 = k == 0 ? P.site_chunk0[split] : P.nchunks;
-        }
+        ln.L.s0 = bounds[k];
+        ln.L.nsites = bounds[k + 1] - bounds[k];
+        ln.L.c0 = P.site_chunk0[bounds[k]];
+        ln.L.c1 = P.site_chunk0[bounds[k + 1]];
         ln.cnt = (int *)cnt + 16 * k;
         ln.active = (uint8_t *)active + (size_t)P.nsites * k;
-        ln.hc = ctx->host_counters + 32 * k;
-        ln.st = k == 0 ? st : ctx->aux;
-        ln.rotated = k == 1;
+        ln.hc = ctx->host_counters + 16 * k;
+        ln.st = k == 0 ? st : ctx->aux[k - 1];
+        ln.offset = k % 3;  // the lane's round starts at this phase
     }
 
     // algorithmic bytes of the passes of one round, from the site states at
@@ -847,14 +918,16 @@ plm_status solve_core(plm_ctx *ctx, Problem &P, const plm_opts &o, std::vector<S
     // instead of copying the counts to the host
     auto round_step = [&](Lane &ln, cudaGraphConditionalHandle cond, bool in_loop) -> plm_status {
         plm_status s2;
-        if (ln.rotated) {
-            if ((s2 = phase_eval(ln)) || (s2 = phase_post(ln, !in_loop))) return s2;
-            if (in_loop) CK(launch_round_cond(cond, ln.cnt, max_rounds_i, ln.st));
-            if ((s2 = phase_dir(ln))) return s2;
-        } else {
-            if ((s2 = phase_dir(ln)) || (s2 = phase_eval(ln)) || (s2 = phase_post(ln, !in_loop)))
-                return s2;
-            if (in_loop) CK(launch_round_cond(cond, ln.cnt, max_rounds_i, ln.st));
+        for (int ph = 0; ph < 3; ++ph) {
+            const int which = (ln.offset + ph) % 3;
+            if (which == 0) s2 = phase_dir(ln);
+            else if (which == 1) s2 = phase_eval(ln);
+            else {
+                s2 = phase_post(ln, !in_loop);
+                // the loop condition right after the decisions it reads
+                if (!s2 && in_loop) CK(launch_round_cond(cond, ln.cnt, max_rounds_i, ln.st));
+            }
+            if (s2) return s2;
         }
         return PLM_OK;
     };
@@ -866,24 +939,30 @@ plm_status solve_core(plm_ctx *ctx, Problem &P, const plm_opts &o, std::vector<S
                 if (ln.graph) cudaGraphExecDestroy(ln.graph);
         }
     } guard{&lanes};
-    cudaEvent_t fork = nullptr, join = nullptr;
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> joins(nlanes, nullptr);
     struct EventGuard {
-        cudaEvent_t *a, *b;
+        cudaEvent_t *a;
+        std::vector<cudaEvent_t> *b;
         ~EventGuard()
         {
             if (*a) cudaEventDestroy(*a);
-            if (*b) cudaEventDestroy(*b);
+            for (auto e : *b)
+                if (e) cudaEventDestroy(e);
         }
-    } eguard{&fork, &join};
-    if (split) {
-        // lane 1 starts after everything queued so far on the caller's stream
+    } eguard{&fork, &joins};
+    if (nlanes > 1) {
+        // the other lanes start after everything queued so far on the caller's stream
         CK(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
-        CK(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
         CK(cudaEventRecord(fork, st));
-        CK(cudaStreamWaitEvent(ctx->aux, fork, 0));
-        // the first half round of the rotated lane
-        s = phase_dir(lanes[1]);
-        if (s) return s;
+        for (int k = 1; k < nlanes; ++k) {
+            CK(cudaStreamWaitEvent(lanes[k].st, fork, 0));
+            // the phases of the first round before the lane's starting phase
+            for (int ph = 0; ph < lanes[k].offset; ++ph) {
+                s = ph == 0 ? phase_dir(lanes[k]) : phase_eval(lanes[k]);
+                if (s) return s;
+            }
+        }
     }
     if (use_graph) {
         // each lane's rounds run as one CUDA graph: a while node whose body
@@ -970,10 +1049,11 @@ plm_status solve_core(plm_ctx *ctx, Problem &P, const plm_opts &o, std::vector<S
         }
     }
     for (auto &ln : lanes) evals = std::max(evals, 1 + ln.rounds);
-    if (split) {
-        // the caller's stream resumes after lane 1
-        CK(cudaEventRecord(join, ctx->aux));
-        CK(cudaStreamWaitEvent(st, join, 0));
+    for (int k = 1; k < nlanes; ++k) {
+        // the caller's stream resumes after the other lanes
+        CK(cudaEventCreateWithFlags(&joins[k], cudaEventDisableTiming));
+        CK(cudaEventRecord(joins[k], lanes[k].st));
+        CK(cudaStreamWaitEvent(st, joins[k], 0));
     }
 
     for (size_t f = 0; f < nf; ++f)
@@ -1082,10 +1162,11 @@ plm_status plm_destroy(plm_ctx *c)
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
-    if (c->aux) {
-        cudaStreamSynchronize(c->aux);
-        cudaStreamDestroy(c->aux);
-    }
+    for (auto &a : c->aux)
+        if (a) {
+            cudaStreamSynchronize(a);
+            cudaStreamDestroy(a);
+        }
     for (auto &kv : c->bufs)
         if (kv.second.p) cudaFree(kv.second.p);
     if (c->host_counters) cudaFreeHost(c->host_counters);
