@@ -348,7 +348,7 @@ k_tc_logits(const __grid_constant__ LogitsParams P, int *__restrict__ err)
     if (threadIdx.x == 0) {
         for (int s = 0; s < MAX_STAGES; ++s) {
             mbar_init(&full_b[s], 1);
-            mbar_init(&full_a[s], 128);
+            mbar_init(&full_a[s], 4);  // one arrival per producer warp
             mbar_init(&empty_[s], 1);
         }
         for (int a = 0; a < 2; ++a) {
@@ -472,8 +472,10 @@ k_tc_logits(const __grid_constant__ LogitsParams P, int *__restrict__ err)
                 const int s = (int)(kit % NST);
                 const long long n = kit / NST;
                 fetch(kc + 1 < NK ? kc + 1 : kc, nxt5);
-                if (n > 0 &&
-                    !mbar_wait(&empty_[s], (uint32_t)((n - 1) & 1), &abort_sh, err, ERR_TIMEOUT_PROD)) {
+                // the warp leaves together (it arrives once per stage)
+                const bool got = n == 0 || mbar_wait(&empty_[s], (uint32_t)((n - 1) & 1), &abort_sh,
+                                                     err, ERR_TIMEOUT_PROD);
+                if (!__all_sync(0xffffffffu, got)) {
                     ok = false;
                     break;
                 }
@@ -498,8 +500,11 @@ k_tc_logits(const __grid_constant__ LogitsParams P, int *__restrict__ err)
                         *(uint16_t *)(rowp + ((((pf >> 3) ^ (p & 7)) << 4) | ((pf & 7) << 1))) =
                             0x3F80;
                 }
+                // every thread makes its stores visible to the tensor core's
+                // proxy; then one arrival per warp
                 fence_proxy_async();
-                mbar_arrive(&full_a[s]);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&full_a[s]);
 #pragma unroll
                 for (int u = 0; u < 5; ++u) cur5[u] = nxt5[u];
             }
@@ -656,7 +661,7 @@ k_tc_grad(const __grid_constant__ GradParams P, float two_lh, float two_lj, int 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NST; ++s) {
             mbar_init(&full_b[s], 1);
-            mbar_init(&full_a[s], GR_PROD);
+            mbar_init(&full_a[s], GR_PROD / 32);  // one arrival per producer warp
             mbar_init(&empty_[s], 1);
         }
         mbar_init(&acc_full, 1);
@@ -737,8 +742,10 @@ k_tc_grad(const __grid_constant__ GradParams P, float two_lh, float two_lj, int 
             const int kn = kc + 1 < NK ? kc + 1 : kc;
 #pragma unroll
             for (int q = 0; q < 4; ++q) nxt[q] = __ldg(srcT + (size_t)kn * (TC_BK / 16) + q);
-            if (n > 0 && !mbar_wait(&empty_[s], (n - 1) & 1, &abort_sh, err, ERR_TIMEOUT_PROD))
-                break;
+            // the warp leaves together (it arrives once per stage)
+            const bool got = n == 0 || mbar_wait(&empty_[s], (n - 1) & 1, &abort_sh, err,
+                                                 ERR_TIMEOUT_PROD);
+            if (!__all_sync(0xffffffffu, got)) break;
             uint8_t *bt = smem + s * GRSTAGE + 2 * GR_A_BYTES;
             if (prow) {
 #pragma unroll
@@ -757,7 +764,8 @@ k_tc_grad(const __grid_constant__ GradParams P, float two_lh, float two_lj, int 
                 }
             }
             fence_proxy_async();
-            mbar_arrive(&full_a[s]);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&full_a[s]);
 #pragma unroll
             for (int q = 0; q < 4; ++q) cur[q] = nxt[q];
         }
