@@ -198,10 +198,20 @@ def run_batch(args):
                     times.append(e0.elapsed_time(e1) / 1000.0)
             out[mode] = {"s": statistics.mean(times),
                          "sites_not_converged": sum(r[2]["n_noise"] + r[2]["n_failed"] for r in res)}
+    # one profiled batched solve: per-kernel device time
+    from paper_1401_4832_gb300 import _native
+    lib = _native.load()
+    lib.plm_profile(ctx.handle, 1)
+    with torch.cuda.stream(stream):
+        res = api.plm_solve_batch(ctx, msas, gtol=args.gtol)
+    kern = read_profile(lib, ctx)
+    lib.plm_profile(ctx.handle, 0)
     print(json.dumps({"workload": "batch: 64 synthetic families, N~U{50..300}, B log-uniform [500,20000]",
                       "families": len(fams), "sum_N": sum(f.N for f in fams),
                       "sum_BN": sum(f.B * f.N for f in fams), "results": out,
-                      "batched_speedup": out["one_by_one"]["s"] / out["batched"]["s"]}), flush=True)
+                      "batched_speedup": out["one_by_one"]["s"] / out["batched"]["s"],
+                      "evals_per_solve": res[0][2]["evals"],
+                      "kernels_profiled_ms": {k: v[1] for k, v in kern.items()}}), flush=True)
 
 
 def run_scale(args):
