@@ -39,6 +39,7 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="auto", choices=["auto", "fp32", "split_bf16"])
     ap.add_argument("--gtol", type=float, default=1e-4)
+    ap.add_argument("--lbfgs-m", type=int, default=5, help="L-BFGS memory (curvature pairs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32-cmp", action="store_true",
                     help="skip timing the plain FP32 path beside the split-bf16 one")
@@ -430,7 +431,7 @@ def main():
             api.plm_solve(ctx, msa[:64, :8].contiguous(), prec="split_bf16", max_iter=1)
         except _native.PlmError:
             prec = "fp32"
-    opts = dict(gtol=args.gtol, prec=prec)
+    opts = dict(gtol=args.gtol, prec=prec, lbfgs_m=args.lbfgs_m)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{device}")
 
     def step():
@@ -561,7 +562,7 @@ def main():
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "bf16" if prec == "split_bf16" else "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "N": N, "B": B, "q": 21, "gtol": args.gtol,
-                       "precision": prec, "lbfgs_m": 5, "lambda_h": 0.01, "lambda_J": 0.01,
+                       "precision": prec, "lbfgs_m": args.lbfgs_m, "lambda_h": 0.01, "lambda_J": 0.01,
                        "x": 0.8, "l2": "flushed between timed steps (256 MiB write)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "evals_per_s": evals / mean_t,
