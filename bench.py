@@ -418,8 +418,8 @@ def main():
     torch.cuda.set_device(device)
     pk, pk_kind = peaks()
 
-    # one replica per rank (weak scaling): family seed = rank
-    fam = synth.protein_family(seed=rank)
+    # one replica per rank (weak scaling): its own family
+    fam = synth.protein_family(seed=replica_seed(rank))
     B, N = fam.B, fam.N
     msa = torch.from_numpy(fam.msa).to(f"cuda:{device}")
     stream = torch.cuda.Stream(device)
@@ -468,13 +468,8 @@ def main():
     if dist:
         dist.barrier()
     mean_t = statistics.mean(times)
-    if dist:
-        tt = torch.tensor([sum(times)], device=f"cuda:{device}", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_max = tt.item()
-    else:
-        total_max = sum(times)
-    value = total_max / (args.steps * world)  # seconds per solve for the whole job
+    value = job_seconds_per_solve(sum(times), args.steps, world, dist,
+                                  f"cuda:{device}" if dist else "cpu")
     evals = statistics.mean(r["evals"] for r in reps)
 
     # the plain FP32 GPU path at the same gtol (the comparison the metric names)
@@ -610,6 +605,24 @@ def ncu_traffic(kernel):
     except OSError:
         return None
     return ent[2] if h == ent[1] else None
+
+
+def replica_seed(rank):
+    """Multi-GPU runs are replicas (the path needs no exchange, each rank
+    solves its own family): the family of rank r is drawn with seed r."""
+    return int(rank)
+
+
+def job_seconds_per_solve(local_total_s, steps, world, dist=None, device="cpu"):
+    """Whole-job seconds per solve: the slowest rank's total over the timed
+    steps (max over ranks), divided by all the solves the job did."""
+    total = float(local_total_s)
+    if dist is not None and world > 1:
+        import torch
+        t = torch.tensor([total], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total = t.item()
+    return total / (steps * world)
 
 
 def read_profile(lib, ctx):
