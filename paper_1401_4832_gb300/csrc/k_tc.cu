@@ -46,7 +46,7 @@ constexpr int MAX_STAGES = 4;
 constexpr int MAX_LG_SITES = 10;           // sites per logits tile: 2..10, even
 constexpr int TMEM_COLS = 256;
 constexpr int LG_A_BYTES = TC_M * TC_BK * 2;          // 16 KB
-constexpr int GR_A_BYTES = TC_M * TC_BK * 2;          // 16 KB
+constexpr int GR_A_BYTES = TC_M * TC_BK * 2;          // 16 KB per 128 rows
 constexpr int SMEM_BUDGET = 224 * 1024;  // pipeline bytes; + 1 KB alignment slack and the static
                                          // shared memory stay under the 227 KB per block
 constexpr long long WAIT_CYCLES = 4000000000LL;        // ~2 s at 2 GHz
@@ -282,7 +282,7 @@ struct LogitsParams {
 
 struct GradParams {
     TcBatch b;
-    int ncols, stages, stage_bytes;  // tile: 128 rows x ncols columns
+    int rows, ncols, stages, stage_bytes;  // tile: rows (128 or 256) x ncols columns
     CUtensorMap dhi[MAX_FAM], dlo[MAX_FAM];
 };
 
@@ -639,6 +639,9 @@ k_tc_grad(const __grid_constant__ GradParams P, float two_lh, float two_lj, int 
     d.K = F.N * Q + 1;
     const int local = blockIdx.x - F.tile0_grad;
     const int GRN = P.ncols, NST = P.stages, GRSTAGE = P.stage_bytes;
+    // MR rows = MH halves of 128; half h accumulates in tensor-memory
+    // columns [256 h, 256 h + GRN) from the A rows at h * GR_A_BYTES
+    const int MR = P.rows, MH = MR / TC_M, ABYTES = MH * GR_A_BYTES;
     const int nct = (d.KP + GRN - 1) / GRN;
     extern __shared__ uint8_t dsmem[];
     uint8_t *smem = align1024(dsmem);
@@ -648,10 +651,10 @@ k_tc_grad(const __grid_constant__ GradParams P, float two_lh, float two_lj, int 
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c0 = (local % nct) * GRN;
-    const int rs0 = (local / nct) * TC_M;
+    const int rs0 = (local / nct) * MR;
     if (F.active) {
         bool any = false;
-        for (int r = rs0 / QP; r <= (rs0 + TC_M - 1) / QP && r < F.N; ++r)
+        for (int r = rs0 / QP; r <= (rs0 + MR - 1) / QP && r < F.N; ++r)
             any |= F.active[r] != 0;
         if (!any) return;
     }
@@ -669,7 +672,7 @@ k_tc_grad(const __grid_constant__ GradParams P, float two_lh, float two_lj, int 
         fence_mbar_init();
     }
     if (warp == 1) {
-        tmem_alloc(&tmem_sh, TMEM_COLS);
+        tmem_alloc(&tmem_sh, MH * TMEM_COLS);
         tmem_relinquish();
     }
     tc_fence_before();
@@ -685,9 +688,9 @@ k_tc_grad(const __grid_constant__ GradParams P, float two_lh, float two_lj, int 
                 if (n > 0 && !mbar_wait(&empty_[s], (n - 1) & 1, &abort_sh, err, ERR_TIMEOUT_TMA))
                     break;
                 uint8_t *st = smem + s * GRSTAGE;
-                mbar_expect_tx(&full_b[s], 2 * GR_A_BYTES);
+                mbar_expect_tx(&full_b[s], 2 * ABYTES);
                 tma_load_2d(st, &tm_dhi, &full_b[s], kc * TC_BK, rs0);
-                tma_load_2d(st + GR_A_BYTES, &tm_dlo, &full_b[s], kc * TC_BK, rs0);
+                tma_load_2d(st + ABYTES, &tm_dlo, &full_b[s], kc * TC_BK, rs0);
                 issued = kc + 1;
             }
             for (int kc = issued - NST < 0 ? 0 : issued - NST; kc < issued; ++kc)
@@ -702,16 +705,19 @@ k_tc_grad(const __grid_constant__ GradParams P, float two_lh, float two_lj, int 
                 if (!mbar_wait(&full_a[s], n & 1, &abort_sh, err, ERR_TIMEOUT_MMA)) break;
                 tc_fence_after();
                 uint8_t *st = smem + s * GRSTAGE;
-                const uint32_t ah = smem_u32(st);
-                const uint32_t al = smem_u32(st + GR_A_BYTES);
-                const uint32_t bx = smem_u32(st + 2 * GR_A_BYTES);
+                const uint32_t bx = smem_u32(st + 2 * ABYTES);
+                for (int h = 0; h < MH; ++h) {
+                    const uint32_t ah = smem_u32(st + h * GR_A_BYTES);
+                    const uint32_t al = smem_u32(st + ABYTES + h * GR_A_BYTES);
+                    const uint32_t dt = tmem + h * TMEM_COLS;
 #pragma unroll
-                for (int k = 0; k < TC_BK / 16; ++k)
-                    mma_bf16(tmem, sdesc(ah + 32 * k), sdesc(bx + 32 * k), idesc,
-                             (kc > 0 || k > 0) ? 1u : 0u);
+                    for (int k = 0; k < TC_BK / 16; ++k)
+                        mma_bf16(dt, sdesc(ah + 32 * k), sdesc(bx + 32 * k), idesc,
+                                 (kc > 0 || k > 0) ? 1u : 0u);
 #pragma unroll
-                for (int k = 0; k < TC_BK / 16; ++k)
-                    mma_bf16(tmem, sdesc(al + 32 * k), sdesc(bx + 32 * k), idesc, 1u);
+                    for (int k = 0; k < TC_BK / 16; ++k)
+                        mma_bf16(dt, sdesc(al + 32 * k), sdesc(bx + 32 * k), idesc, 1u);
+                }
                 mma_commit(&empty_[s]);
             }
             mma_commit(&acc_full);
@@ -746,7 +752,7 @@ k_tc_grad(const __grid_constant__ GradParams P, float two_lh, float two_lj, int 
             const bool got = n == 0 || mbar_wait(&empty_[s], (n - 1) & 1, &abort_sh, err,
                                                  ERR_TIMEOUT_PROD);
             if (!__all_sync(0xffffffffu, got)) break;
-            uint8_t *bt = smem + s * GRSTAGE + 2 * GR_A_BYTES;
+            uint8_t *bt = smem + s * GRSTAGE + 2 * ABYTES;
             if (prow) {
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {  // 16 sequences per word group
@@ -780,8 +786,10 @@ k_tc_grad(const __grid_constant__ GradParams P, float two_lh, float two_lj, int 
         tc_fence_after();
         const int GS = GRN + 4;
         float *acc_s = (float *)smem;  // [128][GS]
-        const uint32_t tl = tmem + ((uint32_t)(q4 * 32) << 16);
         const int ng = GRN / 32;  // 16-column groups per half
+        for (int h = 0; h < MH; ++h) {
+        const uint32_t tl = tmem + h * TMEM_COLS + ((uint32_t)(q4 * 32) << 16);
+        const int rh = rs0 + h * TC_M;  // first row of this half
 #pragma unroll 1
         for (int cc = half * ng; cc < (half + 1) * ng; ++cc) {
             float v[16];
@@ -802,7 +810,7 @@ k_tc_grad(const __grid_constant__ GradParams P, float two_lh, float two_lj, int 
             for (int k = 0; k < UNR; ++k) {  // issue all loads first
                 const int e = e0 + GR_PROD * k;
                 const int rr = e / (GRN / 4), c4 = e % (GRN / 4);
-                const int row = rs0 + rr, cb = c0 + 4 * c4;
+                const int row = rh + rr, cb = c0 + 4 * c4;
                 live[k] = ok && e < TC_M * (GRN / 4) && row < d.R && cb < d.KP;
                 th[k] = live[k] ? *(const float4 *)(theta + (size_t)row * d.KP + cb)
                                 : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -812,7 +820,7 @@ k_tc_grad(const __grid_constant__ GradParams P, float two_lh, float two_lj, int 
                 if (!live[k]) continue;
                 const int e = e0 + GR_PROD * k;
                 const int rr = e / (GRN / 4), c4 = e % (GRN / 4);
-                const int row = rs0 + rr, cb = c0 + 4 * c4;
+                const int row = rh + rr, cb = c0 + 4 * c4;
                 const int r = row / QP, sstate = row % QP;
                 const float4 a = *(const float4 *)(acc_s + rr * GS + 4 * c4);
                 const float av[4] = {a.x, a.y, a.z, a.w};
@@ -830,6 +838,8 @@ k_tc_grad(const __grid_constant__ GradParams P, float two_lh, float two_lj, int 
                 *(float4 *)(G + (size_t)row * d.KP + cb) = make_float4(o[0], o[1], o[2], o[3]);
             }
         }
+        if (h + 1 < MH) epi_bar256();  // the staging buffer is reused by the next half
+        }
     }
     tc_fence_before();
     __syncthreads();
@@ -838,7 +848,7 @@ k_tc_grad(const __grid_constant__ GradParams P, float two_lh, float two_lj, int 
         if (lane == 0) mbar_drain(&acc_full, 0);
         __syncwarp();
         tc_fence_after();
-        tmem_dealloc(tmem, TMEM_COLS);
+        tmem_dealloc(tmem, MH * TMEM_COLS);
     }
 }
 
@@ -989,7 +999,8 @@ int num_sms()
 bool tc_config_valid(const TcConfig &c)
 {
     return c.lg_sites >= 2 && c.lg_sites <= MAX_LG_SITES && c.lg_sites % 2 == 0 &&
-           c.gr_ncols >= 32 && c.gr_ncols <= 256 && c.gr_ncols % 32 == 0;
+           c.gr_ncols >= 32 && c.gr_ncols <= 256 && c.gr_ncols % 32 == 0 &&
+           (c.gr_rows == TC_M || c.gr_rows == 2 * TC_M);
 }
 
 cudaError_t launch_tc_eval(void *prof, const TcBatch &b_in, const TcConfig &cfg, double lambda_h,
@@ -1018,7 +1029,7 @@ cudaError_t launch_tc_eval(void *prof, const TcBatch &b_in, const TcConfig &cfg,
         F.tile0_logits = tl;
         F.tile0_grad = tg;
         tl += (F.BP / TC_M) * ((F.N + cfg.lg_sites - 1) / cfg.lg_sites);
-        tg += ((F.KP + cfg.gr_ncols - 1) / cfg.gr_ncols) * ((F.R + TC_M - 1) / TC_M);
+        tg += ((F.KP + cfg.gr_ncols - 1) / cfg.gr_ncols) * ((F.R + cfg.gr_rows - 1) / cfg.gr_rows);
     }
     lp.b.ntiles_logits = tl;
     lp.b.ntiles_grad = tg;
@@ -1027,15 +1038,16 @@ cudaError_t launch_tc_eval(void *prof, const TcBatch &b_in, const TcConfig &cfg,
     lp.ncols = lg_ncols;
     lp.stage_bytes = LG_A_BYTES + 2 * lg_ncols * TC_BK * 2;
     lp.stages = tc_stages(lp.stage_bytes, 0);
+    gp.rows = cfg.gr_rows;
     gp.ncols = cfg.gr_ncols;
-    gp.stage_bytes = 2 * GR_A_BYTES + cfg.gr_ncols * TC_BK * 2;
+    gp.stage_bytes = 2 * (cfg.gr_rows / TC_M) * GR_A_BYTES + cfg.gr_ncols * TC_BK * 2;
     gp.stages = tc_stages(gp.stage_bytes, 0);
     for (int i = 0; i < lp.b.nfam; ++i) {
         const FamDesc &F = lp.b.f[i];
         if (!make_map(&lp.hi[i], F.th_hi, F.KP, F.R, TC_BK, lg_ncols) ||
             !make_map(&lp.lo[i], F.th_lo, F.KP, F.R, TC_BK, lg_ncols) ||
-            !make_map(&gp.dhi[i], F.dt_hi, F.BP, F.R, TC_BK, TC_M) ||
-            !make_map(&gp.dlo[i], F.dt_lo, F.BP, F.R, TC_BK, TC_M))
+            !make_map(&gp.dhi[i], F.dt_hi, F.BP, F.R, TC_BK, cfg.gr_rows) ||
+            !make_map(&gp.dlo[i], F.dt_lo, F.BP, F.R, TC_BK, cfg.gr_rows))
             return cudaErrorInvalidValue;
     }
     if (which & 1) {

@@ -440,12 +440,15 @@ std::string problem_signature(const Problem &P)
 }
 
 // first sites of the lanes of a one-family pipelined solve: boundaries at
-// multiples of lcm(16, sites per logits group), so that no gradient row
-// tile (128 rows = 16/3 sites) and no logits site group straddles two lanes
-std::vector<int> lane_bounds(int N, int lg_sites, int K)
+// multiples of lcm(16 or 32, sites per logits group), so that no gradient
+// row tile (128 rows = 16/3 sites, or 256 rows) and no logits site group
+// straddles two lanes
+std::vector<int> lane_bounds(int N, const TcConfig &c, int K)
 {
-    int unit = 16;  // 16 sites = 384 rows = three gradient row tiles
-    while (unit % lg_sites) unit += 16;
+    // 16 sites = 384 rows = three 128-row tiles; 32 sites = three 256-row tiles
+    const int step = c.gr_rows > 128 ? 32 : 16;
+    int unit = step;
+    while (unit % c.lg_sites) unit += step;
     std::vector<int> b{0};
     for (int k = 1; k < K; ++k) {
         const int h = (int)(((long long)N * k / K + unit / 2) / unit * unit);
@@ -483,7 +486,7 @@ plm_status autotune_tc(plm_ctx *ctx, Problem &P, int *tc_err)
     auto time_it = [&](const TcConfig &c, int which, float *best) -> plm_status {
         int nl = 1;
         if (laned) {
-            const std::vector<int> b = lane_bounds(N, c.lg_sites, P.tune_lanes);
+            const std::vector<int> b = lane_bounds(N, c, P.tune_lanes);
             nl = (int)b.size() - 1;
             if (nl < P.tune_lanes) {
                 // this shape cannot be split into the lanes: not a candidate
@@ -514,7 +517,7 @@ plm_status autotune_tc(plm_ctx *ctx, Problem &P, int *tc_err)
     };
     TcConfig best;
     float tbest = 1e30f;
-    if (laned && lane_bounds(N, best.lg_sites, P.tune_lanes).size() - 1 < (size_t)P.tune_lanes)
+    if (laned && lane_bounds(N, best, P.tune_lanes).size() - 1 < (size_t)P.tune_lanes)
         best.lg_sites = 4;  // a default that splits
     for (int sites : {4, 6, 8, 10}) {
         TcConfig c = best;
@@ -528,17 +531,20 @@ plm_status autotune_tc(plm_ctx *ctx, Problem &P, int *tc_err)
         }
     }
     tbest = 1e30f;
-    for (int cols : {128, 160, 192, 224, 256}) {
-        TcConfig c = best;
-        c.gr_ncols = cols;
-        float t;
-        plm_status s = time_it(c, 2, &t);
-        if (s) return s;
-        if (t < tbest) {
-            tbest = t;
-            best.gr_ncols = cols;
+    for (int rows : {128, 256})
+        for (int cols : {128, 160, 192, 224, 256}) {
+            TcConfig c = best;
+            c.gr_rows = rows;
+            c.gr_ncols = cols;
+            float t;
+            plm_status s = time_it(c, 2, &t);
+            if (s) return s;
+            if (t < tbest) {
+                tbest = t;
+                best.gr_rows = rows;
+                best.gr_ncols = cols;
+            }
         }
-    }
     ctx->event_pool.push_back(e0);
     ctx->event_pool.push_back(e1);
     P.tc_cfg = best;
@@ -613,10 +619,10 @@ plm_status evaluate(plm_ctx *ctx, plm_precision prec, Problem &P, const float *w
             f0 += b.nfam;
         }
         if (!P.tc_tuned) {
-            // PLMDCA_TC_TILES="sites,cols" forces a tile shape (tests, experiments)
+            // PLMDCA_TC_TILES="sites,cols[,rows]" forces a tile shape (tests, experiments)
             const char *force = getenv("PLMDCA_TC_TILES");
             TcConfig fc;
-            if (force && sscanf(force, "%d,%d", &fc.lg_sites, &fc.gr_ncols) == 2 &&
+            if (force && sscanf(force, "%d,%d,%d", &fc.lg_sites, &fc.gr_ncols, &fc.gr_rows) >= 2 &&
                 tc_config_valid(fc)) {
                 P.tc_cfg = fc;
                 P.tc_tuned = true;
@@ -761,7 +767,7 @@ plm_status solve_core(plm_ctx *ctx, Problem &P, const plm_opts &o, std::vector<S
     // lanes 0.032 s.  Every other case runs one lane.
     struct Lane {
         LbLayout L;
-        int *cnt;          // 16 ints: [0] searching, [1] ready, [2] continuing, [4] tc error, [8] round
+        int *cnt;          // 16 ints: [0] searching, [1] ready, [2] continuing, [4] tc error, [8] round, [9] rounds
         uint8_t *active;   // evaluation flags (nsites; only this lane's sites set)
         int *hc;           // pinned host copy of cnt[0..4]
         cudaStream_t st;
@@ -775,7 +781,7 @@ plm_status solve_core(plm_ctx *ctx, Problem &P, const plm_opts &o, std::vector<S
     if (pipelined && P.tc_tuned) {
         std::vector<int> b{0};
         if (nf == 1) {
-            b = lane_bounds(P.fam[0].d.N, P.tc_cfg.lg_sites, K);
+            b = lane_bounds(P.fam[0].d.N, P.tc_cfg, K);
             b.pop_back();
         } else {
             // whole families per lane (no tile straddles a family), boundaries

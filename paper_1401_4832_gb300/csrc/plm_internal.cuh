@@ -291,11 +291,13 @@ int tc_padded_B(int B);
 // (launches the transposes); scratch[f] points at tc_family_scratch_bytes
 cudaError_t launch_tc_prepare(TcBatch &b, void *const *scratch, cudaStream_t st);
 // tile shapes: logits tiles of `lg_sites` sites (24 columns each, even,
-// 2..10) x 128 sequences; gradient tiles of 128 rows x `gr_ncols` columns
-// (multiple of 32, <= 256)
+// 2..10) x 128 sequences; gradient tiles of `gr_rows` rows (128, or 256 as
+// two 128-row accumulators sharing each one-hot operand stage) x `gr_ncols`
+// columns (multiple of 32, <= 256)
 struct TcConfig {
     int lg_sites = 8;
     int gr_ncols = 256;
+    int gr_rows = 128;
 };
 bool tc_config_valid(const TcConfig &c);
 // one evaluation of every family of the batch at its split theta (th_hi/lo):

@@ -140,15 +140,18 @@ def test_tc_solve_tiny_identical_contacts(ctx):
     assert np.array_equal(top_g.cpu().numpy()[:len(top_o)], top_o)
 
 
-TILE_SHAPES = [(s, 256) for s in (2, 4, 6, 10)] + [(8, c) for c in (32, 128, 160, 192, 224)]
+TILE_SHAPES = ([(s, 256, 128) for s in (2, 4, 6, 10)] + [(8, c, 128) for c in (32, 128, 160, 192, 224)]
+               + [(8, c, 256) for c in (32, 128, 224, 256)])
 
 
-@pytest.mark.parametrize("sites,cols", TILE_SHAPES)
-def test_tc_every_tile_shape(sites, cols, monkeypatch):
+@pytest.mark.parametrize("sites,cols,rows", TILE_SHAPES)
+def test_tc_every_tile_shape(sites, cols, rows, monkeypatch):
     # every shape the autotuner may pick gives the same numbers (ragged in
-    # both GEMM dimensions: N=37 -> 37 % sites != 0, K = 800 -> K % cols != 0)
+    # both GEMM dimensions: N=37 -> 37 % sites != 0, K = 800 -> K % cols != 0,
+    # R = 37 * 24 = 888 rows -> the last 256-row tile holds 120 real rows, so
+    # its second 128-row half is all padding)
     from paper_1401_4832_gb300 import api
-    monkeypatch.setenv("PLMDCA_TC_TILES", f"{sites},{cols}")
+    monkeypatch.setenv("PLMDCA_TC_TILES", f"{sites},{cols},{rows}")
     S = synth.add_clusters(synth.small_random(37, 203, 4), 0.3, 4, max_redraw=0.1)
     h, J = _theta(37, 4, 0.2)
     with api.Context(0) as c:
