@@ -677,6 +677,21 @@ def kernel_rooflines(kern, tc_full, B, N, pk, pk_kind):
                          "frac": ach / hbm, "traffic": None,
                          "bytes_per_launch": by / cnt,
                          "peak_note": f"HBM copy bandwidth, {pk_kind}"}
+    if "reweight" in kern:
+        # pair tests of the bit-plane kernel: 64 x 64 tiles of the upper
+        # triangle, ceil(N/32) words each, 7 integer instructions per word
+        # (5 three-input logic ops folding XOR/OR over the planes, POPC, add)
+        cnt, ms, _ = kern["reweight"]
+        tiles = -(-B // 64)
+        ops = tiles * (tiles + 1) // 2 * 64 * 64 * (-(-N // 32)) * 7
+        sm_mhz = pk.get("sm_max_mhz", 2070.0)
+        peak = 152 * 128 * sm_mhz * 1e6 / 1e12
+        ach = ops / (ms / 1000.0 / cnt) / 1e12
+        out["reweight"] = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Tintop/s",
+                           "frac": ach / peak, "traffic": None, "ops_per_launch": ops,
+                           "peak_note": f"152 SMs x 128 lanes x {sm_mhz:.0f} MHz, one 32-bit "
+                                        "integer op per lane per clock (derived); time of the "
+                                        "whole reweighting (packing, pair counts, weights, B_eff)"}
     for name, avg_s in tc_full.items():
         if name in ("tc_logits", "tc_grad"):
             # the one-hot contraction as a dense GEMM (unpadded): B x Nq x (Nq + 1)
@@ -700,6 +715,16 @@ def kernel_rooflines(kern, tc_full, B, N, pk, pk_kind):
                          "frac": ach / peak, "traffic": None,
                          "launch_us_full_eval": avg_s * 1e6,
                          "peak_note": f"152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (derived)"}
+        if name in out and name in ("tc_logits", "tc_grad", "logits_gather", "grad_gather"):
+            # the method's own work, whatever the formulation: B N (N-1) q adds
+            # (one gathered coupling per sequence, site, state and other site)
+            # and one pass over the couplings or the gradient (FP32) plus the
+            # MSA; the time that work needs at the FP32-add or HBM peak over
+            # the measured time
+            add_peak = 152 * 128 * pk.get("sm_max_mhz", 2070.0) * 1e6
+            t_alg = max(B * N * (N - 1) * q / add_peak,
+                        (N * q * (N * q + 1) * 4 + B * N) / (hbm * 1e9))
+            out[name]["algorithmic_frac"] = t_alg / avg_s
     return out
 
 
