@@ -22,17 +22,19 @@ def test_graph_replay_equals_eager(prec):
     assert r1["n_converged"] == S.shape[1]
 
 
+@pytest.mark.parametrize("tiles", ["8,224", "8,224,256"])
 @pytest.mark.parametrize("which", ["family", "ragged"])
-def test_two_lane_pipeline_equals_one_lane(which, monkeypatch):
+def test_two_lane_pipeline_equals_one_lane(which, tiles, monkeypatch):
     # With graphs on, a one-family tensor-core solve runs in two lanes (two
     # streams, device-side loops, one lane rotated by half a round) when the
-    # sites split at a boundary shared by the site groups and the 128-row
-    # gradient tiles; 8-site groups make that boundary a multiple of 16
-    # sites (N = 120: 64 + 56; N = 70: 32 + 38).  Each site's iterates
-    # depend only on its own row block, so the result must equal the
-    # one-lane eager solve bit for bit.
+    # sites split at a boundary shared by the site groups and the gradient
+    # row tiles; with 8-site groups that boundary is a multiple of 16 sites
+    # for 128-row tiles and of 32 sites for 256-row tiles (N = 120: 64 + 56
+    # both ways; N = 70: 32 + 38 both ways).  Each site's iterates depend
+    # only on its own row block, so the result must equal the one-lane
+    # eager solve bit for bit.
     from paper_1401_4832_gb300 import api
-    monkeypatch.setenv("PLMDCA_TC_TILES", "8,224")
+    monkeypatch.setenv("PLMDCA_TC_TILES", tiles)
     if which == "family":
         S = synth.protein_family().msa
     else:  # N = 70: lanes of 32 and 38 sites, ragged tiles in both GEMM dimensions
