@@ -321,6 +321,14 @@ plm_status msa_reweight_static(const int8_t *msa, int B, int N, int q, double x,
  * kernels not counted); it synchronises the stream and returns the number
  * of bytes needed. */
 long long plm_kernel_launches(void);
+/* plm_selftest_wait: a diagnostic, not part of the method.  Runs, on the
+ * context's stream, the bounded wait that every tensor-core pipeline stage
+ * uses, on a barrier nothing arrives on: after its budget (~2 s at the
+ * maximum SM clock) the wait gives up, the kernel records a timeout code in
+ * an error word and returns normally.  Returns PLM_ETIMEOUT with the code
+ * in *code_out (may be NULL) when that happened — the expected outcome —
+ * and the context stays usable; PLM_ECUDA if no timeout was reported. */
+plm_status plm_selftest_wait(plm_ctx *ctx, int *code_out);
 plm_status plm_profile(plm_ctx *ctx, int enable);
 int plm_profile_report(plm_ctx *ctx, char *buf, int len);
 

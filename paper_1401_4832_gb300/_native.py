@@ -127,6 +127,8 @@ def load():
         lib.msa_parse.restype = I
         lib.msa_frequencies.argtypes = [P, P, P, D, I, I, I, P]
         lib.msa_frequencies.restype = I
+        lib.plm_selftest_wait.argtypes = [P, ctypes.POINTER(I)]
+        lib.plm_selftest_wait.restype = I
         lib.plm_kernel_launches.argtypes = []
         lib.plm_kernel_launches.restype = ctypes.c_longlong
         lib.plm_profile.argtypes = [P, I]

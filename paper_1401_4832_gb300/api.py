@@ -322,3 +322,13 @@ def plmdca(ctx: Context, msa, L: int | None = None, min_sep: int = 5, out=None,
     d = rep.as_dict()
     d["status"] = N_.STATUS_NAMES.get(st, st)
     return dict(h=out["h"], J=out["J"], report=d, fn=out["fn"], cfn=out["cfn"], top=out["top"])
+
+
+def selftest_wait(ctx: Context):
+    """Run the tensor-core pipelines' bounded wait on a barrier nothing
+    arrives on (``plm_selftest_wait``, a diagnostic).  Returns (status name,
+    timeout code); the expected outcome is ("PLM_ETIMEOUT", non-zero code)
+    after about two seconds, with the context still usable."""
+    code = ctypes.c_int(0)
+    st = ctx.lib.plm_selftest_wait(ctx.handle, ctypes.byref(code))
+    return N_.STATUS_NAMES.get(st, st), code.value

@@ -52,7 +52,7 @@ constexpr int SMEM_BUDGET = 224 * 1024;  // pipeline bytes; + 1 KB alignment sla
 constexpr long long WAIT_CYCLES = 4000000000LL;        // ~2 s at 2 GHz
 
 enum { ERR_TIMEOUT_TMA = 1 << 4, ERR_TIMEOUT_MMA = 1 << 5, ERR_TIMEOUT_PROD = 1 << 6,
-       ERR_TIMEOUT_EPI = 1 << 7 };
+       ERR_TIMEOUT_EPI = 1 << 7, ERR_TIMEOUT_SELFTEST = 1 << 8 };
 
 // ---------------------------------------------------------------- PTX glue
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -852,6 +852,25 @@ k_tc_grad(const __grid_constant__ GradParams P, float two_lh, float two_lj, int 
     }
 }
 
+// ---------------------------------------------------------------- self-test
+// The bounded wait of the pipelines above on a barrier that nothing
+// arrives on: it gives up after its cycle budget, raises the CTA's abort
+// flag and records ERR_TIMEOUT_SELFTEST in the error word, and the kernel
+// returns normally (no fault, the context stays usable).
+__global__ void k_wait_selftest(int *__restrict__ err)
+{
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int abort_sh;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        abort_sh = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_wait(&bar, 0, &abort_sh, err, ERR_TIMEOUT_SELFTEST);
+    __syncthreads();
+}
+
 // ---------------------------------------------------------------- helpers
 __global__ void k_split(const float *__restrict__ theta, size_t n,
                         __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo)
@@ -926,6 +945,13 @@ size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 }  // namespace
 
 int tc_padded_B(int B) { return (B + TC_M - 1) / TC_M * TC_M; }
+
+cudaError_t launch_wait_selftest(int *err, cudaStream_t st)
+{
+    k_wait_selftest<<<1, 32, 0, st>>>(err);
+    count_launches(1);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_split_theta(const float *theta, size_t n, __nv_bfloat16 *hi,
                                __nv_bfloat16 *lo, cudaStream_t st)

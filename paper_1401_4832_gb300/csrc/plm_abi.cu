@@ -1188,6 +1188,26 @@ plm_status plm_destroy(plm_ctx *c)
 
 long long plm_kernel_launches(void) { return plm::g_launches.load(); }
 
+plm_status plm_selftest_wait(plm_ctx *ctx, int *code_out)
+{
+    using namespace plm;
+    if (!ctx) return PLM_EINVAL;
+    if (code_out) *code_out = 0;
+    cudaSetDevice(ctx->device);
+    void *flag;
+    CK(ws(ctx, "flag_selftest", sizeof(int), &flag));
+    CK(cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream));
+    CK(launch_wait_selftest((int *)flag, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->host_counters + 11, flag, sizeof(int), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    const int code = ctx->host_counters[11];
+    if (code_out) *code_out = code;
+    if (code)
+        return fail(ctx, PLM_ETIMEOUT, "device wait gave up as designed (code 0x%x)", code);
+    return fail(ctx, PLM_ECUDA, "the bounded wait did not report its timeout");
+}
+
 plm_status plm_profile(plm_ctx *c, int enable)
 {
     if (!c) return PLM_EINVAL;

@@ -300,6 +300,9 @@ struct TcConfig {
     int gr_rows = 128;
 };
 bool tc_config_valid(const TcConfig &c);
+// one bounded pipeline wait on a barrier nothing arrives on: ORs a timeout
+// code into *err after the wait budget (~2 s) and returns normally
+cudaError_t launch_wait_selftest(int *err, cudaStream_t st);
 // one evaluation of every family of the batch at its split theta (th_hi/lo):
 // f_data (data term) and G (with 2 lambda theta) per family.  which: 1 =
 // logits + objective only, 2 = gradient only, 3 = both.
