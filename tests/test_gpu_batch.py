@@ -24,6 +24,18 @@ def ctx():
     c.close()
 
 
+@pytest.fixture(scope="module")
+def ctx_stream():
+    # on a non-default stream the split-BF16 solves run as bench.py times
+    # them: CUDA graphs with device-side round loops, two lanes (the batch
+    # split at a family boundary, a single family at a tile boundary)
+    from paper_1401_4832_gb300 import api
+    stream = torch.cuda.Stream()
+    c = api.Context(0, stream)
+    yield c
+    c.close()
+
+
 def _families():
     # uneven sizes: several tile counts, ragged tails, one very small family
     shapes = [(23, 310, 0), (8, 40, 1), (61, 777, 2), (37, 129, 3), (120, 1000, 4)]
@@ -35,14 +47,18 @@ def _families():
     return fams
 
 
-@pytest.mark.parametrize("prec", ["split_bf16", "fp32"])
-def test_batch_equals_separate_solves(ctx, prec):
+@pytest.mark.parametrize("prec,where", [("split_bf16", "default"), ("fp32", "default"),
+                                        ("split_bf16", "stream")])
+def test_batch_equals_separate_solves(ctx, ctx_stream, prec, where):
     from paper_1401_4832_gb300 import api
+    c = ctx if where == "default" else ctx_stream
     msas = _families()
-    dev = [torch.from_numpy(m).cuda() for m in msas]
-    batch = api.plm_solve_batch(ctx, dev, gtol=1e-4, prec=prec)
-    for m, (h_b, J_b, rep_b) in zip(dev, batch):
-        h_s, J_s, rep_s = api.plm_solve(ctx, m, gtol=1e-4, prec=prec)
+    with torch.cuda.stream(c.stream):
+        dev = [torch.from_numpy(m).cuda() for m in msas]
+        batch = api.plm_solve_batch(c, dev, gtol=1e-4, prec=prec)
+        sep = [api.plm_solve(c, m, gtol=1e-4, prec=prec) for m in dev]
+        c.stream.synchronize()
+    for m, (h_b, J_b, rep_b), (h_s, J_s, rep_s) in zip(dev, batch, sep):
         assert rep_b["n_converged"] == m.shape[1], rep_b
         assert torch.equal(h_b, h_s) and torch.equal(J_b, J_s)
         assert rep_b["iters"] == rep_s["iters"]

@@ -1,5 +1,7 @@
 """Full-size parity at the benchmark's workload (N=120, B=5000, q=21) and in
-the benchmark's launch configuration (plm_solve + fn_apc_scores, gtol 1e-4).
+the benchmark's launch configuration (plm_solve + fn_apc_scores, gtol 1e-4,
+on a dedicated stream, so the split-BF16 solve runs as bench.py times it:
+two pipelined lanes, device-side round loops, autotuned tile shapes).
 
 The oracle solves every site problem to ||grad|| <= 1e-6 on the host cores
 (the site problems are independent, so OpenMP over sites).  Bars:
@@ -40,8 +42,11 @@ def ref(fam):
 
 @pytest.fixture(scope="module")
 def ctx():
+    # a non-default stream, as bench.py uses: CUDA graphs (and with them the
+    # lanes and the device-side loops) need a capturable stream
     from paper_1401_4832_gb300 import api
-    c = api.Context(0)
+    stream = torch.cuda.Stream()
+    c = api.Context(0, stream)
     yield c
     c.close()
 
@@ -65,9 +70,11 @@ def test_family_solve_matches_oracle(ctx, fam, ref, prec):
     from paper_1401_4832_gb300 import api
     S = fam.msa
     N = fam.N
-    h_g, J_g, rep = api.plm_solve(ctx, torch.from_numpy(S).cuda(), gtol=1e-4, prec=prec)
+    with torch.cuda.stream(ctx.stream):
+        h_g, J_g, rep = api.plm_solve(ctx, torch.from_numpy(S).cuda(), gtol=1e-4, prec=prec)
+        fn_g, cfn_g, top_g = api.fn_apc_scores(ctx, J_g)
+        ctx.stream.synchronize()
     assert rep["n_converged"] == N, rep
-    fn_g, cfn_g, top_g = api.fn_apc_scores(ctx, J_g)
     h_g = h_g.cpu().numpy().astype(np.float64)
     J_g = J_g.cpu().numpy().astype(np.float64)
     m, w, w32, beff = oracle.reweight(S, 0.8)
