@@ -34,7 +34,7 @@ MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="auto", choices=["auto", "fp32", "split_bf16"])
@@ -65,8 +65,12 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clock/throttle samples every 200 ms during the timed region."""
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi clock/throttle samples every 50 ms.  Started before the
+    warm-up (the tool needs ~0.1 s to begin); `window` marks the timed region
+    on the host clock, and only the samples nvidia-smi stamped inside it are
+    kept (or, for a region shorter than the sampling period, the sample
+    nearest to it)."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -74,12 +78,16 @@ class ClockSampler:
         self.index = index
         self.proc = None
         self.lines = []
+        self.t0 = self.t1 = None
+
+    def window(self, t0, t1):
+        self.t0, self.t1 = t0, t1
 
     def start(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -98,23 +106,35 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
-            except ValueError:
-                continue
-            for n, v in zip(names, parts[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(n)
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        return summarize_clocks(self.lines, self.t0, self.t1)
+
+
+def summarize_clocks(lines, t0=None, t1=None):
+    """Median SM clock, its maximum and the throttle reasons seen, over the
+    nvidia-smi samples stamped within [t0, t1] (host wall-clock seconds);
+    with none inside, the one nearest to the window."""
+    import datetime
+    rows = []
+    for ln in lines:
+        parts = [p.strip() for p in ln.split(",")]
+        if len(parts) < 10:
+            continue
+        try:
+            ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            rows.append((ts, float(parts[2]), float(parts[3]), parts[6:10]))
+        except ValueError:
+            continue
+    if t0 is not None and rows:
+        inside = [r for r in rows if t0 <= r[0] <= t1]
+        if not inside:
+            inside = [min(rows, key=lambda r: min(abs(r[0] - t0), abs(r[0] - t1)))]
+        rows = inside
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = {n for r in rows for n, v in zip(names, r[3]) if v.lower().startswith("active")}
+    sm = [r[1] for r in rows]
+    return {"sm_mhz": statistics.median(sm) if sm else None,
+            "sm_max_mhz": max(r[2] for r in rows) if rows else None,
+            "reasons": sorted(reasons), "samples": len(sm)}
 
 
 def cpu_sample(fam, n_sites, gtol):
@@ -439,6 +459,8 @@ def main():
         fn, cfn, top = api.fn_apc_scores(ctx, J)
         return rep, top
 
+    sampler = ClockSampler(device)
+    sampler.start()
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             step()
@@ -447,10 +469,9 @@ def main():
             dist.barrier()
         lib = _native.load()
         launches0 = lib.plm_kernel_launches()
-        sampler = ClockSampler(device)
-        sampler.start()
         times, reps = [], []
         t_wall0 = time.perf_counter()
+        t_epoch0 = time.time()
         for _ in range(args.steps):
             flush.zero_()
             torch.cuda.synchronize(device)
@@ -463,6 +484,7 @@ def main():
             times.append(e0.elapsed_time(e1) / 1000.0)
             reps.append(rep)
         t_wall = time.perf_counter() - t_wall0
+        sampler.window(t_epoch0, time.time())
         clocks = sampler.stop()
         launches = lib.plm_kernel_launches() - launches0
     if dist:

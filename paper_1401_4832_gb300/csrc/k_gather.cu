@@ -276,13 +276,9 @@ cudaError_t launch_logits_gather(const int8_t *msa, const float *theta,
                                  const Dims &d, float *L, const uint8_t *active,
                                  cudaStream_t st)
 {
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(
-            k_logits_gather, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LG_SMEM);
-        if (e) return e;
-        attr_set = true;
-    }
+    static std::atomic<unsigned long long> attr{0};
+    cudaError_t e = set_smem_limit_once((const void *)k_logits_gather, (int)LG_SMEM, attr);
+    if (e) return e;
     dim3 grid((d.R + LG_ROWS - 1) / LG_ROWS, (d.B + LG_BT - 1) / LG_BT);
     k_logits_gather<<<grid, 256, LG_SMEM, st>>>(msa, theta, d, L, active);
     count_launches(1);

@@ -388,13 +388,10 @@ cudaError_t launch_topL(const double *score, int N, int L, int min_sep, int32_t 
 {
     if (L <= 0) return cudaSuccess;
     if (L > TOPL_MAX || (long long)N * N >= 0xFFFFFFFFll) return cudaErrorInvalidValue;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_sel_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             TOPL_MAX * (int)sizeof(Cand));
-        if (e) return e;
-        attr = true;
-    }
+    static std::atomic<unsigned long long> attr{0};
+    cudaError_t e = set_smem_limit_once((const void *)k_sel_sort, TOPL_MAX * (int)sizeof(Cand),
+                                        attr);
+    if (e) return e;
     SelState *ss = (SelState *)scratch;
     Cand *cand = (Cand *)((char *)scratch + ((sizeof(SelState) + 255) / 256) * 256);
     k_sel_init<<<1, 256, 0, st>>>(ss, score, N, L, min_sep);

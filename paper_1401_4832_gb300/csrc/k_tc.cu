@@ -912,15 +912,17 @@ __global__ void k_tc_finish(const __grid_constant__ TcBatch b)
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (!fn) {
+    // looked up once per process (a function-local static is initialised
+    // exactly once, whichever thread gets here first)
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
         void *p = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
                                              cudaEnableDefault, &q) == cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
-            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-    }
+            return (PFN_cuTensorMapEncodeTiled_v12000)p;
+        return (PFN_cuTensorMapEncodeTiled_v12000) nullptr;
+    }();
     return fn;
 }
 
@@ -1012,12 +1014,15 @@ int tc_stages(int stage_bytes, int slab_bytes)
 
 int num_sms()
 {
-    static int n = 0;
+    static std::atomic<int> cache[64];  // per device; 0 = not queried yet
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::atomic<int> &c = cache[dev & 63];
+    int n = c.load();
     if (!n) {
-        int dev = 0;
-        cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
         if (n <= 0) n = 1;
+        c.store(n);
     }
     return n;
 }
@@ -1032,21 +1037,18 @@ bool tc_config_valid(const TcConfig &c)
 cudaError_t launch_tc_eval(void *prof, const TcBatch &b_in, const TcConfig &cfg, double lambda_h,
                            double lambda_Jp, int *err, cudaStream_t st, int which)
 {
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_tc_logits,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             SMEM_BUDGET + 1024);
-        if (e) return e;
-        e = cudaFuncSetAttribute(k_tc_grad, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 SMEM_BUDGET + 1024);
-        if (e) return e;
-        attr = true;
-    }
+    static std::atomic<unsigned long long> attr_lg{0}, attr_gr{0};
+    cudaError_t e = set_smem_limit_once((const void *)k_tc_logits, SMEM_BUDGET + 1024, attr_lg);
+    if (e) return e;
+    e = set_smem_limit_once((const void *)k_tc_grad, SMEM_BUDGET + 1024, attr_gr);
+    if (e) return e;
     if (b_in.nfam < 1 || b_in.nfam > MAX_FAM || !tc_config_valid(cfg))
         return cudaErrorInvalidValue;
-    static LogitsParams lp;  // large parameter blocks: built on the host, passed by value
-    static GradParams gp;
+    // large parameter blocks, built on the host and passed by value (a launch
+    // copies them), one pair per host thread so that contexts driven from
+    // different threads do not share them
+    thread_local LogitsParams lp;
+    thread_local GradParams gp;
     lp.b = b_in;
     const int lg_ncols = cfg.lg_sites * QP;
     int tl = 0, tg = 0;

@@ -23,7 +23,25 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <atomic>
+
 namespace plm {
+
+// Raises a kernel's dynamic shared-memory limit on the current device the
+// first time a launcher runs there (the attribute is per device; `done`
+// holds one bit per device, set once the call succeeded).
+inline cudaError_t set_smem_limit_once(const void *kernel, int bytes,
+                                       std::atomic<unsigned long long> &done)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e) return e;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (done.load() & bit) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) done.fetch_or(bit);
+    return e;
+}
 
 // running count of kernel launches issued by the library (diagnostics)
 void count_launches(int n);

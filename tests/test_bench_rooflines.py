@@ -40,3 +40,22 @@ def test_reweight_integer_ops():
     assert r["bound"] == "alu" and r["ops_per_launch"] == ops
     assert math.isclose(r["achieved"], ops / 0.1e-3 / 1e12)
     assert math.isclose(r["peak"], 152 * 128 * 2070e6 / 1e12)
+
+
+def test_clock_summary_keeps_the_timed_window():
+    import datetime
+    base = datetime.datetime(2026, 1, 2, 3, 4, 5)
+
+    def line(dt_s, mhz, slow="Not Active", cap="Not Active"):
+        ts = (base + datetime.timedelta(seconds=dt_s)).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
+        return f"{ts}, 0, {mhz}, 2070, 900.0, 0x0, {slow}, Not Active, Not Active, {cap}"
+
+    t0 = base.timestamp() + 1.0
+    lines = [line(0.5, 1200, slow="Active"), line(1.05, 2070), line(1.10, 2040, cap="Active"),
+             line(1.15, 2070), line(2.5, 1000)]
+    c = bench.summarize_clocks(lines, t0, t0 + 0.2)
+    assert c["samples"] == 3 and c["sm_mhz"] == 2070 and c["sm_max_mhz"] == 2070
+    assert c["reasons"] == ["sw_power_cap"]  # the slowdown before the window is not counted
+    # a window shorter than the sampling period keeps the nearest sample
+    c = bench.summarize_clocks(lines, t0 + 0.085, t0 + 0.095)
+    assert c["samples"] == 1 and c["sm_mhz"] == 2040
