@@ -104,6 +104,32 @@ __device__ __forceinline__ double lane_chunk_sum(const double *part, const SiteI
     return t;
 }
 
+// Above this many chunks (a site of a very large problem, or the single
+// problem of the symmetric solve with all parameters) a thread per slot
+// walking every chunk record is bound by load latency; such a site's slots
+// are summed by the whole warp instead (warp_chunk_sums).  Sites at or below
+// it keep the per-thread chunk order.
+constexpr int LB_WARP_SUM_MIN = 64;
+
+// totals of the K slots slot[0..K) of one site: the lanes take alternate
+// chunks and accumulate every slot of each chunk record they read (all loads
+// independent), then a fixed-order butterfly; every lane gets the totals
+template <int K>
+__device__ __forceinline__ void warp_chunk_sums(const double *part, const SiteInfo &si,
+                                                const int (&slot)[K], double (&t)[K])
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < K; ++k) t[k] = 0.0;
+    for (int c = lane; c < si.nchunks; c += 32) {
+        const double *q = part + (size_t)(si.chunk0 + c) * LB_PART;
+#pragma unroll
+        for (int k = 0; k < K; ++k) t[k] += q[slot[k]];
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) t[k] = warp_sum_d(t[k]);
+}
+
 struct Chunk {
     size_t base4, e0, e1;
     int site;
@@ -230,7 +256,17 @@ __global__ void k_dir_solve(SiteState *ss, const double *part, const SiteInfo *s
     const int lane = threadIdx.x;
     if (hist > 0) {
         // slots 0..2M-1: S'y_n, Y'y_n; then s_n'g_new and y_n'g_old
-        if (lane < 2 * M + 2) {
+        if (si[r].nchunks > LB_WARP_SUM_MIN) {
+            int slot[2 * M + 2];
+            double t[2 * M + 2];
+#pragma unroll
+            for (int k = 0; k < 2 * M + 2; ++k)
+                slot[k] = k < 2 * M ? k : (k == 2 * M ? LB_SLOT_SG : LB_SLOT_YG);
+            warp_chunk_sums(part, si[r], slot, t);
+            if (lane == 0)
+#pragma unroll
+                for (int k = 0; k < 2 * M + 2; ++k) tot[k] = t[k];
+        } else if (lane < 2 * M + 2) {
             const int k = lane < 2 * M ? lane : (lane == 2 * M ? LB_SLOT_SG : LB_SLOT_YG);
             tot[lane] = lane_chunk_sum(part, si[r], k);
         }
@@ -499,7 +535,16 @@ __global__ void k_ls_decide(SiteState *ss, const double *__restrict__ f_data, co
     SiteState &s = ss[r];
     if (s.status != SITE_SEARCHING) return;
     __shared__ double t4[4];
-    if (threadIdx.x < 4) t4[threadIdx.x] = lane_chunk_sum(part, si[r], threadIdx.x);
+    if (si[r].nchunks > LB_WARP_SUM_MIN) {
+        const int slot[4] = {0, 1, 2, 3};
+        double t[4];
+        warp_chunk_sums(part, si[r], slot, t);
+        if (threadIdx.x == 0)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) t4[k] = t[k];
+    } else if (threadIdx.x < 4) {
+        t4[threadIdx.x] = lane_chunk_sum(part, si[r], threadIdx.x);
+    }
     __syncwarp();
     if (threadIdx.x != 0) return;
     const double pj = t4[0], ph = t4[1], dgt = t4[2], gn2 = t4[3];
