@@ -35,10 +35,21 @@ def scale():
 
 @pytest.fixture(scope="module")
 def ctx():
+    # a non-default stream, as bench.py uses: the split-BF16 solves then run
+    # in two lanes with device-side round loops (N = 500: lanes of 256 and
+    # 244 sites)
     from paper_1401_4832_gb300 import api
-    c = api.Context(0)
+    stream = torch.cuda.Stream()
+    c = api.Context(0, stream)
     yield c
     c.close()
+
+
+@pytest.fixture(autouse=True)
+def _on_ctx_stream(ctx):
+    with torch.cuda.stream(ctx.stream):
+        yield
+    ctx.stream.synchronize()
 
 
 @pytest.mark.parametrize("prec,rf,rg", [("split_bf16", 1e-4, 2e-3), ("fp32", 1e-6, 1e-5)])
