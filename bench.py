@@ -462,10 +462,16 @@ def main():
     torch.cuda.set_device(device)
     pk, pk_kind = peaks()
 
-    # one replica per rank (weak scaling): its own family
-    fam = synth.protein_family(seed=replica_seed(rank))
+    # one replica per rank (weak scaling): rank 0 generates the family (and
+    # caches it on disk), the other ranks load it after the barrier and take
+    # their own order of its sequences
+    if dist and rank != 0:
+        dist.barrier()
+    fam = synth.protein_family()
+    if dist and rank == 0:
+        dist.barrier()
     B, N = fam.B, fam.N
-    msa = torch.from_numpy(fam.msa).to(f"cuda:{device}")
+    msa = torch.from_numpy(replica_msa(fam.msa, rank)).to(f"cuda:{device}")
     stream = torch.cuda.Stream(device)
     ctx = api.Context(device, stream)
     prec = args.prec
@@ -653,10 +659,16 @@ def ncu_traffic(kernel):
     return ent[2] if h == ent[1] else None
 
 
-def replica_seed(rank):
-    """Multi-GPU runs are replicas (the path needs no exchange, each rank
-    solves its own family): the family of rank r is drawn with seed r."""
-    return int(rank)
+def replica_msa(msa, rank):
+    """Multi-GPU runs are replicas (the path needs no exchange): rank r
+    solves the family with its sequences in an order drawn with seed r
+    (rank 0: as generated) -- its own copy of the data, the same problem and
+    the same work on every rank, from one family that rank 0 generates."""
+    import numpy as np
+    if rank == 0:
+        return msa
+    perm = np.random.default_rng(int(rank)).permutation(msa.shape[0])
+    return np.ascontiguousarray(msa[perm])
 
 
 def job_seconds_per_solve(local_total_s, steps, world, dist=None, device="cpu"):

@@ -1,6 +1,7 @@
 """The multi-GPU path is replicas (the solve needs no exchange): each rank
-solves its own family, and the bench reports the slowest rank's time over
-all the solves of the job.  Checked here with two gloo ranks on the CPU."""
+solves its own copy of the family (its own order of the sequences), and the
+bench reports the slowest rank's time over all the solves of the job.
+Checked here with two gloo ranks on the CPU."""
 import os
 import socket
 import sys
@@ -26,7 +27,9 @@ def _rank(rank, world, port, q):
     try:
         local = [1.0, 3.0][rank]  # rank 1 is the slow one
         v = bench.job_seconds_per_solve(local, steps=4, world=world, dist=dist)
-        q.put((rank, v, bench.replica_seed(rank)))
+        import numpy as np
+        msa = np.arange(40, dtype=np.int8).reshape(10, 4) % 21
+        q.put((rank, v, bench.replica_msa(msa, rank).tobytes()))
         dist.barrier()
     finally:
         dist.destroy_process_group()
@@ -45,8 +48,14 @@ def test_two_rank_aggregation_and_replicas():
     got = dict((r, (v, s)) for r, v, s in (q.get(timeout=5) for _ in range(2)))
     # max over ranks (3.0 s) over 4 steps x 2 ranks
     assert got[0][0] == pytest.approx(3.0 / 8) and got[1][0] == pytest.approx(3.0 / 8)
-    # each rank its own family
-    assert got[0][1] != got[1][1]
+    # each rank its own copy: rank 0 the data as generated, rank 1 the same
+    # rows in another order
+    import numpy as np
+    msa = np.arange(40, dtype=np.int8).reshape(10, 4) % 21
+    r0 = np.frombuffer(got[0][1], np.int8).reshape(10, 4)
+    r1 = np.frombuffer(got[1][1], np.int8).reshape(10, 4)
+    assert np.array_equal(r0, msa) and not np.array_equal(r1, msa)
+    assert sorted(map(bytes, r1)) == sorted(map(bytes, msa))
 
 
 def test_single_rank_value():
