@@ -117,13 +117,17 @@ __global__ void k_apc_rows(const double *__restrict__ fn, int N,
     row[i] = s;  // the raw sum; divided below
 }
 
+// one warp: the grand total of the raw row sums (lanes take alternate rows,
+// then a fixed-order butterfly), the row means and the total mean
 __global__ void k_apc_total(double *__restrict__ row, int N)
 {
-    if (threadIdx.x != 0) return;
+    const int lane = threadIdx.x & 31;
     double tot = 0.0;
-    for (int i = 0; i < N; ++i) tot += row[i];
-    for (int i = 0; i < N; ++i) row[i] /= (N - 1);
-    row[N] = tot / ((double)N * (N - 1));
+    for (int i = lane; i < N; i += 32) tot += row[i];
+    tot = warp_sum_d(tot);
+    __syncwarp();
+    for (int i = lane; i < N; i += 32) row[i] /= (N - 1);
+    if (lane == 0) row[N] = tot / ((double)N * (N - 1));
 }
 
 // correction 0: APC (Eq. corr_norm2); 1: average sum correction (Eq.
@@ -183,6 +187,7 @@ struct SelState {
     unsigned int k;             // rank still to find inside the current prefix
     unsigned int count;         // gathered candidates
     unsigned int eligible;
+    unsigned int done;          // the prefix already selects exactly the top k
     unsigned int hist[256];
 };
 
@@ -236,6 +241,7 @@ __global__ void k_sel_init(SelState *st, const double *score, int N, int L, int 
         st->pre_hi = 0;
         st->pre_lo = 0;
         st->count = 0;
+        st->done = 0;
     }
     for (int b = threadIdx.x; b < 256; b += blockDim.x) st->hist[b] = 0;
 }
@@ -243,6 +249,7 @@ __global__ void k_sel_init(SelState *st, const double *score, int N, int L, int 
 __global__ void k_sel_hist(SelState *st, const double *__restrict__ score, int N, int min_sep,
                            int t)
 {
+    if (st->done) return;  // the remaining passes have nothing to decide
     __shared__ unsigned int h[256];
     for (int b = threadIdx.x; b < 256; b += blockDim.x) h[b] = 0;
     __syncthreads();
@@ -259,24 +266,52 @@ __global__ void k_sel_hist(SelState *st, const double *__restrict__ score, int N
         if (h[b]) atomicAdd(&st->hist[b], h[b]);
 }
 
+// One warp: the digit of byte t of the k-th largest key among those that
+// match the prefix (lane l scans bins 255 - 8l down to 248 - 8l, an
+// exclusive scan over the lanes orders the lanes' totals from the top).
+// When every key in the chosen bin is among the top k (the bin's count is
+// exactly the rank still to find), the prefix with zero lower bytes
+// already separates the top k from the rest: the remaining passes are
+// skipped and the gather takes the same set.
 __global__ void k_sel_pick(SelState *st, int t)
 {
-    if (threadIdx.x != 0) return;
-    if (st->k == 0) return;  // nothing to select
-    unsigned int k = st->k, acc = 0;
-    int digit = 0;
-    for (int b = 255; b >= 0; --b) {
-        const unsigned int c = st->hist[b];
-        if (acc + c >= k) {
-            digit = b;
-            break;
-        }
-        acc += c;
+    const int lane = threadIdx.x & 31;
+    if (st->k == 0 || st->done) return;  // nothing to select (the histogram is empty)
+    const unsigned int k = st->k;
+    unsigned int c[8], sum = 0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        c[u] = st->hist[255 - 8 * lane - u];
+        sum += c[u];
     }
-    st->k = k - acc;
-    if (t < 8) st->pre_hi |= (unsigned long long)digit << (56 - 8 * t);
-    else st->pre_lo |= (unsigned int)digit << (24 - 8 * (t - 8));
-    for (int b = 0; b < 256; ++b) st->hist[b] = 0;
+    unsigned int pre = sum;  // inclusive scan over the lanes, then made exclusive
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned int v = __shfl_up_sync(0xffffffffu, pre, o);
+        if (lane >= o) pre += v;
+    }
+    pre -= sum;
+    const unsigned int mine = __ballot_sync(0xffffffffu, pre < k && k <= pre + sum);
+    if (lane == __ffs(mine) - 1) {
+        unsigned int acc = pre;
+        int digit = 0;
+        unsigned int cnt = 0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            if (acc + c[u] >= k) {
+                digit = 255 - 8 * lane - u;
+                cnt = c[u];
+                break;
+            }
+            acc += c[u];
+        }
+        st->k = k - acc;
+        if (t < 8) st->pre_hi |= (unsigned long long)digit << (56 - 8 * t);
+        else st->pre_lo |= (unsigned int)digit << (24 - 8 * (t - 8));
+        if (acc + cnt == k) st->done = 1;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) st->hist[255 - 8 * lane - u] = 0;
 }
 
 struct Cand {

@@ -85,3 +85,28 @@ def test_score_variant_errors(ctx):
     f = torch.full((6, Q), 1.0 / Q, dtype=torch.float64, device="cuda")
     with pytest.raises(_native.PlmError):
         api.plm_scores(ctx, J, norm="burkoff", freq=f, exclude_gap=True)
+
+
+@pytest.mark.parametrize("L", [8, 20, 35, 60])
+def test_topL_selection_with_ties_at_the_boundary(ctx, L):
+    # one non-zero entry per chosen block: the block's FN is proportional to
+    # |v|, so equal v give bitwise equal scores.  Ten distinct scores lie
+    # above forty equal ones (the L-th place falls among the equal ones for
+    # L = 20, 35 and above them for L = 8); L = 60 takes all fifty.  With no
+    # correction the list ranks the FN themselves; it must be the oracle's
+    # selection on the same matrix (descending, ties by (i, j)).
+    from paper_1401_4832_gb300 import api
+    N = 30
+    J = np.zeros((N, Q, N, Q), np.float32)
+    rng = np.random.default_rng(11)
+    pairs = [(i, j) for i in range(N) for j in range(i + 5, N)]
+    pick = rng.choice(len(pairs), 50, replace=False)
+    for t, p in enumerate(pick):
+        i, j = pairs[p]
+        J[i, 3, j, 7] = 100.0 + t if t < 10 else 50.0
+    sc, co, top = api.plm_scores(ctx, torch.from_numpy(J).cuda(), correction="none", L=L)
+    co = co.cpu().numpy()
+    top_o = oracle.topL(co, L)
+    got = top.cpu().numpy()
+    assert np.array_equal(got[:len(top_o)], top_o)
+    assert np.all(got[len(top_o):] == -1)
