@@ -46,28 +46,55 @@ k_fn(const float *__restrict__ J, int N, int combine, ScoreKind sk, double *__re
             }
         }
         __syncwarp();
-        double rowA = 0, colA = 0, rowB = 0, colB = 0;
-        if (lane < Q) {
-            for (int l = 0; l < Q; ++l) {
-                rowA += A[w][lane][l];
-                colA += A[w][l][lane];
-                rowB += Bt[w][lane][l];
-                colB += Bt[w][l][lane];
+        if (combine == 0) {
+            // mean of the two estimates: the Ising gauge is linear, so the
+            // mean is formed first and gauged once, C = (A + B^T) / 2
+            double rowC = 0.0;
+            if (lane < Q)
+                for (int l = 0; l < Q; ++l) {
+                    const double c = 0.5 * (A[w][lane][l] + Bt[w][lane][l]);
+                    Bt[w][lane][l] = c;
+                    rowC += c;
+                }
+            __syncwarp();
+            double colC = 0.0;
+            if (lane < Q) {
+                for (int k = 0; k < Q; ++k) colC += Bt[w][k][lane];
+                rowC /= Q;
+                colC /= Q;
+                mA[w][0][lane] = rowC;
+                mA[w][1][lane] = colC;
             }
-            rowA /= Q; colA /= Q; rowB /= Q; colB /= Q;
-            mA[w][0][lane] = rowA; mA[w][1][lane] = colA;
-            mB[w][0][lane] = rowB; mB[w][1][lane] = colB;
-        }
-        double allA = warp_sum_d(lane < Q ? rowA : 0.0) / Q;
-        double allB = warp_sum_d(lane < Q ? rowB : 0.0) / Q;
-        __syncwarp();
-        // the combined gauged block, row k = lane, kept in place of A
-        if (lane < Q) {
-            const int k = lane;
-            for (int l = 0; l < Q; ++l) {
-                double a = A[w][k][l] - mA[w][1][l] - mA[w][0][k] + allA;
-                double b = Bt[w][k][l] - mB[w][1][l] - mB[w][0][k] + allB;
-                Bt[w][k][l] = combine == 1 ? fmin(a, b) : combine == 2 ? fmax(a, b) : 0.5 * (a + b);
+            const double allC = warp_sum_d(lane < Q ? rowC : 0.0) / Q;
+            __syncwarp();
+            if (lane < Q)
+                for (int l = 0; l < Q; ++l)
+                    Bt[w][lane][l] = Bt[w][lane][l] - mA[w][1][l] - mA[w][0][lane] + allC;
+        } else {
+            double rowA = 0, colA = 0, rowB = 0, colB = 0;
+            if (lane < Q) {
+                for (int l = 0; l < Q; ++l) {
+                    rowA += A[w][lane][l];
+                    colA += A[w][l][lane];
+                    rowB += Bt[w][lane][l];
+                    colB += Bt[w][l][lane];
+                }
+                rowA /= Q; colA /= Q; rowB /= Q; colB /= Q;
+                mA[w][0][lane] = rowA; mA[w][1][lane] = colA;
+                mB[w][0][lane] = rowB; mB[w][1][lane] = colB;
+            }
+            double allA = warp_sum_d(lane < Q ? rowA : 0.0) / Q;
+            double allB = warp_sum_d(lane < Q ? rowB : 0.0) / Q;
+            __syncwarp();
+            // the combined gauged block (min or max of the two gauged
+            // estimates), row k = lane
+            if (lane < Q) {
+                const int k = lane;
+                for (int l = 0; l < Q; ++l) {
+                    double a = A[w][k][l] - mA[w][1][l] - mA[w][0][k] + allA;
+                    double b = Bt[w][k][l] - mB[w][1][l] - mB[w][0][k] + allB;
+                    Bt[w][k][l] = combine == 1 ? fmin(a, b) : fmax(a, b);
+                }
             }
         }
         __syncwarp();
