@@ -115,14 +115,17 @@ k_fn(const float *__restrict__ J, int N, int combine, ScoreKind sk, double *__re
                 }
             out = warp_sum_d(d);
         } else {
+            // l_p with p = 1 is the sum of |a| and with p = 2 the Frobenius
+            // norm: no pow for those (pow(a, 1) = a exactly)
+            const int pk = sk.kind != 1 ? 2 : sk.p == 1.0 ? 1 : sk.p == 2.0 ? 2 : 0;
             double ss = 0.0;
             if (lane < Q && !(sk.exclude_gap && lane == 0))
                 for (int l = sk.exclude_gap ? 1 : 0; l < Q; ++l) {
                     const double a = fabs(Bt[w][lane][l]);
-                    ss += sk.kind == 1 ? pow(a, sk.p) : a * a;
+                    ss += pk == 1 ? a : pk == 2 ? a * a : pow(a, sk.p);
                 }
             ss = warp_sum_d(ss);
-            out = sk.kind == 1 ? pow(ss, 1.0 / sk.p) : sqrt(ss);
+            out = pk == 1 ? ss : pk == 2 ? sqrt(ss) : pow(ss, 1.0 / sk.p);
         }
         if (lane == 0) {
             fn[(size_t)i * N + j] = out;

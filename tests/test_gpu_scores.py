@@ -110,3 +110,13 @@ def test_topL_selection_with_ties_at_the_boundary(ctx, L):
     got = top.cpu().numpy()
     assert np.array_equal(got[:len(top_o)], top_o)
     assert np.all(got[len(top_o):] == -1)
+
+
+def test_lp2_is_frobenius(ctx):
+    # the l_p score with p = 2 is the Frobenius norm (same arithmetic)
+    from paper_1401_4832_gb300 import api
+    J = torch.from_numpy(_J(17, 5)).cuda()
+    a = api.plm_scores(ctx, J, norm="lp", p=2.0)
+    b = api.plm_scores(ctx, J, norm="fro")
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
