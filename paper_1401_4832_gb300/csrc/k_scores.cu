@@ -102,15 +102,21 @@ k_fn(const float *__restrict__ J, int N, int combine, ScoreKind sk, double *__re
         if (sk.kind == 2) {
             // Burkoff: P = f_i(k) f_j(l) e^v / Z and ln(P / (f_i f_j)) = v - ln Z
             const double *fi = sk.freq + (size_t)i * Q, *fj = sk.freq + (size_t)j * Q;
+            // the unnormalised weights f_i f_j e^v, kept in A (free after the
+            // gauge) for the second pass
             double z = 0.0;
             if (lane < Q)
-                for (int l = 0; l < Q; ++l) z += fi[lane] * fj[l] * exp(Bt[w][lane][l]);
+                for (int l = 0; l < Q; ++l) {
+                    const double u = fi[lane] * fj[l] * exp(Bt[w][lane][l]);
+                    A[w][lane][l] = u;
+                    z += u;
+                }
             const double Z = warp_sum_d(z);
             const double lz = log(Z);
             double d = 0.0;
             if (lane < Q)
                 for (int l = 0; l < Q; ++l) {
-                    const double P = fi[lane] * fj[l] * exp(Bt[w][lane][l]) / Z;
+                    const double P = A[w][lane][l] / Z;
                     if (P > 0.0) d += P * (Bt[w][lane][l] - lz);
                 }
             out = warp_sum_d(d);
