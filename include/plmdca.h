@@ -296,15 +296,20 @@ plm_status msa_frequencies(plm_ctx *ctx, const int8_t *msa, const float *w, doub
  * bytes; larger problems return PLM_ENOMEM before anything is launched.
  *   msa [B][N] int8, m_out [B] int32 (may be NULL), w_out [B] float (may be
  *   NULL), beff_out: one double -- all DEVICE pointers, owned by the caller.
- *   cuda_stream: the cudaStream_t the work is ordered on (NULL = legacy).
+ *   cuda_stream: the cudaStream_t the work is ordered on (NULL = legacy);
+ *   it must belong to the current device (the array used is the current
+ *   device's), else PLM_EINVAL.
  * Work is queued on the stream; the call does not synchronise.  States
  * outside 0..20 make *beff_out NaN.  PLM_EINVAL for q != 21, B < 1, N < 1,
- * x outside [0,1] or a NULL msa/beff_out; PLM_ECUDA if a CUDA call fails.
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Every call shares the array and it keeps the
- * previous call's contents (each call clears what must start at zero), so
- * calls whose work overlaps on the GPU race: order them on one stream. */
+ * x outside [0,1], a NULL msa/beff_out or a stream of another device;
+ * PLM_ECUDA if a CUDA call fails.  Every call looks up the array's device
+ * address (cudaGetSymbolAddress, a host-side lookup) in the current
+ * context, so calls after cudaDeviceReset or from another context on the
+ * same device use that context's array.  The first call in a context may
+ * load the library's device code: make it before any stream capture.
+ * Every call shares the array and it keeps the previous call's contents
+ * (each call clears what must start at zero), so calls whose work overlaps
+ * on the GPU race: order them on one stream. */
 plm_status msa_reweight_static(const int8_t *msa, int B, int N, int q, double x,
                                int32_t *m_out, float *w_out, double *beff_out,
                                void *cuda_stream);

@@ -739,12 +739,18 @@ void orc_score_matrix(const double *J, int N, int q, int combine, int kind, doub
             double out = 0.0;
             if (kind == 2) {
                 const double *fi = freq + (size_t)i * q, *fj = freq + (size_t)j * q;
+                /* P is unchanged when the same constant is taken off every
+                 * exponent (Z absorbs it); taking off the block maximum keeps
+                 * exp() finite for large couplings */
+                double vmax = v[0];
+                for (int e = 1; e < q * q; ++e)
+                    if (v[e] > vmax) vmax = v[e];
                 double Z = 0.0;
                 for (int k = 0; k < q; ++k)
-                    for (int l = 0; l < q; ++l) Z += fi[k] * fj[l] * exp(v[k * q + l]);
+                    for (int l = 0; l < q; ++l) Z += fi[k] * fj[l] * exp(v[k * q + l] - vmax);
                 for (int k = 0; k < q; ++k)
                     for (int l = 0; l < q; ++l) {
-                        double P = fi[k] * fj[l] * exp(v[k * q + l]) / Z;
+                        double P = fi[k] * fj[l] * exp(v[k * q + l] - vmax) / Z;
                         if (P > 0.0) out += P * log(P / (fi[k] * fj[l]));
                     }
             } else {

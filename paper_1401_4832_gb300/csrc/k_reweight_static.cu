@@ -17,25 +17,25 @@
 // calls whose work overlaps on the GPU (different streams, or one device
 // used from several host threads without ordering) race on the array and
 // give undefined results: order them.
-#include <cmath>
-#include <mutex>
-
+//
+// In host code the array's name is a host-side stand-in, not a device
+// address.  Every call looks the device address up again with
+// cudaGetSymbolAddress, with the stream's device current (a host-side
+// lookup, no allocation), so an address never outlives the context it
+// belongs to: after cudaDeviceReset, or from another context on the same
+// device, the next call gets the array of the context that is current.
+// The first call in a context may load the library's device code; make it
+// before any stream capture.
 #include "../../include/plmdca.h"
 #include "plm_internal.cuh"
 
 namespace {
 
 constexpr size_t kScratchBytes = 16u << 20;  // 16 MiB
-constexpr int kMaxDevices = 64;
 
 // the shared scratch of every call on a device: bit-planes, counts,
 // histogram and the state-range flag
 __device__ __align__(256) unsigned char g_reweight_scratch[kScratchBytes];
-
-// In host code `g_reweight_scratch` names a host-side stand-in, not the
-// device array; the device address is looked up once per device.
-std::mutex g_setup_mutex;
-void *g_scratch_addr[kMaxDevices] = {nullptr};
 
 // marks B_eff as NaN when some state was outside 0..20
 __global__ void k_flag_to_beff(const int *err, double *beff)
@@ -58,26 +58,27 @@ extern "C" plm_status msa_reweight_static(const int8_t *msa, int B, int N, int q
     const size_t need = rw + 256;
     if (need > kScratchBytes) return PLM_ENOMEM;  // beyond the static maximum
 
+    // the work runs on the stream's device, which must be the current one:
+    // the array's address below is the current device's
+    cudaStream_t st = (cudaStream_t)cuda_stream;
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    if (cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();
         return PLM_ECUDA;
     }
-    void *base = nullptr;
-    {
-        std::lock_guard<std::mutex> lock(g_setup_mutex);
-        if (!g_scratch_addr[dev]) {
-            void *p = nullptr;
-            cudaError_t e = cudaGetSymbolAddress(&p, g_reweight_scratch);
-            if (e != cudaSuccess || !p) {
-                cudaGetLastError();
-                return PLM_ECUDA;
-            }
-            g_scratch_addr[dev] = p;
+    if (st) {
+        int sdev = -1;
+        if (cudaStreamGetDevice(st, &sdev) != cudaSuccess) {
+            cudaGetLastError();
+            return PLM_EINVAL;
         }
-        base = g_scratch_addr[dev];
+        if (sdev != dev) return PLM_EINVAL;
     }
-    cudaStream_t st = (cudaStream_t)cuda_stream;
+    void *base = nullptr;
+    if (cudaGetSymbolAddress(&base, g_reweight_scratch) != cudaSuccess || !base) {
+        cudaGetLastError();
+        return PLM_ECUDA;
+    }
     unsigned char *scratch = (unsigned char *)base;
     int *err = (int *)(scratch + rw);
 
@@ -86,9 +87,8 @@ extern "C" plm_status msa_reweight_static(const int8_t *msa, int B, int N, int q
         return PLM_ECUDA;
     }
     // the launcher clears the counts and the histogram itself
-    const double t = std::ceil(x * (double)N - 1e-9);
-    const int T = t < 0 ? 0 : (int)t;
-    cudaError_t e = plm::launch_reweight(msa, B, N, T, m_out, w_out, beff_out, scratch, err, st);
+    cudaError_t e = plm::launch_reweight(msa, B, N, plm::identity_threshold(x, N), m_out, w_out,
+                                         beff_out, scratch, err, st);
     if (e == cudaSuccess) {
         k_flag_to_beff<<<1, 1, 0, st>>>(err, beff_out);
         plm::count_launches(1);

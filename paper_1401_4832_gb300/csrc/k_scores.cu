@@ -100,19 +100,26 @@ k_fn(const float *__restrict__ J, int N, int combine, ScoreKind sk, double *__re
         __syncwarp();
         double out;
         if (sk.kind == 2) {
-            // Burkoff: P = f_i(k) f_j(l) e^v / Z and ln(P / (f_i f_j)) = v - ln Z
+            // Burkoff: P = f_i(k) f_j(l) e^(v - vmax) / Z and ln(P / (f_i f_j))
+            // = v - vmax - ln Z; the block maximum vmax cancels in P and keeps
+            // every exponential finite
             const double *fi = sk.freq + (size_t)i * Q, *fj = sk.freq + (size_t)j * Q;
-            // the unnormalised weights f_i f_j e^v, kept in A (free after the
-            // gauge) for the second pass
+            double vmax = -INFINITY;
+            if (lane < Q)
+                for (int l = 0; l < Q; ++l) vmax = fmax(vmax, Bt[w][lane][l]);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) vmax = fmax(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+            // the unnormalised weights f_i f_j e^(v - vmax), kept in A (free
+            // after the gauge) for the second pass
             double z = 0.0;
             if (lane < Q)
                 for (int l = 0; l < Q; ++l) {
-                    const double u = fi[lane] * fj[l] * exp(Bt[w][lane][l]);
+                    const double u = fi[lane] * fj[l] * exp(Bt[w][lane][l] - vmax);
                     A[w][lane][l] = u;
                     z += u;
                 }
             const double Z = warp_sum_d(z);
-            const double lz = log(Z);
+            const double lz = log(Z) + vmax;
             double d = 0.0;
             if (lane < Q)
                 for (int l = 0; l < Q; ++l) {

@@ -110,6 +110,13 @@ void prof_stop(void *ctx, const char *name, void *start)
     cudaEventRecord(b, c->stream);
     c->prof_records.push_back({name, (cudaEvent_t)start, b, 0.0});
 }
+
+int identity_threshold(double x, int N)
+{
+    // smallest integer count T with T / N >= x
+    double t = std::ceil(x * (double)N - 1e-9);
+    return t < 0 ? 0 : (int)t;
+}
 }  // namespace plm
 
 namespace {
@@ -209,13 +216,6 @@ cudaError_t copy_back(plm_ctx *ctx, const Staged &s)
 {
     if (!s.host) return cudaSuccess;
     return cudaMemcpyAsync(s.host, s.dev, s.bytes, cudaMemcpyDeviceToHost, ctx->stream);
-}
-
-int identity_threshold(double x, int N)
-{
-    // smallest integer count T with T / N >= x
-    double t = std::ceil(x * (double)N - 1e-9);
-    return t < 0 ? 0 : (int)t;
 }
 
 __global__ void k_check_msa(const int8_t *msa, size_t n, int *err)

@@ -123,6 +123,10 @@ struct SolveParams {
 // scratch: planes [5][B][W] uint32 with W = ceil(N/32), m [B], hist [B+1];
 // err (device int, caller-zeroed) gets bit 0 set for states outside 0..20
 size_t reweight_scratch_bytes(int B, int N);
+// the integer identity threshold of Sec. 3.1 (two sequences are similar
+// when at least a fraction x of their N positions match): the smallest
+// count T with T / N >= x, computed as ceil(x N - 1e-9)
+int identity_threshold(double x, int N);
 cudaError_t launch_reweight(const int8_t *msa, int B, int N, int T,
                             int32_t *m_out, float *w_out, double *beff_dev,
                             void *scratch, int *err, cudaStream_t st);

@@ -120,3 +120,21 @@ def test_lp2_is_frobenius(ctx):
     b = api.plm_scores(ctx, J, norm="fro")
     for x, y in zip(a, b):
         assert torch.equal(x, y)
+
+
+def test_burkoff_large_couplings_match_oracle(ctx):
+    # couplings far beyond exp's range (gauged entries of several hundred):
+    # both sides take the block maximum off the exponent, so D_ij stays
+    # finite and equal to the oracle's
+    from paper_1401_4832_gb300 import api
+    N = 13
+    J = _J(N, 7) * 4000.0
+    S = synth.small_random(N, 300, 9, gap_p=0.15)
+    m, w, w32, beff = oracle.reweight(S, 0.8)
+    freq = oracle.site_freqs(S, w, beff)
+    sc_o = oracle.score_matrix(J.astype(np.float64), "burkoff", freq=freq)
+    assert np.all(np.isfinite(sc_o))
+    sc, co, top = api.plm_scores(ctx, torch.from_numpy(J).cuda(), norm="burkoff",
+                                 freq=torch.from_numpy(freq).cuda())
+    assert np.allclose(sc.cpu().numpy(), sc_o, rtol=1e-9, atol=1e-12)
+    assert np.array_equal(top.cpu().numpy(), oracle.topL(oracle.apc(sc_o), N))

@@ -35,6 +35,15 @@ MUTANTS = {
         ("if (i == r) continue;\n                        gJ_r[((size_t)s * N + i) * q + seq[i]] += d;",
          "gJ_r[((size_t)s * N + i) * q + seq[i]] += d;"),
     "weights not normalised by B_eff": ("return -loglik / beff + lambda_h", "return -loglik / B + lambda_h"),
+    "min and max combiners swapped":
+        ("if (combine == 1) v = gi[e] < gj[e] ? gi[e] : gj[e];",
+         "if (combine == 1) v = gi[e] > gj[e] ? gi[e] : gj[e];"),
+    "min combiner computed as the mean":
+        ("if (combine == 1) v = gi[e] < gj[e] ? gi[e] : gj[e];",
+         "if (combine == 1) v = 0.5 * (gi[e] + gj[e]);"),
+    "max combiner of the score alternatives computed as the min":
+        ("else if (combine == 2) v[e] = gi[e] > gj[e] ? gi[e] : gj[e];",
+         "else if (combine == 2) v[e] = gi[e] < gj[e] ? gi[e] : gj[e];"),
     # symmetric plmDCA (caught by the symmetric pins)
     "symmetric mirror copy not transposed":
         ("J[(((size_t)j * q + l) * N + i) * q + k] = blk[k * q + l]; /* J_ji(l,k) */",

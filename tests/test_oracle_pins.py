@@ -348,6 +348,55 @@ def test_fn_uses_the_transposed_mirror_block():
     assert np.allclose(fmin, fn, rtol=1e-12) and np.allclose(fmax, fn, rtol=1e-12)
 
 
+def _gauge_by_lstsq(M):
+    # Ising-gauge part of a q x q block computed as the residual of a
+    # least-squares fit of a(k) + b(l) (independent of the oracle's gauge map)
+    A = np.zeros((Q * Q, 2 * Q))
+    for k in range(Q):
+        for l in range(Q):
+            A[k * Q + l, k] = 1
+            A[k * Q + l, Q + l] = 1
+    coef, *_ = np.linalg.lstsq(A, M.ravel(), rcond=None)
+    return (M.ravel() - A @ coef).reshape(Q, Q)
+
+
+def test_min_max_combiners_on_distinct_estimates():
+    # Sec. 6 names the elementwise minimum and maximum of the two gauged
+    # estimates as alternatives to the average (Eq. average2).  Site i
+    # carries G1 (first index at i) and site j carries G2 transposed, each
+    # with its own gauge junk; the combined block is then min(G1, G2),
+    # max(G1, G2) or (G1 + G2)/2 elementwise and every score follows.
+    rng = np.random.default_rng(11)
+    N = 5
+    J = np.zeros((N, Q, N, Q))
+    G1, G2 = {}, {}
+    for i in range(N):
+        for j in range(i + 1, N):
+            g1 = _gauge_by_lstsq(rng.normal(0, 1, (Q, Q)))
+            g2 = _gauge_by_lstsq(rng.normal(0, 1, (Q, Q)))
+            G1[i, j], G2[i, j] = g1, g2
+            a, b = rng.normal(0, 2, Q), rng.normal(0, 2, Q)
+            J[i, :, j, :] = g1 + a[:, None] + b[None, :]
+            a, b = rng.normal(0, 2, Q), rng.normal(0, 2, Q)
+            J[j, :, i, :] = g2.T + a[:, None] + b[None, :]
+    expect = {"min": np.minimum, "max": np.maximum, "mean": lambda x, y: 0.5 * (x + y)}
+    for comb, op in expect.items():
+        fn, _ = oracle.scores(J, comb)
+        l1 = oracle.score_matrix(J, kind="lp", p=1.0, combine=comb)
+        fro = oracle.score_matrix(J, kind="fro", combine=comb)
+        for (i, j) in G1:
+            v = op(G1[i, j], G2[i, j])
+            assert fn[i, j] == pytest.approx(np.linalg.norm(v), rel=1e-12), comb
+            assert fn[j, i] == fn[i, j]
+            assert fro[i, j] == pytest.approx(np.linalg.norm(v), rel=1e-12), comb
+            assert l1[i, j] == pytest.approx(np.abs(v).sum(), rel=1e-12), comb
+    # the three combiners really differ here
+    fmin, _ = oracle.scores(J, "min")
+    fmax, _ = oracle.scores(J, "max")
+    fmean, _ = oracle.scores(J, "mean")
+    assert not np.allclose(fmin, fmax) and not np.allclose(fmin, fmean)
+
+
 def test_gauge_and_average_commute():
     # both maps are linear, so the order does not matter (Sec. 3.2)
     rng = np.random.default_rng(2)

@@ -74,11 +74,13 @@ def test_norms_are_gauge_invariant():
                            rtol=1e-12, atol=1e-13)
 
 
-def test_burkoff_two_states_symbolic():
+@pytest.mark.parametrize("a_num", [3, 10000])
+def test_burkoff_two_states_symbolic(a_num):
     # q = 2: D_ij evaluated symbolically (sympy) from Eqs. burkoffscore1-2 with
-    # the block in the Ising gauge, v = a [[1, -1], [-1, 1]]
+    # the block in the Ising gauge, v = a [[1, -1], [-1, 1]]; a = 1000 puts
+    # e^v far beyond the double range, where only a shifted exponent is finite
     sp = pytest.importorskip("sympy")
-    a, x, y = sp.Rational(3, 10), sp.Rational(1, 5), sp.Rational(7, 10)
+    a, x, y = sp.Rational(a_num, 10), sp.Rational(1, 5), sp.Rational(7, 10)
     V = sp.Matrix([[a, -a], [-a, a]])
     fi = [x, 1 - x]
     fj = [y, 1 - y]

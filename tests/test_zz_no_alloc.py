@@ -76,3 +76,21 @@ def test_static_reweight_rejects_problems_beyond_its_scratch():
     assert st == -2  # PLM_ENOMEM
     st = lib.msa_reweight_static(ctypes.c_void_p(S_dev.data_ptr()), 4, 8, 20, 0.8, p, p, p, None)
     assert st == -1  # PLM_EINVAL
+
+
+def test_static_reweight_flags_states_outside_the_alphabet():
+    # a state outside 0..20 makes B_eff NaN (the call itself succeeds: the
+    # check runs on the GPU and the call does not synchronise); the next
+    # call with a valid MSA starts from a cleared flag and is exact again
+    lib = _lib()
+    stream = torch.cuda.current_stream()
+    S = synth.small_random(23, 150, 4)
+    bad = S.copy()
+    bad[17, 5] = 25
+    bad[90, 11] = -3
+    _, _, beff_bad = _static_call(lib, torch.from_numpy(bad).cuda(), 0.8, stream)
+    assert np.isnan(beff_bad)
+    m, w, beff = _static_call(lib, torch.from_numpy(S).cuda(), 0.8, stream)
+    m_o, _, w32_o, beff_o = oracle.reweight(S, 0.8)
+    assert np.array_equal(m, m_o) and beff == beff_o
+    assert np.array_equal(w.view(np.uint32), w32_o.view(np.uint32))
