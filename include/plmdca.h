@@ -336,6 +336,17 @@ long long plm_kernel_launches(void);
 plm_status plm_selftest_wait(plm_ctx *ctx, int *code_out);
 plm_status plm_profile(plm_ctx *ctx, int enable);
 int plm_profile_report(plm_ctx *ctx, char *buf, int len);
+/* plm_measure_peak: a diagnostic, not part of the method.  Measures the
+ * CUDA cores' throughput of one instruction on the current device, the
+ * denominator of an ALU-bound roofline: kind 0 FP32 add, 1 FP32 fused
+ * multiply-add (one instruction counted once), 2 FP64 add, 3 32-bit
+ * three-input logic op (lop3), 4 population count.  Every thread of a grid
+ * of 4 x 256-thread blocks per SM runs 16 independent chains; the best of
+ * five launches (after two warm-ups, CUDA events on cuda_stream, NULL =
+ * legacy stream) gives *ops_per_s, instructions per second over all
+ * threads.  Synchronises the stream.  PLM_EINVAL for an unknown kind or a
+ * NULL output; PLM_ECUDA if a CUDA call fails. */
+plm_status plm_measure_peak(int kind, void *cuda_stream, double *ops_per_s);
 
 #ifdef __cplusplus
 }

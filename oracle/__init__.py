@@ -56,6 +56,8 @@ def _load():
         I = ctypes.c_int
         D = ctypes.c_double
         lib.orc_num_threads.restype = I
+        lib.orc_set_threads.argtypes = [I]
+        lib.orc_set_threads.restype = None
         lib.orc_identity_threshold.argtypes = [D, I]
         lib.orc_identity_threshold.restype = I
         lib.orc_reweight.argtypes = [P, I, I, I, P, P, P, P]
@@ -107,6 +109,11 @@ def _msa(S) -> np.ndarray:
 
 def num_threads() -> int:
     return _load().orc_num_threads()
+
+
+def set_threads(n: int) -> None:
+    """Thread count of the oracle's OpenMP loops over sites (timing only)."""
+    _load().orc_set_threads(int(n))
 
 
 def identity_threshold(x: float, N: int) -> int:

@@ -51,6 +51,17 @@ int orc_num_threads(void)
 #endif
 }
 
+/* thread count of the OpenMP loops over sites (timing only; results do not
+ * depend on it) */
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /* ------------------------------------------------------------------------
  * Step 2 of the rundown (Eq. inverse_weights2): sequence reweighting.
  *

@@ -135,6 +135,10 @@ def load():
         lib.plm_profile.restype = I
         lib.plm_profile_report.argtypes = [P, ctypes.c_char_p, I]
         lib.plm_profile_report.restype = I
+        lib.plm_measure_peak.argtypes = [I, P, ctypes.POINTER(D)]
+        lib.plm_measure_peak.restype = I
+        lib.msa_reweight_static.argtypes = [P, I, I, I, D, P, P, P, P]
+        lib.msa_reweight_static.restype = I
         _lib = lib
         return lib
 

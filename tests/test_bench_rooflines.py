@@ -5,7 +5,8 @@ import math
 
 import bench
 
-PK = {"hbm_gbs": 6689.8, "bf16_tflops_sustained": 1744.5, "sm_max_mhz": 2070.0}
+PK = {"hbm_gbs": 6689.8, "bf16_tflops": 1908.3, "bf16_tflops_sustained": 1744.5,
+      "sm_max_mhz": 2070.0}
 
 
 def test_hbm_and_tensor_entries():
@@ -18,7 +19,9 @@ def test_hbm_and_tensor_entries():
     flops = 2 * 2 * 1000 * (50 * 21) * (50 * 21 + 1)
     assert t["flops_per_launch"] == flops
     assert math.isclose(t["achieved"], flops / 100e-6 / 1e12)
-    assert math.isclose(t["frac"], t["achieved"] / 1744.5)
+    # timed alone on full evaluations: the burst peak is the denominator
+    assert math.isclose(t["frac"], t["achieved"] / 1908.3)
+    assert math.isclose(t["frac_of_sustained"], t["achieved"] / 1744.5)
 
 
 def test_algorithmic_fraction():
@@ -39,7 +42,21 @@ def test_reweight_integer_ops():
     r = out["reweight"]
     assert r["bound"] == "alu" and r["ops_per_launch"] == ops
     assert math.isclose(r["achieved"], ops / 0.1e-3 / 1e12)
-    assert math.isclose(r["peak"], 152 * 128 * 2070e6 / 1e12)
+    assert math.isclose(r["peak"], 152 * 128 * 2070e6 / 1e12)  # derived without measurements
+    # with measured lop3 and popc rates the peak is the 6 + 1 mix's rate
+    alu = {"lop3_b32": 40e12, "popc_b32": 5e12, "fadd_f32": 39e12}
+    r = bench.kernel_rooflines({"reweight": (2, 0.2, 0)}, {}, B, N, PK, "measured", alu)["reweight"]
+    assert math.isclose(r["peak"], 7.0 / max(6 / 40e12, 1 / 5e12) / 1e12)
+
+
+def test_measured_fp32_add_rate_sets_the_algorithmic_fraction():
+    B, N = 5000, 120
+    alu = {"fadd_f32": 30e12}
+    out = bench.kernel_rooflines({}, {"tc_logits": 130e-6, "logits_gather": 1e-3}, B, N, PK,
+                                 "measured", alu)
+    assert math.isclose(out["tc_logits"]["algorithmic_frac"], B * N * (N - 1) * 21 / 30e12 / 130e-6)
+    g = out["logits_gather"]
+    assert math.isclose(g["peak"], 30.0) and math.isclose(g["frac"], B * N * N * 21 / 1e-3 / 30e12)
 
 
 def test_clock_summary_keeps_the_timed_window():
