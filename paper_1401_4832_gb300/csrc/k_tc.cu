@@ -611,6 +611,421 @@ k_tc_logits(const __grid_constant__ LogitsParams P, int *__restrict__ err)
     }
 }
 
+// ---------------------------------------------------------------- CTA pair
+// The logits on a pair of CTAs (a 2-CTA cluster, tcgen05 cta_group::2):
+// one MMA instruction computes a 256-sequence x NMMA-column product, each
+// CTA holding its own 128 sequences' one-hot rows (A) and half of the Theta
+// rows (B), each accumulating its 128 rows in its own tensor memory.  Half
+// the Theta bytes per SM let a pipeline stage carry 128 of K (16 MMAs per
+// stage handshake instead of 8).  Sites are packed 21 columns apart (no
+// padding rows): a CTA's B half holds SH sites (21 SH rows, the rest of the
+// NMMA/2 rows unused), loaded by one 3-D TMA box per operand and K atom.
+__device__ __forceinline__ uint32_t cluster_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// the shared::cluster address of `p` (this CTA's shared memory) in CTA `rank`
+__device__ __forceinline__ uint32_t cluster_addr(const void *p, uint32_t rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t caddr)
+{
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(caddr)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cluster_sync_all()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\t"
+                 "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// 3-D box into this CTA's shared memory, completion counted on the barrier
+// at cluster address `bar_cl` (the leader CTA's)
+__device__ __forceinline__ void tma_load_3d_pair(void *dst, const CUtensorMap *map, uint32_t bar_cl,
+                                                 int x, int y, int z)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(bar_cl)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc_pair(uint32_t *dst, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(dst)),
+                 "r"(ncols)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_relinquish_pair()
+{
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc_pair(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mma_bf16_pair(uint32_t d_tmem, uint64_t a, uint64_t b,
+                                              uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// arrives (when the MMAs issued so far are complete) on the barrier at the
+// same shared-memory offset in both CTAs of the pair
+__device__ __forceinline__ void mma_commit_pair(uint64_t *bar)
+{
+    const uint16_t mask = 3;
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 "
+        "[%0], %1;" ::"r"(smem_u32(bar)),
+        "h"(mask)
+        : "memory");
+}
+
+struct PairParams {
+    TcBatch b;
+    int stages, stage_bytes;   // a stage holds one or two K atoms of 64
+    CUtensorMap hi[MAX_FAM], lo[MAX_FAM];  // 3-D maps (KP, 21 states, N sites), box (64, 21, SH)
+};
+
+constexpr int LP_THREADS = 448;
+
+template <int SH, int ATOMS>
+struct PairShape {
+    static constexpr int SITES = 2 * SH;                        // sites per tile
+    static constexpr int NMMA = (SITES * Q + 15) / 16 * 16;     // MMA N (accumulator columns)
+    static constexpr int NH = NMMA / 2;                         // B rows per CTA
+    static constexpr int A_ATOM = TC_M * TC_BK * 2;             // 16 KB
+    static constexpr int B_ATOM = (NH * TC_BK * 2 + 1023) / 1024 * 1024;
+    static constexpr int STAGE = ATOMS * (A_ATOM + 2 * B_ATOM);  // ATOMS K atoms of 64
+    static constexpr int BOX_BYTES = TC_BK * 2 * Q * SH;        // one (64, 21, SH) box
+};
+
+// tile t of the pair grid: family, 256-sequence tile, site group
+__device__ __forceinline__ void lp_tile(const TcBatch &b, int t, int sites, int &fi, int &ptb,
+                                        int &tr)
+{
+    fi = family_of(b, t, false);
+    const FamDesc &F = b.f[fi];
+    const int local = t - F.tile0_logits;
+    const int nbt2 = (F.BP / TC_M + 1) / 2;
+    ptb = local % nbt2;
+    tr = local / nbt2;
+}
+
+// Roles (both CTAs): warp 0 TMA of this CTA's Theta half, signalled on the
+// leader's barrier; warp 1 tensor memory (both) and MMA issue (leader
+// only); warps 2-5 one-hot producers of this CTA's 128 sequences, arriving
+// on the leader's barrier; warps 6-13 epilogue of this CTA's accumulator
+// rows, two groups of four warps taking the two site halves.
+template <int SH, int LP_ATOMS>
+__global__ void __launch_bounds__(LP_THREADS, 1)
+k_tc_logits_pair(const __grid_constant__ PairParams P, int *__restrict__ err)
+{
+    using S = PairShape<SH, LP_ATOMS>;
+    extern __shared__ uint8_t dsmem[];
+    uint8_t *smem = align1024(dsmem);
+    const int NST = P.stages;
+    __shared__ __align__(8) uint64_t full_[MAX_STAGES], empty_[MAX_STAGES];
+    __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2], mma_done;
+    __shared__ uint32_t tmem_sh;
+    __shared__ int abort_sh;
+    __shared__ double red[4][S::SITES];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_rank();
+    const bool leader = rank == 0;
+    const int pair = blockIdx.x >> 1, npairs = gridDim.x >> 1;
+    const int ntiles = P.b.ntiles_logits;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < MAX_STAGES; ++s) {
+            mbar_init(&full_[s], 1 + 2 * 4);  // leader's TMA arrival + 4 producer warps per CTA
+            mbar_init(&empty_[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&acc_full[a], 1);
+            mbar_init(&acc_empty[a], 2 * 8);  // 8 epilogue warps per CTA
+        }
+        mbar_init(&mma_done, 1);
+        abort_sh = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+    cluster_sync_all();  // both CTAs' barriers exist before any remote arrival
+    if (warp == 1) {
+        // one warp of each CTA allocates, together, the same columns in both
+        tmem_alloc_pair(&tmem_sh, 2 * TMEM_COLS);
+        tmem_relinquish_pair();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_sh;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            long long kit = 0;
+            bool ok = true;
+            for (int t = pair; t < ntiles && ok; t += npairs) {
+                int fi, ptb, tr;
+                lp_tile(P.b, t, S::SITES, fi, ptb, tr);
+                const FamDesc &F = P.b.f[fi];
+                if (!sites_active(F, tr * S::SITES, tr * S::SITES + S::SITES - 1)) continue;
+                const int site0 = tr * S::SITES + (int)rank * SH;
+                const int NA = F.KP / TC_BK;
+                for (int ka = 0; ka < NA; ka += LP_ATOMS, ++kit) {
+                    const int na = NA - ka < LP_ATOMS ? NA - ka : LP_ATOMS;
+                    const int s = (int)(kit % NST);
+                    const long long n = kit / NST;
+                    if (n > 0 &&
+                        !mbar_wait(&empty_[s], (uint32_t)((n - 1) & 1), &abort_sh, err, ERR_TIMEOUT_TMA)) {
+                        ok = false;
+                        break;
+                    }
+                    uint8_t *st = smem + s * S::STAGE;
+                    const uint32_t bar = cluster_addr(&full_[s], 0);
+                    if (leader) mbar_expect_tx(&full_[s], 2 * na * 2 * S::BOX_BYTES);
+                    for (int a = 0; a < na; ++a) {
+                        uint8_t *bh = st + LP_ATOMS * S::A_ATOM + 2 * a * S::B_ATOM;
+                        tma_load_3d_pair(bh, &P.hi[fi], bar, (ka + a) * TC_BK, 0, site0);
+                        tma_load_3d_pair(bh + S::B_ATOM, &P.lo[fi], bar, (ka + a) * TC_BK, 0, site0);
+                    }
+                }
+            }
+            // the leader's barriers count both CTAs' copies: let the copies
+            // still in flight land before either CTA can exit
+            if (leader)
+                for (long long k = kit - NST < 0 ? 0 : kit - NST; k < kit; ++k)
+                    mbar_drain(&full_[k % NST], (uint32_t)((k / NST) & 1));
+        }
+    } else if (warp == 1) {
+        if (lane == 0 && leader) {
+            const uint32_t idesc = idesc_bf16(2 * TC_M, S::NMMA);
+            long long kit = 0;
+            int ti = 0;
+            bool ok = true;
+            for (int t = pair; t < ntiles && ok; t += npairs) {
+                int fi, ptb, tr;
+                lp_tile(P.b, t, S::SITES, fi, ptb, tr);
+                const FamDesc &F = P.b.f[fi];
+                if (!sites_active(F, tr * S::SITES, tr * S::SITES + S::SITES - 1)) continue;
+                const int a = ti & 1, use = ti >> 1;
+                if (use > 0 && !mbar_wait(&acc_empty[a], (uint32_t)((use - 1) & 1), &abort_sh,
+                                                  err, ERR_TIMEOUT_MMA))
+                    break;
+                tc_fence_after();
+                const uint32_t dt = tmem + a * TMEM_COLS;
+                const int NA = F.KP / TC_BK;
+                for (int ka = 0; ka < NA; ka += LP_ATOMS, ++kit) {
+                    const int na = NA - ka < LP_ATOMS ? NA - ka : LP_ATOMS;
+                    const int s = (int)(kit % NST);
+                    const uint32_t ph = (uint32_t)((kit / NST) & 1);
+                    if (!mbar_wait(&full_[s], ph, &abort_sh, err, ERR_TIMEOUT_MMA)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    uint8_t *st = smem + s * S::STAGE;
+                    for (int a2 = 0; a2 < na; ++a2) {
+                        const uint32_t aa = smem_u32(st + a2 * S::A_ATOM);
+                        const uint32_t bh = smem_u32(st + LP_ATOMS * S::A_ATOM + 2 * a2 * S::B_ATOM);
+                        const uint32_t bl = bh + S::B_ATOM;
+#pragma unroll
+                        for (int k = 0; k < TC_BK / 16; ++k)
+                            mma_bf16_pair(dt, sdesc(aa + 32 * k), sdesc(bh + 32 * k), idesc,
+                                          (ka > 0 || a2 > 0 || k > 0) ? 1u : 0u);
+#pragma unroll
+                        for (int k = 0; k < TC_BK / 16; ++k)
+                            mma_bf16_pair(dt, sdesc(aa + 32 * k), sdesc(bl + 32 * k), idesc, 1u);
+                    }
+                    mma_commit_pair(&empty_[s]);
+                }
+                if (!ok) break;
+                mma_commit_pair(&acc_full[a]);
+                ++ti;
+            }
+            mma_commit_pair(&mma_done);  // arrives in both CTAs when every MMA above is complete
+        }
+    } else if (warp < 6) {
+        // ---- one-hot producers: thread p writes row p of X (this CTA's
+        // 128 sequences) for each K atom of a stage
+        const int p = threadIdx.x - 64;
+        long long kit = 0;
+        bool ok = true;
+        for (int t = pair; t < ntiles && ok; t += npairs) {
+            int fi, ptb, tr;
+            lp_tile(P.b, t, S::SITES, fi, ptb, tr);
+            const FamDesc &F = P.b.f[fi];
+            if (!sites_active(F, tr * S::SITES, tr * S::SITES + S::SITES - 1)) continue;
+            const int b = (2 * ptb + (int)rank) * TC_M + p;
+            const bool valid = b < F.B;
+            const int8_t *srow = F.msa + (size_t)(valid ? b : 0) * F.N;
+            const int NA = F.KP / TC_BK, NQ = F.N * Q, N = F.N;
+            for (int ka = 0; ka < NA; ka += LP_ATOMS, ++kit) {
+                const int na = NA - ka < LP_ATOMS ? NA - ka : LP_ATOMS;
+                const int s = (int)(kit % NST);
+                const long long n = kit / NST;
+                // states of the (at most 8) positions the stage's columns touch,
+                // read before the wait so the loads overlap it
+                const int i_lo = (ka * TC_BK) / Q;
+                int st8[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int i = i_lo + u;
+                    st8[u] = (valid && i < N) ? (int)srow[i] : 0;
+                }
+                const bool got = n == 0 || mbar_wait(&empty_[s], (uint32_t)((n - 1) & 1), &abort_sh,
+                                                     err, ERR_TIMEOUT_PROD);
+                if (!__all_sync(0xffffffffu, got)) {
+                    ok = false;
+                    break;
+                }
+                for (int a = 0; a < na; ++a) {
+                    uint8_t *rowp = smem + s * S::STAGE + a * S::A_ATOM + p * 128;
+                    const uint4 z = make_uint4(0, 0, 0, 0);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) *(uint4 *)(rowp + ((j + p) & 7) * 16) = z;
+                    if (valid) {
+                        const int c0 = (ka + a) * TC_BK;
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            const int i = i_lo + u;
+                            const int pos = i * Q + st8[u] - c0;
+                            if (i < N && pos >= 0 && pos < TC_BK)
+                                *(uint16_t *)(rowp + ((((pos >> 3) ^ (p & 7)) << 4) | ((pos & 7) << 1))) =
+                                    0x3F80;
+                        }
+                        const int pf = NQ - c0;  // the field column: feature 1
+                        if (pf >= 0 && pf < TC_BK)
+                            *(uint16_t *)(rowp + ((((pf >> 3) ^ (p & 7)) << 4) | ((pf & 7) << 1))) =
+                                0x3F80;
+                    }
+                }
+                fence_proxy_async();
+                __syncwarp();
+                if (lane == 0) mbar_arrive_cluster(cluster_addr(&full_[s], 0));
+            }
+        }
+    } else {
+        // ---- epilogue: one sequence per thread (its tensor-memory lane);
+        // group g takes the sites of B half g (columns g NH + 21 j)
+        const int q4 = warp & 3;
+        const int g = (warp - 6) >> 2;
+        const int er = q4 * 32 + lane;
+        int ti = 0;
+        for (int t = pair; t < ntiles; t += npairs) {
+            int fi, ptb, tr;
+            lp_tile(P.b, t, S::SITES, fi, ptb, tr);
+            const FamDesc &F = P.b.f[fi];
+            const int r0 = tr * S::SITES;
+            if (!sites_active(F, r0, r0 + S::SITES - 1)) continue;
+            const int a = ti & 1, use = ti >> 1;
+            const int tb = 2 * ptb + (int)rank;    // this CTA's 128-sequence tile
+            const bool tile_ok = tb < F.BP / TC_M;  // the last pair may have one tile
+            const int BP = F.BP;
+            const int eb = tb * TC_M + er;
+            const bool ev = tile_ok && eb < F.B;
+            const float wb = ev ? F.w[eb] : 0.0f;
+            const float scale = (float)((double)wb * F.inv_beff);
+            int sr[SH];
+#pragma unroll
+            for (int j = 0; j < SH; ++j) {
+                const int r = r0 + g * SH + j;
+                sr[j] = (tile_ok && r < F.N) ? (int)F.msaT[(size_t)r * BP + eb] : -1;
+            }
+            const bool ok = mbar_wait(&acc_full[a], (uint32_t)(use & 1), &abort_sh, err, ERR_TIMEOUT_EPI);
+            tc_fence_after();
+            const uint32_t tl = tmem + a * TMEM_COLS + ((uint32_t)(q4 * 32) << 16);
+#pragma unroll
+            for (int j = 0; j < SH; ++j) {
+                const int jj = g * SH + j;         // site within the tile
+                const int r = r0 + jj;
+                const int cl = 21 * j;             // column within the half
+                const int ws = cl & ~7, o = cl & 7;
+                float l[32];
+                tmem_ld16(tl + g * S::NH + ws, l);
+                if (o + Q > 24) tmem_ld16(tl + g * S::NH + ws + 16, l + 16);
+                else tmem_ld8(tl + g * S::NH + ws + 16, l + 16);
+                tmem_wait_ld();
+                if (j == SH - 1) {
+                    // this warp's last tensor-memory read of the tile
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive_cluster(cluster_addr(&acc_empty[a], 0));
+                }
+                const int srv = sr[j];
+                const bool live = ev && r < F.N && ok;
+                float mx = l[o];
+#pragma unroll
+                for (int s2 = 1; s2 < Q; ++s2) mx = fmaxf(mx, l[o + s2]);
+                float z = 0.0f, lsr = 0.0f;
+#pragma unroll
+                for (int s2 = 0; s2 < Q; ++s2) {
+                    if (s2 == srv) lsr = l[o + s2];
+                    l[o + s2] = __expf(l[o + s2] - mx);
+                    z += l[o + s2];
+                }
+                const float lse = mx + __logf(z);
+                const float iz = __fdividef(1.0f, z);
+                const double c = warp_sum_pair(live ? wb * (lsr - lse) : 0.0f);
+                if (lane == 0) red[q4][jj] = c;
+                if (ok && tile_ok && r < F.N) {
+                    // the residual's rows of this site (the QP - Q padding rows
+                    // only feed gradient rows that the gradient kernel zeroes,
+                    // so they are not written)
+                    __nv_bfloat16 *dh = F.dt_hi + (size_t)(r * QP) * BP + eb;
+                    __nv_bfloat16 *dl = F.dt_lo + (size_t)(r * QP) * BP + eb;
+#pragma unroll
+                    for (int s2 = 0; s2 < Q; ++s2) {
+                        float dv = 0.0f;
+                        if (ev) dv = scale * (l[o + s2] * iz - (s2 == srv ? 1.0f : 0.0f));
+                        const __nv_bfloat16 hi = __float2bfloat16_rn(dv);
+                        dh[(size_t)s2 * BP] = hi;
+                        dl[(size_t)s2 * BP] = __float2bfloat16_rn(dv - __bfloat162float(hi));
+                    }
+                }
+            }
+            epi_bar_all();
+            const int t256 = threadIdx.x - 192;
+            if (t256 < S::SITES && r0 + t256 < F.N && ok && tile_ok)
+                F.partial[(size_t)tb * F.N + r0 + t256] =
+                    ((red[0][t256] + red[1][t256]) + red[2][t256]) + red[3][t256];
+            epi_bar_all();
+            ++ti;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1 && lane == 0) mbar_drain(&mma_done, 0);  // every MMA into this CTA's memory
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync_all();  // no arrival or copy of either CTA is still in flight
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc_pair(tmem, 2 * TMEM_COLS);
+    }
+    cluster_sync_all();
+}
+
 // ---------------------------------------------------------------- gradient
 // One 128 x ncols tile per CTA (measured faster here than a persistent
 // variant: with ~1.5 tiles per SM there is little epilogue to overlap, and
@@ -926,6 +1341,23 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
     return fn;
 }
 
+// 3-D bf16 map over the split Theta [N][QP][KP] that skips the padding
+// rows: dims (KP, Q states, N sites), box (64, Q, sh) lands as sh x Q rows
+// of 128 bytes, 128-byte swizzled
+bool make_map_sites(CUtensorMap *m, const void *base, uint64_t KP, uint64_t N, uint32_t sh)
+{
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[3] = {KP, (cuuint64_t)Q, N};
+    cuuint64_t strides[2] = {KP * 2, (cuuint64_t)QP * KP * 2};
+    cuuint32_t box[3] = {(cuuint32_t)TC_BK, (cuuint32_t)Q, sh};
+    cuuint32_t es[3] = {1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides,
+              box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
+
 // 2D bf16 map over a row-major [outer][inner] array, 128-byte swizzled boxes
 bool make_map(CUtensorMap *m, const void *base, uint64_t inner, uint64_t outer,
               uint32_t box_inner, uint32_t box_outer)
@@ -1029,9 +1461,67 @@ int num_sms()
 
 bool tc_config_valid(const TcConfig &c)
 {
-    return c.lg_sites >= 2 && c.lg_sites <= MAX_LG_SITES && c.lg_sites % 2 == 0 &&
-           c.gr_ncols >= 32 && c.gr_ncols <= 256 && c.gr_ncols % 32 == 0 &&
+    const bool lg = c.lg_pair ? ((c.lg_pair == 1 || c.lg_pair == 2) &&
+                                 (c.lg_sites == 4 || c.lg_sites == 8 || c.lg_sites == 12))
+                              : (c.lg_sites >= 2 && c.lg_sites <= MAX_LG_SITES && c.lg_sites % 2 == 0);
+    return lg && c.gr_ncols >= 32 && c.gr_ncols <= 256 && c.gr_ncols % 32 == 0 &&
            (c.gr_rows == TC_M || c.gr_rows == 2 * TC_M);
+}
+
+// resident 2-CTA clusters of the pair kernel on this device (cached)
+template <int SH, int ATOMS>
+int pair_clusters(int smem)
+{
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::atomic<int> &c = cache[dev & 63];
+    int n = c.load();
+    if (!n) {
+        cudaLaunchConfig_t lc = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 2;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        lc.gridDim = dim3(2 * 256);
+        lc.blockDim = dim3(LP_THREADS);
+        lc.dynamicSmemBytes = smem;
+        lc.attrs = at;
+        lc.numAttrs = 1;
+        if (cudaOccupancyMaxActiveClusters(&n, k_tc_logits_pair<SH, ATOMS>, &lc) != cudaSuccess || n <= 0) {
+            cudaGetLastError();
+            n = num_sms() / 2;
+        }
+        c.store(n);
+    }
+    return n;
+}
+
+template <int SH, int ATOMS>
+cudaError_t launch_logits_pair(PairParams &pp, int ntiles, int *err, cudaStream_t st)
+{
+    static std::atomic<unsigned long long> attr{0};
+    pp.stage_bytes = PairShape<SH, ATOMS>::STAGE;
+    pp.stages = tc_stages(pp.stage_bytes, 0);
+    const int smem = pp.stages * pp.stage_bytes + 1024;
+    cudaError_t e = set_smem_limit_once((const void *)k_tc_logits_pair<SH, ATOMS>, smem, attr);
+    if (e) return e;
+    const int clusters = std::min(ntiles, pair_clusters<SH, ATOMS>(smem));
+    if (clusters <= 0) return cudaSuccess;
+    cudaLaunchConfig_t lc = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    lc.gridDim = dim3(2 * clusters);
+    lc.blockDim = dim3(LP_THREADS);
+    lc.dynamicSmemBytes = smem;
+    lc.stream = st;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    return cudaLaunchKernelEx(&lc, k_tc_logits_pair<SH, ATOMS>, (const PairParams)pp, err);
 }
 
 cudaError_t launch_tc_eval(void *prof, const TcBatch &b_in, const TcConfig &cfg, double lambda_h,
@@ -1049,6 +1539,7 @@ cudaError_t launch_tc_eval(void *prof, const TcBatch &b_in, const TcConfig &cfg,
     // different threads do not share them
     thread_local LogitsParams lp;
     thread_local GradParams gp;
+    thread_local PairParams pp;
     lp.b = b_in;
     const int lg_ncols = cfg.lg_sites * QP;
     int tl = 0, tg = 0;
@@ -1056,7 +1547,8 @@ cudaError_t launch_tc_eval(void *prof, const TcBatch &b_in, const TcConfig &cfg,
         FamDesc &F = lp.b.f[i];
         F.tile0_logits = tl;
         F.tile0_grad = tg;
-        tl += (F.BP / TC_M) * ((F.N + cfg.lg_sites - 1) / cfg.lg_sites);
+        const int nbt = cfg.lg_pair ? (F.BP / TC_M + 1) / 2 : F.BP / TC_M;
+        tl += nbt * ((F.N + cfg.lg_sites - 1) / cfg.lg_sites);
         tg += ((F.KP + cfg.gr_ncols - 1) / cfg.gr_ncols) * ((F.R + cfg.gr_rows - 1) / cfg.gr_rows);
     }
     lp.b.ntiles_logits = tl;
@@ -1070,19 +1562,36 @@ cudaError_t launch_tc_eval(void *prof, const TcBatch &b_in, const TcConfig &cfg,
     gp.ncols = cfg.gr_ncols;
     gp.stage_bytes = 2 * (cfg.gr_rows / TC_M) * GR_A_BYTES + cfg.gr_ncols * TC_BK * 2;
     gp.stages = tc_stages(gp.stage_bytes, 0);
+    const int sh = cfg.lg_sites / 2;
     for (int i = 0; i < lp.b.nfam; ++i) {
         const FamDesc &F = lp.b.f[i];
-        if (!make_map(&lp.hi[i], F.th_hi, F.KP, F.R, TC_BK, lg_ncols) ||
-            !make_map(&lp.lo[i], F.th_lo, F.KP, F.R, TC_BK, lg_ncols) ||
-            !make_map(&gp.dhi[i], F.dt_hi, F.BP, F.R, TC_BK, cfg.gr_rows) ||
+        const bool lg_ok =
+            cfg.lg_pair ? (make_map_sites(&pp.hi[i], F.th_hi, F.KP, F.N, sh) &&
+                           make_map_sites(&pp.lo[i], F.th_lo, F.KP, F.N, sh))
+                        : (make_map(&lp.hi[i], F.th_hi, F.KP, F.R, TC_BK, lg_ncols) &&
+                           make_map(&lp.lo[i], F.th_lo, F.KP, F.R, TC_BK, lg_ncols));
+        if (!lg_ok || !make_map(&gp.dhi[i], F.dt_hi, F.BP, F.R, TC_BK, cfg.gr_rows) ||
             !make_map(&gp.dlo[i], F.dt_lo, F.BP, F.R, TC_BK, cfg.gr_rows))
             return cudaErrorInvalidValue;
     }
     if (which & 1) {
         void *t0 = prof ? prof_start(prof) : nullptr;
-        const int grid = std::min(tl, num_sms());
-        if (grid > 0)
-            k_tc_logits<<<grid, LG_THREADS, lp.stages * lp.stage_bytes + 1024, st>>>(lp, err);
+        if (cfg.lg_pair) {
+            pp.b = lp.b;
+            cudaError_t e2 = cudaSuccess;
+            // lg_pair 1: stages of two K atoms; 2: stages of one atom (more stages)
+            if (sh == 2) e2 = cfg.lg_pair == 2 ? launch_logits_pair<2, 1>(pp, tl, err, st)
+                                               : launch_logits_pair<2, 2>(pp, tl, err, st);
+            else if (sh == 4) e2 = cfg.lg_pair == 2 ? launch_logits_pair<4, 1>(pp, tl, err, st)
+                                                    : launch_logits_pair<4, 2>(pp, tl, err, st);
+            else e2 = cfg.lg_pair == 2 ? launch_logits_pair<6, 1>(pp, tl, err, st)
+                                       : launch_logits_pair<6, 2>(pp, tl, err, st);
+            if (e2) return e2;
+        } else {
+            const int grid = std::min(tl, num_sms());
+            if (grid > 0)
+                k_tc_logits<<<grid, LG_THREADS, lp.stages * lp.stage_bytes + 1024, st>>>(lp, err);
+        }
         if (prof) prof_stop(prof, "tc_logits", t0);
         k_tc_finish<<<lp.b.nfam, 128, 0, st>>>(lp.b);
         count_launches(2);

@@ -519,15 +519,19 @@ plm_status autotune_tc(plm_ctx *ctx, Problem &P, int *tc_err)
     float tbest = 1e30f;
     if (laned && lane_bounds(N, best, P.tune_lanes).size() - 1 < (size_t)P.tune_lanes)
         best.lg_sites = 4;  // a default that splits
-    for (int sites : {4, 6, 8, 10}) {
+    // logits: single-CTA tiles of 4..10 sites, pair tiles of 8 or 12 sites
+    const int lg_cand[6][2] = {{4, 0}, {6, 0}, {8, 0}, {10, 0}, {8, 1}, {12, 1}};
+    for (const auto &lc : lg_cand) {
         TcConfig c = best;
-        c.lg_sites = sites;
+        c.lg_sites = lc[0];
+        c.lg_pair = lc[1];
         float t;
         plm_status s = time_it(c, 1, &t);
         if (s) return s;
         if (t < tbest) {
             tbest = t;
-            best.lg_sites = sites;
+            best.lg_sites = lc[0];
+            best.lg_pair = lc[1];
         }
     }
     tbest = 1e30f;
@@ -619,10 +623,12 @@ plm_status evaluate(plm_ctx *ctx, plm_precision prec, Problem &P, const float *w
             f0 += b.nfam;
         }
         if (!P.tc_tuned) {
-            // PLMDCA_TC_TILES="sites,cols[,rows]" forces a tile shape (tests, experiments)
+            // PLMDCA_TC_TILES="sites,cols[,rows[,pair]]" forces a tile shape (tests,
+            // experiments)
             const char *force = getenv("PLMDCA_TC_TILES");
             TcConfig fc;
-            if (force && sscanf(force, "%d,%d,%d", &fc.lg_sites, &fc.gr_ncols, &fc.gr_rows) >= 2 &&
+            if (force &&
+                sscanf(force, "%d,%d,%d,%d", &fc.lg_sites, &fc.gr_ncols, &fc.gr_rows, &fc.lg_pair) >= 2 &&
                 tc_config_valid(fc)) {
                 P.tc_cfg = fc;
                 P.tc_tuned = true;

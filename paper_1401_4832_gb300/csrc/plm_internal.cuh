@@ -316,10 +316,14 @@ cudaError_t launch_tc_prepare(TcBatch &b, void *const *scratch, cudaStream_t st)
 // 2..10) x 128 sequences; gradient tiles of `gr_rows` rows (128, or 256 as
 // two 128-row accumulators sharing each one-hot operand stage) x `gr_ncols`
 // columns (multiple of 32, <= 256)
+// lg_pair = 1 or 2: the logits on 2-CTA clusters (256 sequences per tile,
+// sites packed 21 columns apart, lg_sites = 4, 8 or 12), pipeline stages of
+// 128 (1) or 64 (2) of K
 struct TcConfig {
     int lg_sites = 8;
     int gr_ncols = 256;
     int gr_rows = 128;
+    int lg_pair = 0;
 };
 bool tc_config_valid(const TcConfig &c);
 // one bounded pipeline wait on a barrier nothing arrives on: ORs a timeout

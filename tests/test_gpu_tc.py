@@ -140,19 +140,61 @@ def test_tc_solve_tiny_identical_contacts(ctx):
     assert np.array_equal(top_g.cpu().numpy()[:len(top_o)], top_o)
 
 
-TILE_SHAPES = ([(s, 256, 128) for s in (2, 4, 6, 10)] + [(8, c, 128) for c in (32, 128, 160, 192, 224)]
-               + [(8, c, 256) for c in (32, 128, 224, 256)])
+TILE_SHAPES = ([(s, 256, 128, 0) for s in (2, 4, 6, 10)]
+               + [(8, c, 128, 0) for c in (32, 128, 160, 192, 224)]
+               + [(8, c, 256, 0) for c in (32, 128, 224, 256)]
+               + [(s, 256, 128, 1) for s in (4, 8, 12)])
 
 
-@pytest.mark.parametrize("sites,cols,rows", TILE_SHAPES)
-def test_tc_every_tile_shape(sites, cols, rows, monkeypatch):
+@pytest.mark.parametrize("sites,cols,rows,pair", TILE_SHAPES)
+def test_tc_every_tile_shape(sites, cols, rows, pair, monkeypatch):
     # every shape the autotuner may pick gives the same numbers (ragged in
     # both GEMM dimensions: N=37 -> 37 % sites != 0, K = 800 -> K % cols != 0,
     # R = 37 * 24 = 888 rows -> the last 256-row tile holds 120 real rows, so
-    # its second 128-row half is all padding)
+    # its second 128-row half is all padding); pair = 1: the logits on 2-CTA
+    # clusters
     from paper_1401_4832_gb300 import api
-    monkeypatch.setenv("PLMDCA_TC_TILES", f"{sites},{cols},{rows}")
+    monkeypatch.setenv("PLMDCA_TC_TILES", f"{sites},{cols},{rows},{pair}")
     S = synth.add_clusters(synth.small_random(37, 203, 4), 0.3, 4, max_redraw=0.1)
     h, J = _theta(37, 4, 0.2)
     with api.Context(0) as c:
         _compare(c, S, h, J)
+
+
+@pytest.mark.parametrize("sites", [4, 8, 12])
+@pytest.mark.parametrize("N,B", [(50, 300), (23, 129), (120, 5000)])
+def test_tc_pair_logits_ragged(sites, N, B, monkeypatch):
+    # 2-CTA logits tiles: an odd number of 128-sequence tiles (the last pair
+    # has one real tile: B = 300 -> 3 tiles, B = 129 -> 2 tiles of which the
+    # second holds one sequence), site groups ragged in N, and the family
+    # size; the same bars as every other tile shape
+    from paper_1401_4832_gb300 import api
+    monkeypatch.setenv("PLMDCA_TC_TILES", f"{sites},224,256,1")
+    if N == 120:
+        S = synth.protein_family().msa
+    else:
+        S = synth.add_clusters(synth.small_random(N, B, 6), 0.3, 6, max_redraw=0.1)
+    h, J = _theta(N, 7, 0.05 if N == 120 else 0.2)
+    with api.Context(0) as c:
+        _compare(c, S, h, J)
+
+
+def test_tc_pair_equals_single_cta_logits(monkeypatch):
+    # the pair tile and the single-CTA tile accumulate the same products in
+    # the same K order: the objective and the residual-driven gradient agree
+    # to FP32 rounding of the accumulation (the tensor core's order inside
+    # one instruction is its own), checked at 1e-6 relative
+    from paper_1401_4832_gb300 import api
+    S = synth.add_clusters(synth.small_random(61, 700, 8), 0.3, 8, max_redraw=0.1)
+    h, J = _theta(61, 8, 0.1)
+    m, w, w32, beff = oracle.reweight(S, 0.8)
+    out = {}
+    for pair in (0, 1):
+        monkeypatch.setenv("PLMDCA_TC_TILES", f"8,224,256,{pair}")
+        with api.Context(0) as c:
+            f, gh, gJ = api.plm_site_objective_grad(c, _dev(S), _dev(w32), beff, _dev(h), _dev(J),
+                                                    0.01, 0.01, "split_bf16")
+            out[pair] = (f.cpu().numpy(), gJ.cpu().numpy())
+    assert np.allclose(out[0][0], out[1][0], rtol=1e-6, atol=0)
+    g0, g1 = out[0][1], out[1][1]
+    assert np.max(np.abs(g0 - g1)) <= 1e-5 * np.max(np.abs(g0))
