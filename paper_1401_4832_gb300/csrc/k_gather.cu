@@ -290,7 +290,7 @@ int softmax_slices(const Dims &d)
     // enough CTAs to fill the GPU, each warp looping over >= 16 sequences
     int ycap = (d.B + 16 * SM_WARPS - 1) / (16 * SM_WARPS);
     int xs = (d.N + 31) / 32;
-    int y = (4 * 152 + xs - 1) / xs;
+    int y = (4 * num_sms() + xs - 1) / xs;
     if (y > ycap) y = ycap;
     if (y < 1) y = 1;
     return y;

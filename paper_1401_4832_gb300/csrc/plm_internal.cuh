@@ -326,6 +326,8 @@ struct TcConfig {
     int lg_pair = 0;
 };
 bool tc_config_valid(const TcConfig &c);
+// streaming multiprocessors of the current device (queried once per device)
+int num_sms();
 // one bounded pipeline wait on a barrier nothing arrives on: ORs a timeout
 // code into *err after the wait budget (~2 s) and returns normally
 cudaError_t launch_wait_selftest(int *err, cudaStream_t st);
