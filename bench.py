@@ -612,6 +612,20 @@ def main():
     tc_full = tc_full_evals(api, lib, ctx, stream, msa, flush, prec, reps=10)
     alu = measure_alu_peaks(lib, stream)
     per_kernel = kernel_rooflines(kern, tc_full, B, N, pk, pk_kind, alu)
+    if fp32_cmp is not None:
+        # the plain FP32 path's kernels on full evaluations, against the
+        # measured FP32 add rate (gathers) and HBM bandwidth (the softmax pass:
+        # logits read, residual written, B x 24N floats each)
+        f32 = tc_full_evals(api, lib, ctx, stream, msa, flush, "fp32", reps=5)
+        fr = kernel_rooflines({}, f32, B, N, pk, pk_kind, alu)
+        if "softmax_resid" in f32:
+            by = 2 * B * 24 * N * 4
+            ach = by / f32["softmax_resid"] / 1e9
+            fr["softmax_resid"] = {"bound": "hbm", "achieved": ach, "peak": pk.get("hbm_gbs", 6800.0),
+                                   "unit": "GB/s", "frac": ach / pk.get("hbm_gbs", 6800.0),
+                                   "launch_us_full_eval": f32["softmax_resid"] * 1e6}
+        fp32_cmp["kernel_rooflines"] = fr
+        fp32_cmp["s_per_full_eval"] = sum(f32.values())
     dom = max(kern, key=lambda k: kern[k][1]) if kern else None
     roof = None
     if dom:

@@ -14,9 +14,11 @@
 //
 // Gradient (Eq. g_gradJ2):  G[(r,s)][i*Q + k] = sum_b D[b][(r,s)] [S_bi == k]
 // A CTA owns 128 rows x 8 positions (one position per warp); each lane keeps
-// 21 x 4 accumulators in registers and, for every staged sequence, adds its
-// residuals to the accumulator of the observed state.  That state is the
-// same for all lanes of the warp, so the selection is a uniform branch.
+// 21 x 4 accumulators in registers.  Residual tiles of 32 sequences are
+// staged by cp.async into two shared buffers; for each state k the warp
+// takes the mask of the tile's sequences showing k at its position (a
+// ballot, the same for all lanes) and adds their residual rows to the
+// state's accumulators in sequence order.
 #include "plm_device.cuh"
 #include "plm_internal.cuh"
 
@@ -173,16 +175,24 @@ __global__ void k_finish_objective(const double *__restrict__ partial,
 
 constexpr int GG_ROWS = 128;
 constexpr int GG_IC = 8;     // positions per CTA (one per warp)
-constexpr int GG_BT = 64;    // sequences per staged tile
+constexpr int GG_BT = 32;    // sequences per staged tile (two tiles in flight)
 
-#define GG_CASE(K)                 \
-    case K:                        \
-        acc[K][0] += v0;           \
-        acc[K][1] += v1;           \
-        acc[K][2] += v2;           \
-        acc[K][3] += v3;           \
-        break;
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
 
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+template <int N_PENDING>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N_PENDING) : "memory"); }
+
+// Lane l of a warp owns rows row0 + 4l .. 4l + 3 (one float4 of a staged
+// residual row); the residual tiles (32 sequences x 128 rows) are staged by
+// cp.async into two buffers, so the next tile's loads overlap this one's sums.
 __global__ void __launch_bounds__(256)
 k_grad_gather(const int8_t *__restrict__ msa, const float *__restrict__ D,
               const float *__restrict__ theta, Dims d, double lambda_h,
@@ -195,14 +205,32 @@ k_grad_gather(const int8_t *__restrict__ msa, const float *__restrict__ D,
             any |= active[r] != 0;
         if (!any) return;
     }
-    __shared__ float ds[GG_BT][GG_ROWS];
-    __shared__ int8_t ss[GG_BT][GG_IC];
+    __shared__ __align__(16) float ds[2][GG_BT][GG_ROWS];
+    __shared__ int8_t ss[2][GG_BT][GG_IC];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int row0 = blockIdx.x * GG_ROWS;
     const int i0 = blockIdx.y * GG_IC;
     const int i = i0 + warp;
     const int NQ = d.N * Q;
     const bool field_warp = (blockIdx.y == 0 && warp == 0);
+
+    // stage sequences b0 .. b0 + GG_BT - 1 into buffer `buf` (R is a multiple
+    // of 4 and row0 of 128, so a float4 is either wholly inside or outside)
+    auto stage = [&](int buf, int b0) {
+        for (int e = tid; e < GG_BT * GG_ROWS / 4; e += blockDim.x) {
+            const int bb = e / (GG_ROWS / 4), c4 = e % (GG_ROWS / 4);
+            const int b = b0 + bb, row = row0 + 4 * c4;
+            float *dst = &ds[buf][bb][4 * c4];
+            if (b < d.B && row < d.R) cp_async16(dst, D + (size_t)b * d.R + row);
+            else *(float4 *)dst = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        for (int e = tid; e < GG_BT * GG_IC; e += blockDim.x) {
+            const int ic = e % GG_IC, bb = e / GG_IC;
+            const int b = b0 + bb, ii = i0 + ic;
+            ss[buf][bb][ic] = (b < d.B && ii < d.N) ? msa[(size_t)b * d.N + ii] : 0;
+        }
+        cp_async_commit();
+    };
 
     float acc[Q][4];
 #pragma unroll
@@ -211,46 +239,55 @@ k_grad_gather(const int8_t *__restrict__ msa, const float *__restrict__ D,
         for (int j = 0; j < 4; ++j) acc[k][j] = 0.0f;
     float tot[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 
-    for (int b0 = 0; b0 < d.B; b0 += GG_BT) {
-        __syncthreads();
-        for (int e = tid; e < GG_BT * GG_ROWS; e += blockDim.x) {
-            int rr = e % GG_ROWS, bb = e / GG_ROWS;
-            int b = b0 + bb, row = row0 + rr;
-            ds[bb][rr] = (b < d.B && row < d.R) ? D[(size_t)b * d.R + row] : 0.0f;
-        }
-        for (int e = tid; e < GG_BT * GG_IC; e += blockDim.x) {
-            int ic = e % GG_IC, bb = e / GG_IC;
-            int b = b0 + bb, ii = i0 + ic;
-            ss[bb][ic] = (b < d.B && ii < d.N) ? msa[(size_t)b * d.N + ii] : 0;
+    stage(0, 0);
+    int buf = 0;
+    for (int b0 = 0; b0 < d.B; b0 += GG_BT, buf ^= 1) {
+        const bool more = b0 + GG_BT < d.B;
+        if (more) {
+            stage(buf ^ 1, b0 + GG_BT);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
         }
         __syncthreads();
         if (i < d.N) {
-            for (int bb = 0; bb < GG_BT; ++bb) {
-                const float v0 = ds[bb][lane], v1 = ds[bb][lane + 32];
-                const float v2 = ds[bb][lane + 64], v3 = ds[bb][lane + 96];
-                if (field_warp) {
-                    tot[0] += v0;
-                    tot[1] += v1;
-                    tot[2] += v2;
-                    tot[3] += v3;
+            if (field_warp) {
+#pragma unroll 4
+                for (int bb = 0; bb < GG_BT; ++bb) {
+                    const float4 v = *(const float4 *)&ds[buf][bb][4 * lane];
+                    tot[0] += v.x;
+                    tot[1] += v.y;
+                    tot[2] += v.z;
+                    tot[3] += v.w;
                 }
-                switch (ss[bb][warp]) {
-                    GG_CASE(0) GG_CASE(1) GG_CASE(2) GG_CASE(3) GG_CASE(4)
-                    GG_CASE(5) GG_CASE(6) GG_CASE(7) GG_CASE(8) GG_CASE(9)
-                    GG_CASE(10) GG_CASE(11) GG_CASE(12) GG_CASE(13) GG_CASE(14)
-                    GG_CASE(15) GG_CASE(16) GG_CASE(17) GG_CASE(18) GG_CASE(19)
-                    GG_CASE(20)
-                    default: break;
+            }
+            // lane l holds the state of staged sequence l at this warp's
+            // position; for each state the warp visits, in sequence order,
+            // the sequences that show it (a uniform mask, no branch per
+            // sequence) and adds their residual rows to that state's sums
+            const int st = ss[buf][lane][warp];
+#pragma unroll
+            for (int k = 0; k < Q; ++k) {
+                unsigned mask = __ballot_sync(0xffffffffu, st == k);
+                while (mask) {
+                    const int bb = __ffs(mask) - 1;
+                    mask &= mask - 1;
+                    const float4 v = *(const float4 *)&ds[buf][bb][4 * lane];
+                    acc[k][0] += v.x;
+                    acc[k][1] += v.y;
+                    acc[k][2] += v.z;
+                    acc[k][3] += v.w;
                 }
             }
         }
+        __syncthreads();  // the buffer is restaged two tiles on
     }
     // epilogue: add the penalty gradient 2 lambda theta; the diagonal block,
     // padding rows and padding columns are zero
     const float two_lj = (float)(2.0 * lambda_Jp), two_lh = (float)(2.0 * lambda_h);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        const int row = row0 + lane + 32 * j;
+        const int row = row0 + 4 * lane + j;
         if (row >= d.R) continue;
         const int r = row / QP, s = row % QP;
         const float *th = theta + (size_t)row * d.KP;
@@ -268,7 +305,6 @@ k_grad_gather(const int8_t *__restrict__ msa, const float *__restrict__ D,
             for (int c = NQ + warp; c < d.KP; c += 7) g[c] = 0.0f;
     }
 }
-#undef GG_CASE
 
 }  // namespace
 
