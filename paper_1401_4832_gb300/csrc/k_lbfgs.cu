@@ -100,6 +100,9 @@ __device__ __forceinline__ double lane_chunk_sum(const double *part, const SiteI
 {
     const double *q = part + (size_t)si.chunk0 * LB_PART + k;
     double t = 0.0;
+    // unrolled so that the independent loads are in flight together; the
+    // additions keep the chunk order
+#pragma unroll 8
     for (int c = 0; c < si.nchunks; ++c) t += q[(size_t)c * LB_PART];
     return t;
 }
