@@ -1267,6 +1267,276 @@ k_tc_grad(const __grid_constant__ GradParams P, float two_lh, float two_lj, int 
     }
 }
 
+// ---------------------------------------------------------------- gradient, CTA pair
+// The gradient on 2-CTA clusters: one MMA instruction computes 256 rows
+// (128 per CTA, each CTA's own D^T rows by TMA into its own accumulator) x
+// ncols columns, each CTA building the one-hot X^T rows of half of the
+// columns.  A stage holds 128 of K (two 64-wide atoms).  Roles: warp 0 TMA
+// (both CTAs, counted on the leader's barrier), warp 1 tensor memory (both)
+// and MMA issue (leader), warps 2-9 one-hot producers (thread p: column
+// p % 128 of this CTA's half, K atom p / 128 of each stage), then the
+// epilogue of this CTA's 128 rows.
+__device__ __forceinline__ void tma_load_2d_pair(void *dst, const CUtensorMap *map, uint32_t bar_cl,
+                                                 int x, int y)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar_cl)
+        : "memory");
+}
+
+constexpr int GP_ATOMS = 2;  // K atoms of 64 per stage
+
+__global__ void __launch_bounds__(GR_THREADS, 1)
+k_tc_grad_pair(const __grid_constant__ GradParams P, float two_lh, float two_lj, int *__restrict__ err)
+{
+    const int pair = blockIdx.x >> 1;
+    const uint32_t rank = cluster_rank();
+    const bool leader = rank == 0;
+    const int fi = family_of(P.b, pair, true);
+    const FamDesc &F = P.b.f[fi];
+    const CUtensorMap &tm_dhi = P.dhi[fi];
+    const CUtensorMap &tm_dlo = P.dlo[fi];
+    const int8_t *__restrict__ msaT = F.msaT;
+    const float *__restrict__ theta = F.theta;
+    float *__restrict__ G = F.G;
+    const int BP = F.BP;
+    Dims d;
+    d.B = F.B;
+    d.N = F.N;
+    d.KP = F.KP;
+    d.R = F.R;
+    d.K = F.N * Q + 1;
+    const int local = pair - F.tile0_grad;
+    const int GRN = P.ncols, NST = P.stages, GRSTAGE = P.stage_bytes;
+    const int HN = GRN / 2;                   // one-hot columns built by this CTA
+    const int A_BYTES = GR_A_BYTES;           // 128 rows x 64 of K, bf16
+    const int B_BYTES = HN * TC_BK * 2;
+    const int nct = (d.KP + GRN - 1) / GRN;
+    const int c0 = (local % nct) * GRN;
+    const int rs0 = (local / nct) * 2 * TC_M;  // first row of the pair tile
+    const int rh = rs0 + (int)rank * TC_M;     // first row of this CTA
+    if (F.active) {
+        // the same decision in both CTAs: any active site in the pair's rows
+        bool any = false;
+        for (int r = rs0 / QP; r <= (rs0 + 2 * TC_M - 1) / QP && r < F.N; ++r)
+            any |= F.active[r] != 0;
+        if (!any) return;
+    }
+    extern __shared__ uint8_t dsmem[];
+    uint8_t *smem = align1024(dsmem);
+    __shared__ __align__(8) uint64_t full_[MAX_STAGES], empty_[MAX_STAGES], acc_full;
+    __shared__ uint32_t tmem_sh;
+    __shared__ int abort_sh;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int NA = BP / TC_BK;
+    const int NQ = d.N * Q;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < MAX_STAGES; ++s) {
+            mbar_init(&full_[s], 1 + 2 * (GR_PROD / 32));  // leader's TMA + 8 producer warps per CTA
+            mbar_init(&empty_[s], 1);
+        }
+        mbar_init(&acc_full, 1);
+        abort_sh = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+    cluster_sync_all();
+    if (warp == 1) {
+        tmem_alloc_pair(&tmem_sh, TMEM_COLS);
+        tmem_relinquish_pair();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_sh;
+    // stage layout: A_hi a0 | A_lo a0 | A_hi a1 | A_lo a1 | B a0 | B a1
+    const int B_OFF = GP_ATOMS * 2 * A_BYTES;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int issued = 0;
+            for (int ks = 0; ks * GP_ATOMS < NA; ++ks) {
+                const int ka = ks * GP_ATOMS;
+                const int na = NA - ka < GP_ATOMS ? NA - ka : GP_ATOMS;
+                const int s = ks % NST, n = ks / NST;
+                if (n > 0 && !mbar_wait(&empty_[s], (n - 1) & 1, &abort_sh, err, ERR_TIMEOUT_TMA))
+                    break;
+                uint8_t *st = smem + s * GRSTAGE;
+                const uint32_t bar = cluster_addr(&full_[s], 0);
+                if (leader) mbar_expect_tx(&full_[s], 2 * na * 2 * A_BYTES);
+                for (int a = 0; a < na; ++a) {
+                    tma_load_2d_pair(st + 2 * a * A_BYTES, &tm_dhi, bar, (ka + a) * TC_BK, rh);
+                    tma_load_2d_pair(st + (2 * a + 1) * A_BYTES, &tm_dlo, bar, (ka + a) * TC_BK, rh);
+                }
+                issued = ks + 1;
+            }
+            if (leader)
+                for (int k = issued - NST < 0 ? 0 : issued - NST; k < issued; ++k)
+                    mbar_drain(&full_[k % NST], (k / NST) & 1);
+        }
+    } else if (warp == 1) {
+        if (lane == 0 && leader) {
+            const uint32_t idesc = idesc_bf16(2 * TC_M, GRN);
+            for (int ks = 0; ks * GP_ATOMS < NA; ++ks) {
+                const int ka = ks * GP_ATOMS;
+                const int na = NA - ka < GP_ATOMS ? NA - ka : GP_ATOMS;
+                const int s = ks % NST, n = ks / NST;
+                if (!mbar_wait(&full_[s], n & 1, &abort_sh, err, ERR_TIMEOUT_MMA)) break;
+                tc_fence_after();
+                uint8_t *st = smem + s * GRSTAGE;
+                for (int a = 0; a < na; ++a) {
+                    const uint32_t ah = smem_u32(st + 2 * a * A_BYTES);
+                    const uint32_t al = smem_u32(st + (2 * a + 1) * A_BYTES);
+                    const uint32_t bx = smem_u32(st + B_OFF + a * B_BYTES);
+#pragma unroll
+                    for (int k = 0; k < TC_BK / 16; ++k)
+                        mma_bf16_pair(tmem, sdesc(ah + 32 * k), sdesc(bx + 32 * k), idesc,
+                                      (ka > 0 || a > 0 || k > 0) ? 1u : 0u);
+#pragma unroll
+                    for (int k = 0; k < TC_BK / 16; ++k)
+                        mma_bf16_pair(tmem, sdesc(al + 32 * k), sdesc(bx + 32 * k), idesc, 1u);
+                }
+                mma_commit_pair(&empty_[s]);
+            }
+            mma_commit_pair(&acc_full);  // arrives in both CTAs when every MMA above is complete
+        }
+    } else {
+        // ---- one-hot X^T producer: thread p writes row p % 128 of this
+        // CTA's column half for K atom p / 128 of every stage
+        const int p = threadIdx.x - 64;
+        const int prow = p % TC_M, pa = p / TC_M;
+        const int c = c0 + (int)rank * HN + prow;
+        int src_i = 0;
+        uint32_t kk = 0xFFu;  // never equals a stored state (0..20, or 0x7F padding)
+        if (c < NQ) {
+            src_i = c / Q;
+            kk = (uint32_t)(c % Q);
+        } else if (c == NQ) {
+            src_i = d.N;  // the all-ones row of msaT
+            kk = 0;
+        }
+        kk *= 0x01010101u;
+        const bool has_row = prow < HN;
+        const uint4 *srcT = (const uint4 *)(msaT + (size_t)src_i * BP);
+        // this thread's atom of the first stage, fetched ahead
+        uint4 cur[4], nxt[4];
+        {
+            const int ka0 = pa < NA ? pa : 0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) cur[q] = __ldg(srcT + (size_t)ka0 * (TC_BK / 16) + q);
+        }
+        for (int ks = 0; ks * GP_ATOMS < NA; ++ks) {
+            const int ka = ks * GP_ATOMS;
+            const int na = NA - ka < GP_ATOMS ? NA - ka : GP_ATOMS;
+            const int s = ks % NST, n = ks / NST;
+            // the next stage's bytes for this thread's atom
+            const int kn = ka + GP_ATOMS + pa < NA ? ka + GP_ATOMS + pa : (ka + pa < NA ? ka + pa : 0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) nxt[q] = __ldg(srcT + (size_t)kn * (TC_BK / 16) + q);
+            const bool got = n == 0 || mbar_wait(&empty_[s], (n - 1) & 1, &abort_sh, err,
+                                                 ERR_TIMEOUT_PROD);
+            if (!__all_sync(0xffffffffu, got)) break;
+            if (has_row && pa < na) {
+                uint8_t *bt = smem + s * GRSTAGE + B_OFF + pa * B_BYTES;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {  // 16 sequences per word group
+                    const uint4 x = cur[q];
+                    const uint32_t xs[4] = {x.x, x.y, x.z, x.w};
+                    uint32_t o[8];
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const uint32_t m = __vcmpeq4(xs[t], kk);
+                        o[2 * t] = __byte_perm(m, 0, 0x1100) & 0x3F803F80u;
+                        o[2 * t + 1] = __byte_perm(m, 0, 0x3322) & 0x3F803F80u;
+                    }
+                    *(uint4 *)(bt + swz(prow, 2 * q)) = make_uint4(o[0], o[1], o[2], o[3]);
+                    *(uint4 *)(bt + swz(prow, 2 * q + 1)) = make_uint4(o[4], o[5], o[6], o[7]);
+                }
+            }
+            fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) mbar_arrive_cluster(cluster_addr(&full_[s], 0));
+#pragma unroll
+            for (int q = 0; q < 4; ++q) cur[q] = nxt[q];
+        }
+
+        // ---- epilogue: TMEM -> shared (rows padded to GRN + 4 floats), then
+        // a coalesced pass adds 2 lambda Theta, applies the masks and writes G
+        const int q4 = warp & 3;
+        const int half = (warp - 2) >> 2;  // column half of the tile
+        const int trow = q4 * 32 + lane;
+        const bool ok = mbar_wait(&acc_full, 0, &abort_sh, err, ERR_TIMEOUT_EPI);
+        tc_fence_after();
+        const int GS = GRN + 4;
+        float *acc_s = (float *)smem;  // [128][GS]: the pipeline stages are free now
+        const int ng = GRN / 32;
+        const uint32_t tl = tmem + ((uint32_t)(q4 * 32) << 16);
+#pragma unroll 1
+        for (int cc = half * ng; cc < (half + 1) * ng; ++cc) {
+            float v[16];
+            tmem_ld16(tl + cc * 16, v);
+            tmem_wait_ld();
+            float4 *dst = (float4 *)(acc_s + trow * GS + cc * 16);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        }
+        epi_bar256();
+        const int t = threadIdx.x - 64;
+        constexpr int UNR = 4;
+        for (int e0 = t; e0 < TC_M * (GRN / 4); e0 += GR_PROD * UNR) {
+            float4 th[UNR];
+            bool live[UNR];
+#pragma unroll
+            for (int k = 0; k < UNR; ++k) {  // issue all loads first
+                const int e = e0 + GR_PROD * k;
+                const int rr = e / (GRN / 4), c4 = e % (GRN / 4);
+                const int row = rh + rr, cb = c0 + 4 * c4;
+                live[k] = ok && e < TC_M * (GRN / 4) && row < d.R && cb < d.KP;
+                th[k] = live[k] ? *(const float4 *)(theta + (size_t)row * d.KP + cb)
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int k = 0; k < UNR; ++k) {
+                if (!live[k]) continue;
+                const int e = e0 + GR_PROD * k;
+                const int rr = e / (GRN / 4), c4 = e % (GRN / 4);
+                const int row = rh + rr, cb = c0 + 4 * c4;
+                const int r = row / QP, sstate = row % QP;
+                const float4 a = *(const float4 *)(acc_s + rr * GS + 4 * c4);
+                const float av[4] = {a.x, a.y, a.z, a.w};
+                const float tv[4] = {th[k].x, th[k].y, th[k].z, th[k].w};
+                float o[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int cu = cb + u;
+                    float val;
+                    if (sstate >= Q || cu > NQ || (cu >= r * Q && cu < r * Q + Q)) val = 0.0f;
+                    else if (cu == NQ) val = av[u] + two_lh * tv[u];
+                    else val = av[u] + two_lj * tv[u];
+                    o[u] = val;
+                }
+                *(float4 *)(G + (size_t)row * d.KP + cb) = make_float4(o[0], o[1], o[2], o[3]);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1 && lane == 0) mbar_drain(&acc_full, 0);  // every MMA into this CTA's memory
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync_all();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc_pair(tmem, TMEM_COLS);
+    }
+    cluster_sync_all();
+}
+
 // ---------------------------------------------------------------- self-test
 // The bounded wait of the pipelines above on a barrier that nothing
 // arrives on: it gives up after its cycle budget, raises the CTA's abort
@@ -1465,7 +1735,31 @@ bool tc_config_valid(const TcConfig &c)
                                  (c.lg_sites == 4 || c.lg_sites == 8 || c.lg_sites == 12))
                               : (c.lg_sites >= 2 && c.lg_sites <= MAX_LG_SITES && c.lg_sites % 2 == 0);
     return lg && c.gr_ncols >= 32 && c.gr_ncols <= 256 && c.gr_ncols % 32 == 0 &&
-           (c.gr_rows == TC_M || c.gr_rows == 2 * TC_M);
+           (c.gr_rows == TC_M || c.gr_rows == 2 * TC_M) &&
+           (c.gr_pair == 0 || (c.gr_pair == 1 && c.gr_rows == 2 * TC_M));
+}
+
+cudaError_t launch_grad_pair(const GradParams &gp, int ntiles, float two_lh, float two_lj, int *err,
+                             cudaStream_t st)
+{
+    static std::atomic<unsigned long long> attr{0};
+    const int smem = gp.stages * gp.stage_bytes + 1024;
+    cudaError_t e = set_smem_limit_once((const void *)k_tc_grad_pair, smem, attr);
+    if (e) return e;
+    if (ntiles <= 0) return cudaSuccess;
+    cudaLaunchConfig_t lc = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    lc.gridDim = dim3(2 * ntiles);
+    lc.blockDim = dim3(GR_THREADS);
+    lc.dynamicSmemBytes = smem;
+    lc.stream = st;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    return cudaLaunchKernelEx(&lc, k_tc_grad_pair, gp, two_lh, two_lj, err);
 }
 
 // resident 2-CTA clusters of the pair kernel on this device (cached)
@@ -1560,7 +1854,10 @@ cudaError_t launch_tc_eval(void *prof, const TcBatch &b_in, const TcConfig &cfg,
     lp.stages = tc_stages(lp.stage_bytes, 0);
     gp.rows = cfg.gr_rows;
     gp.ncols = cfg.gr_ncols;
-    gp.stage_bytes = 2 * (cfg.gr_rows / TC_M) * GR_A_BYTES + cfg.gr_ncols * TC_BK * 2;
+    if (cfg.gr_pair)  // two K atoms per stage: D^T hi/lo of 128 rows and half the columns each
+        gp.stage_bytes = GP_ATOMS * (2 * GR_A_BYTES + (cfg.gr_ncols / 2) * TC_BK * 2);
+    else
+        gp.stage_bytes = 2 * (cfg.gr_rows / TC_M) * GR_A_BYTES + cfg.gr_ncols * TC_BK * 2;
     gp.stages = tc_stages(gp.stage_bytes, 0);
     const int sh = cfg.lg_sites / 2;
     for (int i = 0; i < lp.b.nfam; ++i) {
@@ -1570,8 +1867,9 @@ cudaError_t launch_tc_eval(void *prof, const TcBatch &b_in, const TcConfig &cfg,
                            make_map_sites(&pp.lo[i], F.th_lo, F.KP, F.N, sh))
                         : (make_map(&lp.hi[i], F.th_hi, F.KP, F.R, TC_BK, lg_ncols) &&
                            make_map(&lp.lo[i], F.th_lo, F.KP, F.R, TC_BK, lg_ncols));
-        if (!lg_ok || !make_map(&gp.dhi[i], F.dt_hi, F.BP, F.R, TC_BK, cfg.gr_rows) ||
-            !make_map(&gp.dlo[i], F.dt_lo, F.BP, F.R, TC_BK, cfg.gr_rows))
+        const int gbox = cfg.gr_pair ? TC_M : cfg.gr_rows;  // a pair's CTA loads 128 rows
+        if (!lg_ok || !make_map(&gp.dhi[i], F.dt_hi, F.BP, F.R, TC_BK, gbox) ||
+            !make_map(&gp.dlo[i], F.dt_lo, F.BP, F.R, TC_BK, gbox))
             return cudaErrorInvalidValue;
     }
     if (which & 1) {
@@ -1598,9 +1896,14 @@ cudaError_t launch_tc_eval(void *prof, const TcBatch &b_in, const TcConfig &cfg,
     }
     if (which & 2) {
         void *t1 = prof ? prof_start(prof) : nullptr;
-        if (tg > 0)
+        if (cfg.gr_pair) {
+            cudaError_t e3 = launch_grad_pair(gp, tg, (float)(2.0 * lambda_h),
+                                              (float)(2.0 * lambda_Jp), err, st);
+            if (e3) return e3;
+        } else if (tg > 0) {
             k_tc_grad<<<tg, GR_THREADS, gp.stages * gp.stage_bytes + 1024, st>>>(
                 gp, (float)(2.0 * lambda_h), (float)(2.0 * lambda_Jp), err);
+        }
         if (prof) prof_stop(prof, "tc_grad", t1);
         count_launches(1);
     }

@@ -535,17 +535,21 @@ plm_status autotune_tc(plm_ctx *ctx, Problem &P, int *tc_err)
         }
     }
     tbest = 1e30f;
-    for (int rows : {128, 256})
+    // gradient: 128- or 256-row single-CTA tiles, or 256-row tiles on CTA pairs
+    for (int shape : {0, 1, 2})
         for (int cols : {128, 160, 192, 224, 256}) {
+            if (shape == 2 && cols < 224) continue;  // pair tiles: two waves or more below 224
             TcConfig c = best;
-            c.gr_rows = rows;
+            c.gr_rows = shape == 0 ? 128 : 256;
+            c.gr_pair = shape == 2 ? 1 : 0;
             c.gr_ncols = cols;
             float t;
             plm_status s = time_it(c, 2, &t);
             if (s) return s;
             if (t < tbest) {
                 tbest = t;
-                best.gr_rows = rows;
+                best.gr_rows = c.gr_rows;
+                best.gr_pair = c.gr_pair;
                 best.gr_ncols = cols;
             }
         }
@@ -623,12 +627,13 @@ plm_status evaluate(plm_ctx *ctx, plm_precision prec, Problem &P, const float *w
             f0 += b.nfam;
         }
         if (!P.tc_tuned) {
-            // PLMDCA_TC_TILES="sites,cols[,rows[,pair]]" forces a tile shape (tests,
-            // experiments)
+            // PLMDCA_TC_TILES="sites,cols[,rows[,pair[,gradient pair]]]" forces a
+            // tile shape (tests, experiments)
             const char *force = getenv("PLMDCA_TC_TILES");
             TcConfig fc;
             if (force &&
-                sscanf(force, "%d,%d,%d,%d", &fc.lg_sites, &fc.gr_ncols, &fc.gr_rows, &fc.lg_pair) >= 2 &&
+                sscanf(force, "%d,%d,%d,%d,%d", &fc.lg_sites, &fc.gr_ncols, &fc.gr_rows, &fc.lg_pair,
+                       &fc.gr_pair) >= 2 &&
                 tc_config_valid(fc)) {
                 P.tc_cfg = fc;
                 P.tc_tuned = true;

@@ -319,11 +319,13 @@ cudaError_t launch_tc_prepare(TcBatch &b, void *const *scratch, cudaStream_t st)
 // lg_pair = 1 or 2: the logits on 2-CTA clusters (256 sequences per tile,
 // sites packed 21 columns apart, lg_sites = 4, 8 or 12), pipeline stages of
 // 128 (1) or 64 (2) of K
+// gr_pair = 1: the gradient on 2-CTA clusters (gr_rows = 256, 128 per CTA)
 struct TcConfig {
     int lg_sites = 8;
     int gr_ncols = 256;
     int gr_rows = 128;
     int lg_pair = 0;
+    int gr_pair = 0;
 };
 bool tc_config_valid(const TcConfig &c);
 // streaming multiprocessors of the current device (queried once per device)

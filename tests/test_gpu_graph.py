@@ -22,7 +22,7 @@ def test_graph_replay_equals_eager(prec):
     assert r1["n_converged"] == S.shape[1]
 
 
-@pytest.mark.parametrize("tiles", ["8,224", "8,224,256", "12,224,128,1"])
+@pytest.mark.parametrize("tiles", ["8,224", "8,224,256", "12,224,128,1", "12,224,256,1,1"])
 @pytest.mark.parametrize("which", ["family", "ragged"])
 def test_two_lane_pipeline_equals_one_lane(which, tiles, monkeypatch):
     # With graphs on, a one-family tensor-core solve runs in two lanes (two

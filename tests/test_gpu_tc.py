@@ -140,36 +140,37 @@ def test_tc_solve_tiny_identical_contacts(ctx):
     assert np.array_equal(top_g.cpu().numpy()[:len(top_o)], top_o)
 
 
-TILE_SHAPES = ([(s, 256, 128, 0) for s in (2, 4, 6, 10)]
-               + [(8, c, 128, 0) for c in (32, 128, 160, 192, 224)]
-               + [(8, c, 256, 0) for c in (32, 128, 224, 256)]
-               + [(s, 256, 128, 1) for s in (4, 8, 12)])
+TILE_SHAPES = ([(s, 256, 128, 0, 0) for s in (2, 4, 6, 10)]
+               + [(8, c, 128, 0, 0) for c in (32, 128, 160, 192, 224)]
+               + [(8, c, 256, 0, 0) for c in (32, 128, 224, 256)]
+               + [(s, 256, 128, 1, 0) for s in (4, 8, 12)]
+               + [(12, c, 256, 1, 1) for c in (128, 160, 192, 224, 256)])
 
 
-@pytest.mark.parametrize("sites,cols,rows,pair", TILE_SHAPES)
-def test_tc_every_tile_shape(sites, cols, rows, pair, monkeypatch):
+@pytest.mark.parametrize("sites,cols,rows,pair,gpair", TILE_SHAPES)
+def test_tc_every_tile_shape(sites, cols, rows, pair, gpair, monkeypatch):
     # every shape the autotuner may pick gives the same numbers (ragged in
     # both GEMM dimensions: N=37 -> 37 % sites != 0, K = 800 -> K % cols != 0,
     # R = 37 * 24 = 888 rows -> the last 256-row tile holds 120 real rows, so
     # its second 128-row half is all padding); pair = 1: the logits on 2-CTA
-    # clusters
+    # clusters, gpair = 1: the gradient on 2-CTA clusters
     from paper_1401_4832_gb300 import api
-    monkeypatch.setenv("PLMDCA_TC_TILES", f"{sites},{cols},{rows},{pair}")
+    monkeypatch.setenv("PLMDCA_TC_TILES", f"{sites},{cols},{rows},{pair},{gpair}")
     S = synth.add_clusters(synth.small_random(37, 203, 4), 0.3, 4, max_redraw=0.1)
     h, J = _theta(37, 4, 0.2)
     with api.Context(0) as c:
         _compare(c, S, h, J)
 
 
-@pytest.mark.parametrize("sites", [4, 8, 12])
+@pytest.mark.parametrize("sites,gpair", [(4, 0), (8, 0), (12, 0), (12, 1)])
 @pytest.mark.parametrize("N,B", [(50, 300), (23, 129), (120, 5000)])
-def test_tc_pair_logits_ragged(sites, N, B, monkeypatch):
+def test_tc_pair_logits_ragged(sites, gpair, N, B, monkeypatch):
     # 2-CTA logits tiles: an odd number of 128-sequence tiles (the last pair
     # has one real tile: B = 300 -> 3 tiles, B = 129 -> 2 tiles of which the
     # second holds one sequence), site groups ragged in N, and the family
     # size; the same bars as every other tile shape
     from paper_1401_4832_gb300 import api
-    monkeypatch.setenv("PLMDCA_TC_TILES", f"{sites},224,256,1")
+    monkeypatch.setenv("PLMDCA_TC_TILES", f"{sites},224,256,1,{gpair}")
     if N == 120:
         S = synth.protein_family().msa
     else:
