@@ -1744,7 +1744,8 @@ cudaError_t launch_grad_pair(const GradParams &gp, int ntiles, float two_lh, flo
 {
     static std::atomic<unsigned long long> attr{0};
     const int smem = gp.stages * gp.stage_bytes + 1024;
-    cudaError_t e = set_smem_limit_once((const void *)k_tc_grad_pair, smem, attr);
+    // the limit is raised once per device, to the largest any column width uses
+    cudaError_t e = set_smem_limit_once((const void *)k_tc_grad_pair, SMEM_BUDGET + 1024, attr);
     if (e) return e;
     if (ntiles <= 0) return cudaSuccess;
     cudaLaunchConfig_t lc = {};
@@ -1799,7 +1800,8 @@ cudaError_t launch_logits_pair(PairParams &pp, int ntiles, int *err, cudaStream_
     pp.stage_bytes = PairShape<SH, ATOMS>::STAGE;
     pp.stages = tc_stages(pp.stage_bytes, 0);
     const int smem = pp.stages * pp.stage_bytes + 1024;
-    cudaError_t e = set_smem_limit_once((const void *)k_tc_logits_pair<SH, ATOMS>, smem, attr);
+    cudaError_t e = set_smem_limit_once((const void *)k_tc_logits_pair<SH, ATOMS>, SMEM_BUDGET + 1024,
+                                        attr);
     if (e) return e;
     const int clusters = std::min(ntiles, pair_clusters<SH, ATOMS>(smem));
     if (clusters <= 0) return cudaSuccess;

@@ -199,3 +199,14 @@ def test_tc_pair_equals_single_cta_logits(monkeypatch):
     assert np.allclose(out[0][0], out[1][0], rtol=1e-6, atol=0)
     g0, g1 = out[0][1], out[1][1]
     assert np.max(np.abs(g0 - g1)) <= 1e-5 * np.max(np.abs(g0))
+
+
+def test_tc_autotuner_tries_every_shape_in_one_process():
+    # the tuner launches every candidate (single-CTA and pair logits, every
+    # gradient shape and width) in one process: each kernel's shared-memory
+    # limit must cover the largest of its shapes, whatever order they come in
+    from paper_1401_4832_gb300 import api
+    S = synth.add_clusters(synth.small_random(45, 900, 13), 0.3, 13, max_redraw=0.1)
+    h, J = _theta(45, 13, 0.1)
+    with api.Context(0) as c:
+        ef, eg = _compare(c, S, h, J)
