@@ -133,8 +133,10 @@ plm_status msa_reweight(plm_ctx *ctx, const int8_t *msa, int B, int N, int q,
  *   lambda_J the user's strength; lambda'_J = 0.5 lambda_J inside (step 1)
  *   prec     PLM_FP32_EXACT or PLM_SPLIT_BF16
  *   f_out    [N] double       out, per-site objective
- *   gh, gJ   out, same layouts as h and J (diagonal blocks zero)
- * Errors: PLM_EINVAL for shapes, beff <= 0, negative lambdas. */
+ *   gh, gJ   out, same layouts as h and J (diagonal blocks zero); both
+ *            NULL: the objective only (the gradient contraction is skipped)
+ * Errors: PLM_EINVAL for shapes, beff <= 0, negative lambdas, exactly one
+ * of gh, gJ NULL. */
 plm_status plm_site_objective_grad(plm_ctx *ctx, const int8_t *msa,
                                    const float *w, double beff, int B, int N,
                                    int q, const float *h, const float *J,

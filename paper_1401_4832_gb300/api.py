@@ -115,20 +115,22 @@ def msa_reweight(ctx: Context, msa, x: float = 0.8):
 
 def plm_site_objective_grad(ctx: Context, msa, w, beff: float, h, J,
                             lambda_h: float = 0.01, lambda_J: float = 0.01,
-                            prec: str = "fp32"):
+                            prec: str = "fp32", grad: bool = True):
     """Objective g_r^(reg) (Eq. g_regdef2) of every site and its gradient
-    (Eqs. g_gradh2, g_gradJ2) at (h, J); returns (f[N], gh[N,q], gJ[N,q,N,q])."""
+    (Eqs. g_gradh2, g_gradJ2) at (h, J); returns (f[N], gh[N,q], gJ[N,q,N,q]),
+    or (f, None, None) with grad=False (the gradient contraction skipped)."""
     msa = _as_input(msa, np.int8)
     B, N = msa.shape
     w = _as_input(w, np.float32)
     h = _as_input(h, np.float32)
     J = _as_input(J, np.float32)
     f = _like(msa, (N,), np.float64)
-    gh = _like(msa, (N, Q), np.float32)
-    gJ = _like(msa, (N, Q, N, Q), np.float32)
+    gh = _like(msa, (N, Q), np.float32) if grad else None
+    gJ = _like(msa, (N, Q, N, Q), np.float32) if grad else None
     ctx.check(ctx.lib.plm_site_objective_grad(
         ctx.handle, _ptr(msa), _ptr(w), float(beff), B, N, Q, _ptr(h), _ptr(J),
-        float(lambda_h), float(lambda_J), N_.PRECISIONS[prec], _ptr(f), _ptr(gh), _ptr(gJ)))
+        float(lambda_h), float(lambda_J), N_.PRECISIONS[prec], _ptr(f),
+        _ptr(gh) if grad else None, _ptr(gJ) if grad else None))
     return f, gh, gJ
 
 

@@ -568,7 +568,7 @@ plm_status autotune_tc(plm_ctx *ctx, Problem &P, int *tc_err)
 plm_status evaluate(plm_ctx *ctx, plm_precision prec, Problem &P, const float *w,
                     const float *theta, const __nv_bfloat16 *hi, const __nv_bfloat16 *lo,
                     double lambda_h, double lambda_Jp, double *f_data, float *G, int *tc_err,
-                    const uint8_t *active = nullptr, cudaStream_t on = nullptr)
+                    const uint8_t *active = nullptr, cudaStream_t on = nullptr, int which = 3)
 {
     cudaStream_t st = on ? on : ctx->stream;
     if (prec == PLM_FP32_EXACT) {
@@ -597,7 +597,7 @@ plm_status evaluate(plm_ctx *ctx, plm_precision prec, Problem &P, const float *w
                 CK(launch_finish_objective((double *)part, slices, d, F.beff, nullptr,
                                            f_data + F.site0, st));
             }
-            {
+            if (which & 2) {
                 ProfScope ps(ctx, "grad_gather");
                 CK(launch_grad_gather(F.msa, (float *)D, th, d, lambda_h, lambda_Jp, G + F.off,
                                       active ? active + F.site0 : nullptr, st));
@@ -647,7 +647,7 @@ plm_status evaluate(plm_ctx *ctx, plm_precision prec, Problem &P, const float *w
         }
         for (auto &b : P.tcb)
             CK(launch_tc_eval(ctx->prof ? (void *)ctx : nullptr, b, P.tc_cfg, lambda_h, lambda_Jp,
-                              tc_err, st));
+                              tc_err, st, which));
         return PLM_OK;
     }
     return fail(ctx, PLM_ENOTIMPL, "precision mode %d is not built", (int)prec);
@@ -1320,6 +1320,9 @@ plm_status plm_site_objective_grad(plm_ctx *ctx, const int8_t *msa,
     if (!msa || !w || !h || !J) return fail(ctx, PLM_EINVAL, "null input array");
     if (!(beff > 0.0)) return fail(ctx, PLM_EINVAL, "beff must be > 0");
     if (lambda_h < 0 || lambda_J < 0) return fail(ctx, PLM_EINVAL, "negative lambda");
+    if ((gh == nullptr) != (gJ == nullptr))
+        return fail(ctx, PLM_EINVAL, "gh and gJ must both be given or both be NULL");
+    const int which = gh ? 3 : 1;  // no gradient asked for: the logits pass only
     CK(cudaSetDevice(ctx->device));
     const Dims d = make_dims(B, N);
     const size_t NQ = (size_t)N * Q;
@@ -1360,7 +1363,7 @@ plm_status plm_site_objective_grad(plm_ctx *ctx, const int8_t *msa,
     CK(cudaMemsetAsync(tcflag, 0, sizeof(int), ctx->stream));
     s = evaluate(ctx, prec, P, (const float *)w_d, (const float *)theta,
                  (const __nv_bfloat16 *)hi, (const __nv_bfloat16 *)lo, lambda_h, lJp,
-                 (double *)fdat, (float *)G, (int *)tcflag);
+                 (double *)fdat, (float *)G, (int *)tcflag, nullptr, nullptr, which);
     if (s) return s;
     // f = data + penalty (the finishing kernel with one "slice" and B_eff = -1
     // computes -(-fdata) + pen)
@@ -1368,8 +1371,9 @@ plm_status plm_site_objective_grad(plm_ctx *ctx, const int8_t *msa,
     CK(ws(ctx, "fsum", (size_t)N * sizeof(double), &fsum));
     CK(launch_finish_objective((const double *)fdat, 1, d, -1.0, (const double *)pen,
                                f_s.dev ? (double *)f_s.dev : (double *)fsum, ctx->stream));
-    CK(launch_unpack_theta((const float *)G, d, (float *)gh_s.dev, (float *)gJ_s.dev,
-                           ctx->stream));
+    if (which & 2)
+        CK(launch_unpack_theta((const float *)G, d, (float *)gh_s.dev, (float *)gJ_s.dev,
+                               ctx->stream));
     CK(copy_back(ctx, f_s));
     CK(copy_back(ctx, gh_s));
     CK(copy_back(ctx, gJ_s));

@@ -77,3 +77,41 @@ def test_autograd_adjoint_matches_fd_and_oracle():
         fd = sw[r] * (vals[0] - vals[1]) / (2 * eps)
         g = gh[r, s] if i == N else gJ[r, s, i, k]
         assert abs(g - fd) <= 1e-5 * scale + 1e-9, (r, s, i, k, g, fd)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "split_bf16"])
+def test_objective_only_equals_objective_with_gradient(prec):
+    # with no gradient asked for (torch.no_grad, or plm_site_objective_grad
+    # with gh = gJ = NULL) the library runs the logits pass alone; the
+    # objective is the same number as the full evaluation's
+    from paper_1401_4832_gb300.autograd import plm_objective
+    from paper_1401_4832_gb300 import api
+    S = synth.add_clusters(synth.small_random(41, 600, 21), 0.3, 21, max_redraw=0.1)
+    N = S.shape[1]
+    m, w64, w32, beff = oracle.reweight(S, 0.8)
+    rng = np.random.default_rng(3)
+    h = torch.from_numpy(rng.normal(0, 0.1, (N, Q)).astype(np.float32)).cuda()
+    J0 = rng.normal(0, 0.1, (N, Q, N, Q)).astype(np.float32)
+    for r in range(N):
+        J0[r, :, r, :] = 0
+    J = torch.from_numpy(J0).cuda()
+    Sd, wd = torch.from_numpy(S).cuda(), torch.from_numpy(w32).cuda()
+    with api.Context(0) as c:
+        f_full, gh, gJ = api.plm_site_objective_grad(c, Sd, wd, beff, h, J, prec=prec)
+        f_only, gh0, gJ0 = api.plm_site_objective_grad(c, Sd, wd, beff, h, J, prec=prec, grad=False)
+        assert gh0 is None and gJ0 is None
+        assert torch.equal(f_full, f_only)
+        with torch.no_grad():
+            f_ng = plm_objective(h, J, Sd, wd, beff, prec=prec, plm_ctx=c)
+        assert torch.equal(f_ng, f_full)
+        # exactly one of the gradient outputs missing is an argument error
+        from paper_1401_4832_gb300 import _native
+        import ctypes
+        f = torch.empty(N, dtype=torch.float64, device="cuda")
+        gh1 = torch.empty((N, Q), device="cuda")
+        st = c.lib.plm_site_objective_grad(
+            c.handle, ctypes.c_void_p(Sd.data_ptr()), ctypes.c_void_p(wd.data_ptr()), float(beff),
+            S.shape[0], N, Q, ctypes.c_void_p(h.data_ptr()), ctypes.c_void_p(J.data_ptr()),
+            0.01, 0.01, _native.PRECISIONS[prec], ctypes.c_void_p(f.data_ptr()),
+            ctypes.c_void_p(gh1.data_ptr()), None)
+        assert st == _native.PLM_EINVAL
