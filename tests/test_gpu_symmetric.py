@@ -10,12 +10,14 @@ also be exactly symmetric (J_ji = J_ij^T bit for bit) and give the oracle's
 contact list.
 """
 import math
+import os
 
 import numpy as np
 import pytest
 
 import oracle
 from paper_1401_4832_gb300 import synth
+from parity_bounds import cfn_bound, compare_top
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -93,3 +95,51 @@ def test_symmetric_family_size(ctx):
     for i in range(0, N, 7):
         for j in range(i + 1, N, 11):
             assert np.all(np.abs(LJ * J[i, :, j, :].sum(1) - LH * h[i]) <= tol)
+
+
+SYM_GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                          "symmetric_family_N120_B5000.npz")
+
+
+@pytest.mark.parametrize("prec", ["split_bf16", "fp32"])
+def test_symmetric_family_matches_oracle_rundown(ctx, prec, record_property):
+    # the family workload against the oracle's symmetric rundown (solved to
+    # ||grad|| <= 1e-6, stored with its MSA by a script that calls only the
+    # oracle): strong convexity bounds ||x_g - x_o|| by (||grad(x_g)|| +
+    # ||grad(x_o)||) / mu, and every pair's tied block moves by at most that
+    # distance, so every FN moves by at most b = that bound (the Ising gauge
+    # is a projection); the CFN bound and the top-L comparison follow as in
+    # the asymmetric tests
+    from paper_1401_4832_gb300 import api
+    g = np.load(SYM_GOLDEN)
+    S = g["msa"]
+    N = S.shape[1]
+    iu = np.triu_indices(N, 1)
+    fn_o = np.zeros((N, N))
+    fn_o[iu] = g["fn_upper"].astype(np.float64)
+    fn_o += fn_o.T
+    cfn_o = np.zeros((N, N))
+    cfn_o[iu] = g["cfn_upper"].astype(np.float64)
+    cfn_o += cfn_o.T
+    h_g, J_g, rep = api.plm_solve_symmetric(ctx, torch.from_numpy(S).cuda(), gtol=1e-4, prec=prec)
+    assert rep["n_converged"] == N, rep
+    h = h_g.cpu().numpy().astype(np.float64)
+    J = J_g.cpu().numpy().astype(np.float64)
+    m, w, w32, beff = oracle.reweight(S, 0.8)
+    _, gr = oracle.sym_objgrad(S, w, beff, _x(h, J), LH, LJ)
+    gn = float(np.linalg.norm(gr))
+    assert gn <= 3e-4, gn
+    b = (gn + float(g["gnorm"])) / MU
+    bound = np.full((N, N), b)
+    np.fill_diagonal(bound, 0.0)
+    fn_g, cfn_g, top_g = api.fn_apc_scores(ctx, J_g)
+    err = np.abs(fn_g.cpu().numpy() - fn_o)
+    assert np.all(err <= bound + 1e-6), (err.max(), b)   # + float32 storage of the golden
+    e = cfn_bound(fn_o, bound)
+    cerr = np.abs(cfn_g.cpu().numpy() - cfn_o)
+    assert np.all(cerr <= e + 1e-6)
+    identical, ok, detail = compare_top(top_g.cpu().numpy()[:len(g["top"])], g["top"], cfn_o, e)
+    print(f"symmetric family {prec}: top-{len(g['top'])} vs oracle: {detail}; max |FN err| "
+          f"{err.max():.3g} (bound {b:.3g})")
+    record_property("top_L_identical", identical)
+    assert ok, detail
