@@ -1268,14 +1268,16 @@ k_tc_grad(const __grid_constant__ GradParams P, float two_lh, float two_lj, int 
 }
 
 // ---------------------------------------------------------------- gradient, CTA pair
-// The gradient on 2-CTA clusters: one MMA instruction computes 256 rows
-// (128 per CTA, each CTA's own D^T rows by TMA into its own accumulator) x
-// ncols columns, each CTA building the one-hot X^T rows of half of the
-// columns.  A stage holds 128 of K (two 64-wide atoms).  Roles: warp 0 TMA
-// (both CTAs, counted on the leader's barrier), warp 1 tensor memory (both)
-// and MMA issue (leader), warps 2-9 one-hot producers (thread p: column
-// p % 128 of this CTA's half, K atom p / 128 of each stage), then the
-// epilogue of this CTA's 128 rows.
+// The gradient on 2-CTA clusters, persistent: a pair tile is 256 rows (128
+// per CTA, each CTA's own D^T rows by TMA into its own accumulator) x ncols
+// columns, each CTA building the one-hot X^T rows of half of the columns.
+// A stage holds 128 of K (two 64-wide atoms).  Roles: warp 0 TMA (both
+// CTAs, counted on the leader's barrier), warp 1 tensor memory (both) and
+// MMA issue (leader), warps 2-9 one-hot producers (thread p: column p % 128
+// of this CTA's half, K atom p / 128 of each stage), warps 10-13 the
+// epilogue of this CTA's 128 rows (one row per thread: 2 lambda Theta added,
+// masks applied, G written from registers).  Two accumulators, so a tile's
+// epilogue overlaps the next tile's MMAs.
 __device__ __forceinline__ void tma_load_2d_pair(void *dst, const CUtensorMap *map, uint32_t bar_cl,
                                                  int x, int y)
 {
@@ -1287,252 +1289,288 @@ __device__ __forceinline__ void tma_load_2d_pair(void *dst, const CUtensorMap *m
 }
 
 constexpr int GP_ATOMS = 2;  // K atoms of 64 per stage
+constexpr int GP_THREADS = 448;
 
-__global__ void __launch_bounds__(GR_THREADS, 1)
+// pair tile t: family, first row (of the 256), first column
+__device__ __forceinline__ void gp_tile(const GradParams &P, int t, int &fi, int &rs0, int &c0)
+{
+    fi = family_of(P.b, t, true);
+    const FamDesc &F = P.b.f[fi];
+    const int local = t - F.tile0_grad;
+    const int nct = (F.KP + P.ncols - 1) / P.ncols;
+    c0 = (local % nct) * P.ncols;
+    rs0 = (local / nct) * 2 * TC_M;
+}
+
+__device__ __forceinline__ bool rows_active(const FamDesc &F, int rs0)
+{
+    if (!F.active) return true;
+    for (int r = rs0 / QP; r <= (rs0 + 2 * TC_M - 1) / QP && r < F.N; ++r)
+        if (F.active[r]) return true;
+    return false;
+}
+
+__global__ void __launch_bounds__(GP_THREADS, 1)
 k_tc_grad_pair(const __grid_constant__ GradParams P, float two_lh, float two_lj, int *__restrict__ err)
 {
-    const int pair = blockIdx.x >> 1;
+    const int pair = blockIdx.x >> 1, npairs = gridDim.x >> 1;
     const uint32_t rank = cluster_rank();
     const bool leader = rank == 0;
-    const int fi = family_of(P.b, pair, true);
-    const FamDesc &F = P.b.f[fi];
-    const CUtensorMap &tm_dhi = P.dhi[fi];
-    const CUtensorMap &tm_dlo = P.dlo[fi];
-    const int8_t *__restrict__ msaT = F.msaT;
-    const float *__restrict__ theta = F.theta;
-    float *__restrict__ G = F.G;
-    const int BP = F.BP;
-    Dims d;
-    d.B = F.B;
-    d.N = F.N;
-    d.KP = F.KP;
-    d.R = F.R;
-    d.K = F.N * Q + 1;
-    const int local = pair - F.tile0_grad;
+    const int ntiles = P.b.ntiles_grad;
     const int GRN = P.ncols, NST = P.stages, GRSTAGE = P.stage_bytes;
     const int HN = GRN / 2;                   // one-hot columns built by this CTA
     const int A_BYTES = GR_A_BYTES;           // 128 rows x 64 of K, bf16
     const int B_BYTES = HN * TC_BK * 2;
-    const int nct = (d.KP + GRN - 1) / GRN;
-    const int c0 = (local % nct) * GRN;
-    const int rs0 = (local / nct) * 2 * TC_M;  // first row of the pair tile
-    const int rh = rs0 + (int)rank * TC_M;     // first row of this CTA
-    if (F.active) {
-        // the same decision in both CTAs: any active site in the pair's rows
-        bool any = false;
-        for (int r = rs0 / QP; r <= (rs0 + 2 * TC_M - 1) / QP && r < F.N; ++r)
-            any |= F.active[r] != 0;
-        if (!any) return;
-    }
+    const int B_OFF = GP_ATOMS * 2 * A_BYTES;  // stage: A_hi a0 | A_lo a0 | A_hi a1 | A_lo a1 | B a0 | B a1
     extern __shared__ uint8_t dsmem[];
     uint8_t *smem = align1024(dsmem);
-    __shared__ __align__(8) uint64_t full_[MAX_STAGES], empty_[MAX_STAGES], acc_full;
+    __shared__ __align__(8) uint64_t full_[MAX_STAGES], empty_[MAX_STAGES];
+    __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2], mma_done;
     __shared__ uint32_t tmem_sh;
     __shared__ int abort_sh;
-
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int NA = BP / TC_BK;
-    const int NQ = d.N * Q;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < MAX_STAGES; ++s) {
             mbar_init(&full_[s], 1 + 2 * (GR_PROD / 32));  // leader's TMA + 8 producer warps per CTA
             mbar_init(&empty_[s], 1);
         }
-        mbar_init(&acc_full, 1);
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&acc_full[a], 1);
+            mbar_init(&acc_empty[a], 2 * 4);  // 4 epilogue warps per CTA
+        }
+        mbar_init(&mma_done, 1);
         abort_sh = 0;
         fence_mbar_init();
     }
     __syncthreads();
     cluster_sync_all();
     if (warp == 1) {
-        tmem_alloc_pair(&tmem_sh, TMEM_COLS);
+        tmem_alloc_pair(&tmem_sh, 2 * TMEM_COLS);
         tmem_relinquish_pair();
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_sh;
-    // stage layout: A_hi a0 | A_lo a0 | A_hi a1 | A_lo a1 | B a0 | B a1
-    const int B_OFF = GP_ATOMS * 2 * A_BYTES;
 
     if (warp == 0) {
         if (lane == 0) {
-            int issued = 0;
-            for (int ks = 0; ks * GP_ATOMS < NA; ++ks) {
-                const int ka = ks * GP_ATOMS;
-                const int na = NA - ka < GP_ATOMS ? NA - ka : GP_ATOMS;
-                const int s = ks % NST, n = ks / NST;
-                if (n > 0 && !mbar_wait(&empty_[s], (n - 1) & 1, &abort_sh, err, ERR_TIMEOUT_TMA))
-                    break;
-                uint8_t *st = smem + s * GRSTAGE;
-                const uint32_t bar = cluster_addr(&full_[s], 0);
-                if (leader) mbar_expect_tx(&full_[s], 2 * na * 2 * A_BYTES);
-                for (int a = 0; a < na; ++a) {
-                    tma_load_2d_pair(st + 2 * a * A_BYTES, &tm_dhi, bar, (ka + a) * TC_BK, rh);
-                    tma_load_2d_pair(st + (2 * a + 1) * A_BYTES, &tm_dlo, bar, (ka + a) * TC_BK, rh);
+            long long kit = 0;
+            bool ok = true;
+            for (int t = pair; t < ntiles && ok; t += npairs) {
+                int fi, rs0, c0;
+                gp_tile(P, t, fi, rs0, c0);
+                const FamDesc &F = P.b.f[fi];
+                if (!rows_active(F, rs0)) continue;
+                const int rh = rs0 + (int)rank * TC_M;
+                const int NA = F.BP / TC_BK;
+                for (int ka = 0; ka < NA; ka += GP_ATOMS, ++kit) {
+                    const int na = NA - ka < GP_ATOMS ? NA - ka : GP_ATOMS;
+                    const int s = (int)(kit % NST);
+                    const long long n = kit / NST;
+                    if (n > 0 &&
+                        !mbar_wait(&empty_[s], (uint32_t)((n - 1) & 1), &abort_sh, err, ERR_TIMEOUT_TMA)) {
+                        ok = false;
+                        break;
+                    }
+                    uint8_t *st = smem + s * GRSTAGE;
+                    const uint32_t bar = cluster_addr(&full_[s], 0);
+                    if (leader) mbar_expect_tx(&full_[s], 2 * na * 2 * A_BYTES);
+                    for (int a = 0; a < na; ++a) {
+                        tma_load_2d_pair(st + 2 * a * A_BYTES, &P.dhi[fi], bar, (ka + a) * TC_BK, rh);
+                        tma_load_2d_pair(st + (2 * a + 1) * A_BYTES, &P.dlo[fi], bar, (ka + a) * TC_BK, rh);
+                    }
                 }
-                issued = ks + 1;
             }
             if (leader)
-                for (int k = issued - NST < 0 ? 0 : issued - NST; k < issued; ++k)
-                    mbar_drain(&full_[k % NST], (k / NST) & 1);
+                for (long long k = kit - NST < 0 ? 0 : kit - NST; k < kit; ++k)
+                    mbar_drain(&full_[k % NST], (uint32_t)((k / NST) & 1));
         }
     } else if (warp == 1) {
         if (lane == 0 && leader) {
             const uint32_t idesc = idesc_bf16(2 * TC_M, GRN);
-            for (int ks = 0; ks * GP_ATOMS < NA; ++ks) {
-                const int ka = ks * GP_ATOMS;
-                const int na = NA - ka < GP_ATOMS ? NA - ka : GP_ATOMS;
-                const int s = ks % NST, n = ks / NST;
-                if (!mbar_wait(&full_[s], n & 1, &abort_sh, err, ERR_TIMEOUT_MMA)) break;
+            long long kit = 0;
+            int ti = 0;
+            bool ok = true;
+            for (int t = pair; t < ntiles && ok; t += npairs) {
+                int fi, rs0, c0;
+                gp_tile(P, t, fi, rs0, c0);
+                const FamDesc &F = P.b.f[fi];
+                if (!rows_active(F, rs0)) continue;
+                const int a = ti & 1, use = ti >> 1;
+                if (use > 0 && !mbar_wait(&acc_empty[a], (uint32_t)((use - 1) & 1), &abort_sh, err,
+                                          ERR_TIMEOUT_MMA))
+                    break;
                 tc_fence_after();
-                uint8_t *st = smem + s * GRSTAGE;
-                for (int a = 0; a < na; ++a) {
-                    const uint32_t ah = smem_u32(st + 2 * a * A_BYTES);
-                    const uint32_t al = smem_u32(st + (2 * a + 1) * A_BYTES);
-                    const uint32_t bx = smem_u32(st + B_OFF + a * B_BYTES);
+                const uint32_t dt = tmem + a * TMEM_COLS;
+                const int NA = F.BP / TC_BK;
+                for (int ka = 0; ka < NA; ka += GP_ATOMS, ++kit) {
+                    const int na = NA - ka < GP_ATOMS ? NA - ka : GP_ATOMS;
+                    const int s = (int)(kit % NST);
+                    const uint32_t ph = (uint32_t)((kit / NST) & 1);
+                    if (!mbar_wait(&full_[s], ph, &abort_sh, err, ERR_TIMEOUT_MMA)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    uint8_t *st = smem + s * GRSTAGE;
+                    for (int a2 = 0; a2 < na; ++a2) {
+                        const uint32_t ah = smem_u32(st + 2 * a2 * A_BYTES);
+                        const uint32_t al = smem_u32(st + (2 * a2 + 1) * A_BYTES);
+                        const uint32_t bx = smem_u32(st + B_OFF + a2 * B_BYTES);
 #pragma unroll
-                    for (int k = 0; k < TC_BK / 16; ++k)
-                        mma_bf16_pair(tmem, sdesc(ah + 32 * k), sdesc(bx + 32 * k), idesc,
-                                      (ka > 0 || a > 0 || k > 0) ? 1u : 0u);
+                        for (int k = 0; k < TC_BK / 16; ++k)
+                            mma_bf16_pair(dt, sdesc(ah + 32 * k), sdesc(bx + 32 * k), idesc,
+                                          (ka > 0 || a2 > 0 || k > 0) ? 1u : 0u);
 #pragma unroll
-                    for (int k = 0; k < TC_BK / 16; ++k)
-                        mma_bf16_pair(tmem, sdesc(al + 32 * k), sdesc(bx + 32 * k), idesc, 1u);
+                        for (int k = 0; k < TC_BK / 16; ++k)
+                            mma_bf16_pair(dt, sdesc(al + 32 * k), sdesc(bx + 32 * k), idesc, 1u);
+                    }
+                    mma_commit_pair(&empty_[s]);
                 }
-                mma_commit_pair(&empty_[s]);
+                if (!ok) break;
+                mma_commit_pair(&acc_full[a]);
+                ++ti;
             }
-            mma_commit_pair(&acc_full);  // arrives in both CTAs when every MMA above is complete
+            mma_commit_pair(&mma_done);  // arrives in both CTAs when every MMA above is complete
         }
-    } else {
+    } else if (warp < 2 + GR_PROD / 32) {
         // ---- one-hot X^T producer: thread p writes row p % 128 of this
         // CTA's column half for K atom p / 128 of every stage
         const int p = threadIdx.x - 64;
         const int prow = p % TC_M, pa = p / TC_M;
-        const int c = c0 + (int)rank * HN + prow;
-        int src_i = 0;
-        uint32_t kk = 0xFFu;  // never equals a stored state (0..20, or 0x7F padding)
-        if (c < NQ) {
-            src_i = c / Q;
-            kk = (uint32_t)(c % Q);
-        } else if (c == NQ) {
-            src_i = d.N;  // the all-ones row of msaT
-            kk = 0;
-        }
-        kk *= 0x01010101u;
-        const bool has_row = prow < HN;
-        const uint4 *srcT = (const uint4 *)(msaT + (size_t)src_i * BP);
-        // this thread's atom of the first stage, fetched ahead
-        uint4 cur[4], nxt[4];
-        {
-            const int ka0 = pa < NA ? pa : 0;
+        long long kit = 0;
+        bool ok = true;
+        for (int t = pair; t < ntiles && ok; t += npairs) {
+            int fi, rs0, c0;
+            gp_tile(P, t, fi, rs0, c0);
+            const FamDesc &F = P.b.f[fi];
+            if (!rows_active(F, rs0)) continue;
+            const int BP = F.BP, NA = BP / TC_BK, NQ = F.N * Q;
+            const int c = c0 + (int)rank * HN + prow;
+            int src_i = 0;
+            uint32_t kk = 0xFFu;  // never equals a stored state (0..20, or 0x7F padding)
+            if (c < NQ) {
+                src_i = c / Q;
+                kk = (uint32_t)(c % Q);
+            } else if (c == NQ) {
+                src_i = F.N;  // the all-ones row of msaT
+                kk = 0;
+            }
+            kk *= 0x01010101u;
+            const bool has_row = prow < HN;
+            const uint4 *srcT = (const uint4 *)(F.msaT + (size_t)src_i * BP);
+            uint4 cur[4], nxt[4];
+            {
+                const int ka0 = pa < NA ? pa : 0;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) cur[q] = __ldg(srcT + (size_t)ka0 * (TC_BK / 16) + q);
-        }
-        for (int ks = 0; ks * GP_ATOMS < NA; ++ks) {
-            const int ka = ks * GP_ATOMS;
-            const int na = NA - ka < GP_ATOMS ? NA - ka : GP_ATOMS;
-            const int s = ks % NST, n = ks / NST;
-            // the next stage's bytes for this thread's atom
-            const int kn = ka + GP_ATOMS + pa < NA ? ka + GP_ATOMS + pa : (ka + pa < NA ? ka + pa : 0);
+                for (int q = 0; q < 4; ++q) cur[q] = __ldg(srcT + (size_t)ka0 * (TC_BK / 16) + q);
+            }
+            for (int ka = 0; ka < NA; ka += GP_ATOMS, ++kit) {
+                const int na = NA - ka < GP_ATOMS ? NA - ka : GP_ATOMS;
+                const int s = (int)(kit % NST);
+                const long long n = kit / NST;
+                // the next stage's bytes for this thread's atom
+                const int kn = ka + GP_ATOMS + pa < NA ? ka + GP_ATOMS + pa
+                                                       : (ka + pa < NA ? ka + pa : 0);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) nxt[q] = __ldg(srcT + (size_t)kn * (TC_BK / 16) + q);
-            const bool got = n == 0 || mbar_wait(&empty_[s], (n - 1) & 1, &abort_sh, err,
-                                                 ERR_TIMEOUT_PROD);
-            if (!__all_sync(0xffffffffu, got)) break;
-            if (has_row && pa < na) {
-                uint8_t *bt = smem + s * GRSTAGE + B_OFF + pa * B_BYTES;
+                for (int q = 0; q < 4; ++q) nxt[q] = __ldg(srcT + (size_t)kn * (TC_BK / 16) + q);
+                const bool got = n == 0 || mbar_wait(&empty_[s], (uint32_t)((n - 1) & 1), &abort_sh,
+                                                     err, ERR_TIMEOUT_PROD);
+                if (!__all_sync(0xffffffffu, got)) {
+                    ok = false;
+                    break;
+                }
+                if (has_row && pa < na) {
+                    uint8_t *bt = smem + s * GRSTAGE + B_OFF + pa * B_BYTES;
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {  // 16 sequences per word group
-                    const uint4 x = cur[q];
-                    const uint32_t xs[4] = {x.x, x.y, x.z, x.w};
-                    uint32_t o[8];
+                    for (int q = 0; q < 4; ++q) {  // 16 sequences per word group
+                        const uint4 x = cur[q];
+                        const uint32_t xs[4] = {x.x, x.y, x.z, x.w};
+                        uint32_t o[8];
 #pragma unroll
-                    for (int t = 0; t < 4; ++t) {
-                        const uint32_t m = __vcmpeq4(xs[t], kk);
-                        o[2 * t] = __byte_perm(m, 0, 0x1100) & 0x3F803F80u;
-                        o[2 * t + 1] = __byte_perm(m, 0, 0x3322) & 0x3F803F80u;
+                        for (int u = 0; u < 4; ++u) {
+                            const uint32_t m = __vcmpeq4(xs[u], kk);
+                            o[2 * u] = __byte_perm(m, 0, 0x1100) & 0x3F803F80u;
+                            o[2 * u + 1] = __byte_perm(m, 0, 0x3322) & 0x3F803F80u;
+                        }
+                        *(uint4 *)(bt + swz(prow, 2 * q)) = make_uint4(o[0], o[1], o[2], o[3]);
+                        *(uint4 *)(bt + swz(prow, 2 * q + 1)) = make_uint4(o[4], o[5], o[6], o[7]);
                     }
-                    *(uint4 *)(bt + swz(prow, 2 * q)) = make_uint4(o[0], o[1], o[2], o[3]);
-                    *(uint4 *)(bt + swz(prow, 2 * q + 1)) = make_uint4(o[4], o[5], o[6], o[7]);
                 }
-            }
-            fence_proxy_async();
-            __syncwarp();
-            if (lane == 0) mbar_arrive_cluster(cluster_addr(&full_[s], 0));
+                fence_proxy_async();
+                __syncwarp();
+                if (lane == 0) mbar_arrive_cluster(cluster_addr(&full_[s], 0));
 #pragma unroll
-            for (int q = 0; q < 4; ++q) cur[q] = nxt[q];
+                for (int q = 0; q < 4; ++q) cur[q] = nxt[q];
+            }
         }
-
-        // ---- epilogue: TMEM -> shared (rows padded to GRN + 4 floats), then
-        // a coalesced pass adds 2 lambda Theta, applies the masks and writes G
+    } else {
+        // ---- epilogue: one row of this CTA's 128 per thread (its tensor-
+        // memory lane), 16 columns at a time: 2 lambda Theta added, the
+        // diagonal block, the padding rows and columns zeroed, G written
         const int q4 = warp & 3;
-        const int half = (warp - 2) >> 2;  // column half of the tile
-        const int trow = q4 * 32 + lane;
-        const bool ok = mbar_wait(&acc_full, 0, &abort_sh, err, ERR_TIMEOUT_EPI);
-        tc_fence_after();
-        const int GS = GRN + 4;
-        float *acc_s = (float *)smem;  // [128][GS]: the pipeline stages are free now
-        const int ng = GRN / 32;
-        const uint32_t tl = tmem + ((uint32_t)(q4 * 32) << 16);
-#pragma unroll 1
-        for (int cc = half * ng; cc < (half + 1) * ng; ++cc) {
-            float v[16];
-            tmem_ld16(tl + cc * 16, v);
-            tmem_wait_ld();
-            float4 *dst = (float4 *)(acc_s + trow * GS + cc * 16);
+        const int er = q4 * 32 + lane;
+        int ti = 0;
+        for (int t = pair; t < ntiles; t += npairs) {
+            int fi, rs0, c0;
+            gp_tile(P, t, fi, rs0, c0);
+            const FamDesc &F = P.b.f[fi];
+            if (!rows_active(F, rs0)) continue;
+            const int a = ti & 1, use = ti >> 1;
+            const int row = rs0 + (int)rank * TC_M + er;
+            const int KP = F.KP, NQ = F.N * Q;
+            const bool live_row = row < F.R;
+            const int r = row / QP, sstate = row % QP;
+            const float *th = F.theta + (size_t)(live_row ? row : 0) * KP;
+            float *g = F.G + (size_t)(live_row ? row : 0) * KP;
+            const bool ok = mbar_wait(&acc_full[a], (uint32_t)(use & 1), &abort_sh, err, ERR_TIMEOUT_EPI);
+            tc_fence_after();
+            const uint32_t tl = tmem + a * TMEM_COLS + ((uint32_t)(q4 * 32) << 16);
+            for (int cc = 0; cc < GRN / 16; ++cc) {
+                float v[16];
+                tmem_ld16(tl + cc * 16, v);
+                tmem_wait_ld();
+                const int cb = c0 + cc * 16;
+                if (ok && live_row && cb < KP) {  // KP is a multiple of 64
+                    float4 tv[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-                dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-        }
-        epi_bar256();
-        const int t = threadIdx.x - 64;
-        constexpr int UNR = 4;
-        for (int e0 = t; e0 < TC_M * (GRN / 4); e0 += GR_PROD * UNR) {
-            float4 th[UNR];
-            bool live[UNR];
+                    for (int q = 0; q < 4; ++q) tv[q] = *(const float4 *)(th + cb + 4 * q);
+                    float o[16];
 #pragma unroll
-            for (int k = 0; k < UNR; ++k) {  // issue all loads first
-                const int e = e0 + GR_PROD * k;
-                const int rr = e / (GRN / 4), c4 = e % (GRN / 4);
-                const int row = rh + rr, cb = c0 + 4 * c4;
-                live[k] = ok && e < TC_M * (GRN / 4) && row < d.R && cb < d.KP;
-                th[k] = live[k] ? *(const float4 *)(theta + (size_t)row * d.KP + cb)
-                                : make_float4(0.f, 0.f, 0.f, 0.f);
-            }
+                    for (int u = 0; u < 16; ++u) {
+                        const int cu = cb + u;
+                        const float tu = (&tv[u >> 2].x)[u & 3];
+                        float val;
+                        if (sstate >= Q || cu > NQ || (cu >= r * Q && cu < r * Q + Q)) val = 0.0f;
+                        else if (cu == NQ) val = v[u] + two_lh * tu;
+                        else val = v[u] + two_lj * tu;
+                        o[u] = val;
+                    }
 #pragma unroll
-            for (int k = 0; k < UNR; ++k) {
-                if (!live[k]) continue;
-                const int e = e0 + GR_PROD * k;
-                const int rr = e / (GRN / 4), c4 = e % (GRN / 4);
-                const int row = rh + rr, cb = c0 + 4 * c4;
-                const int r = row / QP, sstate = row % QP;
-                const float4 a = *(const float4 *)(acc_s + rr * GS + 4 * c4);
-                const float av[4] = {a.x, a.y, a.z, a.w};
-                const float tv[4] = {th[k].x, th[k].y, th[k].z, th[k].w};
-                float o[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int cu = cb + u;
-                    float val;
-                    if (sstate >= Q || cu > NQ || (cu >= r * Q && cu < r * Q + Q)) val = 0.0f;
-                    else if (cu == NQ) val = av[u] + two_lh * tv[u];
-                    else val = av[u] + two_lj * tv[u];
-                    o[u] = val;
+                    for (int q = 0; q < 4; ++q)
+                        *(float4 *)(g + cb + 4 * q) =
+                            make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
                 }
-                *(float4 *)(G + (size_t)row * d.KP + cb) = make_float4(o[0], o[1], o[2], o[3]);
+                __syncwarp();
             }
+            // this warp's tensor-memory reads of the tile are done
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive_cluster(cluster_addr(&acc_empty[a], 0));
+            ++ti;
         }
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 1 && lane == 0) mbar_drain(&acc_full, 0);  // every MMA into this CTA's memory
+    if (warp == 1 && lane == 0) mbar_drain(&mma_done, 0);  // every MMA into this CTA's memory
     tc_fence_before();
     __syncthreads();
     cluster_sync_all();
     if (warp == 1) {
         tc_fence_after();
-        tmem_dealloc_pair(tmem, TMEM_COLS);
+        tmem_dealloc_pair(tmem, 2 * TMEM_COLS);
     }
     cluster_sync_all();
 }
@@ -1748,14 +1786,16 @@ cudaError_t launch_grad_pair(const GradParams &gp, int ntiles, float two_lh, flo
     cudaError_t e = set_smem_limit_once((const void *)k_tc_grad_pair, SMEM_BUDGET + 1024, attr);
     if (e) return e;
     if (ntiles <= 0) return cudaSuccess;
+    // persistent: as many clusters as fit at once (one CTA per SM)
+    const int clusters = std::min(ntiles, num_sms() / 2);
     cudaLaunchConfig_t lc = {};
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = 2;
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
-    lc.gridDim = dim3(2 * ntiles);
-    lc.blockDim = dim3(GR_THREADS);
+    lc.gridDim = dim3(2 * clusters);
+    lc.blockDim = dim3(GP_THREADS);
     lc.dynamicSmemBytes = smem;
     lc.stream = st;
     lc.attrs = at;

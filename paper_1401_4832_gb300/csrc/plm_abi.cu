@@ -538,7 +538,6 @@ plm_status autotune_tc(plm_ctx *ctx, Problem &P, int *tc_err)
     // gradient: 128- or 256-row single-CTA tiles, or 256-row tiles on CTA pairs
     for (int shape : {0, 1, 2})
         for (int cols : {128, 160, 192, 224, 256}) {
-            if (shape == 2 && cols < 224) continue;  // pair tiles: two waves or more below 224
             TcConfig c = best;
             c.gr_rows = shape == 0 ? 128 : 256;
             c.gr_pair = shape == 2 ? 1 : 0;
