@@ -3,10 +3,10 @@
 // Logits (Eq. condpfinal):  L[b][(r,s)] = sum_i Theta[(r,s)][i*Q + S_bi] + h_r(s)
 // i.e. the one-hot product X Theta^T done as gathers: for every position i
 // only the column of the observed state contributes.  A CTA stages a tile
-// of 128 rows (r,s) x 8 positions x 21 states of Theta transposed in shared
+// of 128 rows (r,s) x 4 positions x 21 states of Theta transposed in shared
 // memory (row stride 129 words, so both the staging stores and the lane-wise
-// loads are bank-conflict free) and each warp sums the gathered entries for
-// 16 sequences.
+// loads are bank-conflict free; two chunks in flight, staged by cp.async) and
+// each warp sums the gathered entries for 16 sequences.
 //
 // Log-softmax, objective and residual (Eq. g_regdef2; Eqs. g_gradh2,
 // g_gradJ2): one thread per (site, sequence) over the 21 states in FP32,
@@ -27,12 +27,20 @@ namespace plm {
 namespace {
 
 constexpr int LG_ROWS = 128;        // rows (r,s) per CTA
-constexpr int LG_IC = 8;            // positions per staged chunk
+constexpr int LG_IC = 4;            // positions per staged chunk (two chunks in flight)
 constexpr int LG_BPW = 16;          // sequences per warp
 constexpr int LG_BT = 8 * LG_BPW;   // sequences per CTA
 constexpr int LG_STRIDE = 129;      // padded row stride of the staged tile
-constexpr size_t LG_SMEM = (size_t)LG_IC * Q * LG_STRIDE * sizeof(float) +
-                           (size_t)LG_BT * LG_IC;
+constexpr int LG_TILE = LG_IC * Q * LG_STRIDE;  // floats per staged Theta chunk
+constexpr size_t LG_SMEM = 2 * (size_t)LG_TILE * sizeof(float) + 2 * (size_t)LG_BT * LG_IC;
+
+__device__ __forceinline__ void cp_async4(void *dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
 
 __global__ void __launch_bounds__(256)
 k_logits_gather(const int8_t *__restrict__ msa, const float *__restrict__ theta,
@@ -46,12 +54,35 @@ k_logits_gather(const int8_t *__restrict__ msa, const float *__restrict__ theta,
         if (!any) return;
     }
     extern __shared__ float smem[];
-    float *ths = smem;                                           // [IC*Q][129]
-    int8_t *ss = (int8_t *)(smem + LG_IC * Q * LG_STRIDE);       // [BT][IC]
+    float *ths0 = smem;                                            // 2 x [IC*Q][129]
+    int8_t *ss0 = (int8_t *)(smem + 2 * LG_TILE);                  // 2 x [BT][IC]
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int row0 = blockIdx.x * LG_ROWS;
     const int b0 = blockIdx.y * LG_BT;
     const int NQ = d.N * Q;
+
+    // stage Theta[row0 .. +128][i0*Q .. +ncol] transposed (cp.async, 4 bytes
+    // per element) and the chunk's states into buffer `buf`
+    auto stage = [&](int buf, int i0) {
+        float *ths = ths0 + buf * LG_TILE;
+        int8_t *ss = ss0 + buf * LG_BT * LG_IC;
+        const int ncol = min(LG_IC, d.N - i0) * Q;
+        for (int e = tid; e < LG_ROWS * LG_IC * Q; e += blockDim.x) {
+            const int cc = e % (LG_IC * Q);
+            const int rr = e / (LG_IC * Q);
+            float *dst = ths + cc * LG_STRIDE + rr;
+            if (cc < ncol && row0 + rr < d.R)
+                cp_async4(dst, theta + (size_t)(row0 + rr) * d.KP + i0 * Q + cc);
+            else
+                *dst = 0.0f;
+        }
+        for (int e = tid; e < LG_BT * LG_IC; e += blockDim.x) {
+            const int ic = e % LG_IC, bb = e / LG_IC;
+            const int b = b0 + bb, i = i0 + ic;
+            ss[e] = (b < d.B && i < d.N) ? msa[(size_t)b * d.N + i] : 0;
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
 
     float acc[LG_BPW][4];
 #pragma unroll
@@ -59,34 +90,29 @@ k_logits_gather(const int8_t *__restrict__ msa, const float *__restrict__ theta,
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[u][j] = 0.0f;
 
-    for (int i0 = 0; i0 < d.N; i0 += LG_IC) {
-        const int ncol = min(LG_IC, d.N - i0) * Q;
-        __syncthreads();
-        // stage Theta[row0 .. +128][i0*Q .. +ncol] transposed
-        for (int e = tid; e < LG_ROWS * LG_IC * Q; e += blockDim.x) {
-            int cc = e % (LG_IC * Q);
-            int rr = e / (LG_IC * Q);
-            float v = 0.0f;
-            if (cc < ncol && row0 + rr < d.R)
-                v = theta[(size_t)(row0 + rr) * d.KP + i0 * Q + cc];
-            ths[cc * LG_STRIDE + rr] = v;
-        }
-        for (int e = tid; e < LG_BT * LG_IC; e += blockDim.x) {
-            int ic = e % LG_IC, bb = e / LG_IC;
-            int b = b0 + bb, i = i0 + ic;
-            ss[e] = (b < d.B && i < d.N) ? msa[(size_t)b * d.N + i] : 0;
+    stage(0, 0);
+    int buf = 0;
+    for (int i0 = 0; i0 < d.N; i0 += LG_IC, buf ^= 1) {
+        if (i0 + LG_IC < d.N) {
+            stage(buf ^ 1, i0 + LG_IC);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
         }
         __syncthreads();
+        const float *ths = ths0 + buf * LG_TILE;
+        const int8_t *ssb = ss0 + buf * LG_BT * LG_IC;
         const int nic = min(LG_IC, d.N - i0);
 #pragma unroll
         for (int u = 0; u < LG_BPW; ++u) {
-            const int8_t *sb = ss + (warp * LG_BPW + u) * LG_IC;
+            const int8_t *sb = ssb + (warp * LG_BPW + u) * LG_IC;
             for (int ic = 0; ic < nic; ++ic) {
                 const float *col = ths + (ic * Q + sb[ic]) * LG_STRIDE + lane;
 #pragma unroll
                 for (int j = 0; j < 4; ++j) acc[u][j] += col[32 * j];
             }
         }
+        __syncthreads();  // the buffer is restaged two chunks on
     }
     // field column (its one-hot feature is 1 for every sequence)
     float hv[4];
