@@ -164,6 +164,41 @@ def cpu_sample(fam, n_sites, gtol):
     return full, (t3 - t0), evals, len(sites)
 
 
+def cpu_full_rundown(fam, gtol, gpu):
+    """The oracle's whole rundown of the workload, timed on all host cores,
+    and the last timed GPU solve compared with it: every pair's FN and CFN
+    against the stated error bound (gradient norms of both points by the
+    oracle, strong convexity mu = 2 min(lambda_h, lambda'_J)) and the top-L
+    lists (exactly identical, or ties only inside the bound)."""
+    import numpy as np
+    import oracle
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from parity_bounds import cfn_bound, compare_top, fn_bound
+    S = fam.msa
+    t0 = time.perf_counter()
+    ro = oracle.plmdca(S, gtol=gtol)
+    wall = time.perf_counter() - t0
+    parity = None
+    if gpu:
+        N = S.shape[1]
+        h = gpu["h"].cpu().numpy().astype(np.float64)
+        J = gpu["J"].cpu().numpy().astype(np.float64)
+        _, gh, gJ = oracle.objgrad(S, ro["w"], ro["beff"], h, J, 0.01, 0.01)
+        gn = np.sqrt((gh ** 2).sum(1) + (gJ ** 2).reshape(N, -1).sum(1))
+        mu = 2 * min(0.01, 0.5 * 0.01)
+        b = fn_bound(gn, ro["info"]["gnorm"], mu)
+        fn_err = np.abs(gpu["fn"].cpu().numpy() - ro["fn"])
+        e = cfn_bound(ro["fn"], b)
+        cfn_err = np.abs(gpu["cfn"].cpu().numpy() - ro["cfn"])
+        top = gpu["top"].cpu().numpy()[:len(ro["top"])]
+        identical, ok, detail = compare_top(top, ro["top"], ro["cfn"], e)
+        parity = {"top_L_identical": identical, "top_L_within_bound": ok, "detail": detail,
+                  "fn_within_bound": bool(np.all(fn_err <= b + 1e-9)),
+                  "max_fn_err": float(fn_err.max()), "max_fn_bound": float(b.max()),
+                  "max_cfn_err": float(cfn_err.max()), "max_cfn_bound": float(e.max())}
+    return wall, parity
+
+
 def cpu_sample_single_thread(fam, n_sites, gtol):
     """The same oracle sample on one host thread (the timing protocol asks for
     one core beside all of them); the thread count is restored after."""
@@ -512,9 +547,12 @@ def main():
     opts = dict(gtol=args.gtol, prec=prec, lbfgs_m=args.lbfgs_m)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{device}")
 
+    last = {}
+
     def step():
         h, J, rep = api.plm_solve(ctx, msa, **opts)
         fn, cfn, top = api.fn_apc_scores(ctx, J)
+        last.update(h=h, J=J, fn=fn, cfn=cfn, top=top)  # kept for the oracle comparison
         return rep, top
 
     sampler = ClockSampler(device)
@@ -639,15 +677,22 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         cores = oracle.num_threads()
-        n_sites = args.cpu_sites or min(16, cores)
-        full, wall, oevals, ns = cpu_sample(fam, n_sites, args.gtol)
+        if args.cpu_sites:
+            full, wall, oevals, ns = cpu_sample(fam, args.cpu_sites, args.gtol)
+            sample = (f"full reweighting + L-BFGS of {ns} of {N} sites (gtol {args.gtol}) "
+                      f"scaled x{N}/{ns} + full FN/APC/top-L; {wall:.1f} s of CPU wall time")
+            parity = None
+        else:
+            full, parity = cpu_full_rundown(fam, args.gtol, last)
+            sample = (f"the whole rundown on all {N} sites (reweighting, L-BFGS to gtol "
+                      f"{args.gtol}, FN/APC/top-L), no extrapolation")
         full1, wall1, _, ns1 = cpu_sample_single_thread(fam, 2, args.gtol)
-        cpu = {"value": full, "unit": "s", "cores": cores, "kind": "oracle",
-               "sample": (f"full reweighting + L-BFGS of {ns} of {N} sites (gtol {args.gtol}) "
-                          f"scaled x{N}/{ns} + full FN/APC/top-L; {wall:.1f} s of CPU wall time"),
+        cpu = {"value": full, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample,
                "single_thread": {"value": full1, "unit": "s", "cores": 1,
-                                 "sample": (f"the same on one thread with {ns1} of {N} sites "
-                                            f"scaled x{N}/{ns1}; {wall1:.1f} s of CPU wall time")}}
+                                 "sample": (f"reweighting + L-BFGS of {ns1} of {N} sites on one "
+                                            f"thread scaled x{N}/{ns1} + FN/APC/top-L; "
+                                            f"{wall1:.1f} s of CPU wall time")},
+               "parity_of_the_timed_solve": parity}
 
     if rank == 0:
         out = {
