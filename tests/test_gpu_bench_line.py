@@ -34,6 +34,8 @@ def test_bench_line_contract():
     assert 0 < roof["frac"] <= 1.5 and abs(roof["frac"] - roof["achieved"] / roof["peak"]) < 1e-9
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] > d["value"]
+    par = cb["parity_of_the_timed_solve"]  # the timed solve against the oracle's rundown
+    assert par["fn_within_bound"] and par["top_L_within_bound"], par
     c = d["clocks"]
     assert {"sm_mhz", "sm_max_mhz", "reasons"} <= set(c)
     assert d["fp32_path"]["top_L_identical_to_split_bf16"] is True
