@@ -210,3 +210,18 @@ def test_tc_autotuner_tries_every_shape_in_one_process():
     h, J = _theta(45, 13, 0.1)
     with api.Context(0) as c:
         ef, eg = _compare(c, S, h, J)
+
+
+@pytest.mark.parametrize("N,B", [(2, 1), (5, 127), (13, 129), (7, 257)])
+@pytest.mark.parametrize("tiles", ["12,224,256,1,0", "4,128,256,1,1", "12,256,256,2,1"])
+def test_tc_pair_shapes_at_the_edges(N, B, tiles, monkeypatch):
+    # smallest problems on the 2-CTA kernels: fewer sites than half a tile
+    # (the peer CTA's Theta box lies wholly beyond N and reads zeros), one
+    # sequence, a single 128-sequence tile (the pair's second CTA computes
+    # nothing), 257 sequences (three tiles, the last with one sequence)
+    from paper_1401_4832_gb300 import api
+    monkeypatch.setenv("PLMDCA_TC_TILES", tiles)
+    S = synth.small_random(N, B, 30 + N)
+    h, J = _theta(N, 30 + N, 0.2)
+    with api.Context(0) as c:
+        _compare(c, S, h, J)
