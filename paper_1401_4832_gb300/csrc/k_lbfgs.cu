@@ -381,14 +381,8 @@ k_dir_apply(const SiteState *ss, const float *__restrict__ g, const float *__res
             cy[j] = (float)s.cy[j];
         }
         DF acc[3];
-        for (size_t e = ch.e0 + threadIdx.x; e < ch.e1; e += LB_THREADS) {
-            const float4 gv = g4[e], tv = t4[e];
-            float4 sv[M], yv[M];
-#pragma unroll
-            for (int j = 0; j < M; ++j) {
-                sv[j] = valid[j] ? S4[(size_t)j * vec4 + e] : f4z();
-                yv[j] = valid[j] ? Y4[(size_t)j * vec4 + e] : f4z();
-            }
+        auto apply = [&](size_t e, const float4 &gv, const float4 &tv, const float4 (&sv)[M],
+                         const float4 (&yv)[M]) {
             float4 a = make_float4(cg * gv.x, cg * gv.y, cg * gv.z, cg * gv.w);
 #pragma unroll
             for (int j = 0; j < M; ++j) {
@@ -404,6 +398,25 @@ k_dir_apply(const SiteState *ss, const float *__restrict__ g, const float *__res
                                          fmaf(al, dv.z, tv.z), fmaf(al, dv.w, tv.w));
             o4[e] = x;
             trial_penalty_split(x, e, ch.base4, NQ, KP, hi, lo, acc[0], acc[1]);
+        };
+        // two elements per thread and iteration, all their loads issued
+        // before any arithmetic (twice the bytes in flight); the elements
+        // are applied and accumulated in index order, as one at a time
+        for (size_t e = ch.e0 + threadIdx.x; e < ch.e1; e += 2 * LB_THREADS) {
+            const size_t e2 = e + LB_THREADS;
+            const bool two = e2 < ch.e1;
+            const float4 gv = g4[e], tv = t4[e];
+            const float4 gv2 = two ? g4[e2] : f4z(), tv2 = two ? t4[e2] : f4z();
+            float4 sv[M], yv[M], sv2[M], yv2[M];
+#pragma unroll
+            for (int j = 0; j < M; ++j) {
+                sv[j] = valid[j] ? S4[(size_t)j * vec4 + e] : f4z();
+                yv[j] = valid[j] ? Y4[(size_t)j * vec4 + e] : f4z();
+                sv2[j] = (valid[j] && two) ? S4[(size_t)j * vec4 + e2] : f4z();
+                yv2[j] = (valid[j] && two) ? Y4[(size_t)j * vec4 + e2] : f4z();
+            }
+            apply(e, gv, tv, sv, yv);
+            if (two) apply(e2, gv2, tv2, sv2, yv2);
         }
         block_write<3>(acc, part_rec(part, c));
     }
