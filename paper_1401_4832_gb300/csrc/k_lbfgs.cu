@@ -213,7 +213,9 @@ __device__ __forceinline__ void trial_penalty_split(const float4 x, size_t e, si
                                                     DF &ph)
 {
     const float xv[4] = {x.x, x.y, x.z, x.w};
-    const int c0 = (int)((4 * e) % KP);
+    // 32-bit arithmetic: 4 e stays below 2^32 for every segment this solver
+    // streams (at most N QP KP elements)
+    const int c0 = (int)((4u * (uint32_t)e) % (uint32_t)KP);
     float sj = 0.0f, sh = 0.0f;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
