@@ -103,11 +103,16 @@ k_logits_gather(const int8_t *__restrict__ msa, const float *__restrict__ theta,
         const float *ths = ths0 + buf * LG_TILE;
         const int8_t *ssb = ss0 + buf * LG_BT * LG_IC;
         const int nic = min(LG_IC, d.N - i0);
+        // positions outer, sequences inner: the 16 sequences' gathers of a
+        // position are independent, so their loads are in flight together
+        // (each accumulator still adds the positions in order)
+        for (int ic = 0; ic < nic; ++ic) {
+            int st[LG_BPW];
 #pragma unroll
-        for (int u = 0; u < LG_BPW; ++u) {
-            const int8_t *sb = ssb + (warp * LG_BPW + u) * LG_IC;
-            for (int ic = 0; ic < nic; ++ic) {
-                const float *col = ths + (ic * Q + sb[ic]) * LG_STRIDE + lane;
+            for (int u = 0; u < LG_BPW; ++u) st[u] = ssb[(warp * LG_BPW + u) * LG_IC + ic];
+#pragma unroll
+            for (int u = 0; u < LG_BPW; ++u) {
+                const float *col = ths + (ic * Q + st[u]) * LG_STRIDE + lane;
 #pragma unroll
                 for (int j = 0; j < 4; ++j) acc[u][j] += col[32 * j];
             }
