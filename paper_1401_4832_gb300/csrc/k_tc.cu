@@ -149,6 +149,16 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, u
         : "memory");
 }
 
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar,
+                                            int x, int y, int z)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
 __device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols)
 {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -283,8 +293,12 @@ struct LogitsParams {
 struct GradParams {
     TcBatch b;
     int rows, ncols, stages, stage_bytes;  // tile: rows (128 or 256) x ncols columns
+    // k_tc_grad: 3-D maps (BP, 21 states, N sites), box (64, 21, GR_SITES);
+    // k_tc_grad_pair: 2-D maps over the padded rows, box (64, 128)
     CUtensorMap dhi[MAX_FAM], dlo[MAX_FAM];
 };
+
+constexpr int GR_BOX_BYTES = TC_BK * 2 * Q * GR_SITES;  // one (64, 21, 6) box: 16128 bytes
 
 // family owning global tile `tile` (tile0 ascending)
 __device__ __forceinline__ int family_of(const TcBatch &b, int tile, bool grad)
@@ -1027,9 +1041,13 @@ k_tc_logits_pair(const __grid_constant__ PairParams P, int *__restrict__ err)
 }
 
 // ---------------------------------------------------------------- gradient
-// One 128 x ncols tile per CTA (measured faster here than a persistent
+// One rows x ncols tile per CTA (measured faster here than a persistent
 // variant: with ~1.5 tiles per SM there is little epilogue to overlap, and
 // the whole-tile shared-memory staging of the epilogue writes G coalesced).
+// The rows are packed by site: each 128-row accumulator holds GR_SITES
+// sites x 21 states (rows 126 and 127 unused), loaded by one 3-D box per
+// operand that skips the padding rows of the residual, so no MMA is spent
+// on them; the epilogue writes the padding rows of G as zeros.
 // Warp 0: TMA for D^T hi/lo; warp 1: TMEM and MMA issue; warps 2-9: the
 // one-hot X^T producers (one operand row per thread: with one warp per
 // scheduler the producers were latency bound), then the epilogue.
@@ -1066,10 +1084,10 @@ k_tc_grad(const __grid_constant__ GradParams P, float two_lh, float two_lj, int 
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c0 = (local % nct) * GRN;
-    const int rs0 = (local / nct) * MR;
+    const int sg0 = (local / nct) * MH * GR_SITES;  // first site of the tile
     if (F.active) {
         bool any = false;
-        for (int r = rs0 / QP; r <= (rs0 + MR - 1) / QP && r < F.N; ++r)
+        for (int r = sg0; r < sg0 + MH * GR_SITES && r < F.N; ++r)
             any |= F.active[r] != 0;
         if (!any) return;
     }
@@ -1103,9 +1121,14 @@ k_tc_grad(const __grid_constant__ GradParams P, float two_lh, float two_lj, int 
                 if (n > 0 && !mbar_wait(&empty_[s], (n - 1) & 1, &abort_sh, err, ERR_TIMEOUT_TMA))
                     break;
                 uint8_t *st = smem + s * GRSTAGE;
-                mbar_expect_tx(&full_b[s], 2 * ABYTES);
-                tma_load_2d(st, &tm_dhi, &full_b[s], kc * TC_BK, rs0);
-                tma_load_2d(st + ABYTES, &tm_dlo, &full_b[s], kc * TC_BK, rs0);
+                // sites beyond N read as zeros; the full box is counted
+                mbar_expect_tx(&full_b[s], 2 * MH * GR_BOX_BYTES);
+                for (int h = 0; h < MH; ++h) {
+                    tma_load_3d(st + h * GR_A_BYTES, &tm_dhi, &full_b[s], kc * TC_BK, 0,
+                                sg0 + h * GR_SITES);
+                    tma_load_3d(st + ABYTES + h * GR_A_BYTES, &tm_dlo, &full_b[s], kc * TC_BK,
+                                0, sg0 + h * GR_SITES);
+                }
                 issued = kc + 1;
             }
             for (int kc = issued - NST < 0 ? 0 : issued - NST; kc < issued; ++kc)
@@ -1201,12 +1224,12 @@ k_tc_grad(const __grid_constant__ GradParams P, float two_lh, float two_lj, int 
         tc_fence_after();
         const int GS = GRN + 4;
         float *acc_s = (float *)smem;  // [128][GS]
-        const int ng = GRN / 32;  // 16-column groups per half
+        const int NG = GRN / 16, ng0 = (NG + 1) / 2;  // 16-column groups; half 0 takes ng0
         for (int h = 0; h < MH; ++h) {
         const uint32_t tl = tmem + h * TMEM_COLS + ((uint32_t)(q4 * 32) << 16);
-        const int rh = rs0 + h * TC_M;  // first row of this half
+        const int sh0 = sg0 + h * GR_SITES;  // first site of this half
 #pragma unroll 1
-        for (int cc = half * ng; cc < (half + 1) * ng; ++cc) {
+        for (int cc = half ? ng0 : 0; cc < (half ? NG : ng0); ++cc) {
             float v[16];
             tmem_ld16(tl + cc * 16, v);
             tmem_wait_ld();
@@ -1218,16 +1241,20 @@ k_tc_grad(const __grid_constant__ GradParams P, float two_lh, float two_lj, int 
         epi_bar256();
         const int t = threadIdx.x - 64;
         constexpr int UNR = 4;
-        for (int e0 = t; e0 < TC_M * (GRN / 4); e0 += GR_PROD * UNR) {
+        // accumulator row rr of this half: site sh0 + rr / Q, state rr % Q
+        constexpr int HR = GR_SITES * Q;  // 126 rows in use
+        for (int e0 = t; e0 < HR * (GRN / 4); e0 += GR_PROD * UNR) {
             float4 th[UNR];
             bool live[UNR];
+            int rowk[UNR];
 #pragma unroll
             for (int k = 0; k < UNR; ++k) {  // issue all loads first
                 const int e = e0 + GR_PROD * k;
                 const int rr = e / (GRN / 4), c4 = e % (GRN / 4);
-                const int row = rh + rr, cb = c0 + 4 * c4;
-                live[k] = ok && e < TC_M * (GRN / 4) && row < d.R && cb < d.KP;
-                th[k] = live[k] ? *(const float4 *)(theta + (size_t)row * d.KP + cb)
+                const int r = sh0 + rr / Q, cb = c0 + 4 * c4;
+                rowk[k] = r * QP + rr % Q;
+                live[k] = ok && e < HR * (GRN / 4) && r < d.N && cb < d.KP;
+                th[k] = live[k] ? *(const float4 *)(theta + (size_t)rowk[k] * d.KP + cb)
                                 : make_float4(0.f, 0.f, 0.f, 0.f);
             }
 #pragma unroll
@@ -1235,8 +1262,7 @@ k_tc_grad(const __grid_constant__ GradParams P, float two_lh, float two_lj, int 
                 if (!live[k]) continue;
                 const int e = e0 + GR_PROD * k;
                 const int rr = e / (GRN / 4), c4 = e % (GRN / 4);
-                const int row = rh + rr, cb = c0 + 4 * c4;
-                const int r = row / QP, sstate = row % QP;
+                const int r = sh0 + rr / Q, cb = c0 + 4 * c4;
                 const float4 a = *(const float4 *)(acc_s + rr * GS + 4 * c4);
                 const float av[4] = {a.x, a.y, a.z, a.w};
                 const float tv[4] = {th[k].x, th[k].y, th[k].z, th[k].w};
@@ -1245,13 +1271,22 @@ k_tc_grad(const __grid_constant__ GradParams P, float two_lh, float two_lj, int 
                 for (int u = 0; u < 4; ++u) {
                     const int c = cb + u;
                     float val;
-                    if (sstate >= Q || c > NQ || (c >= r * Q && c < r * Q + Q)) val = 0.0f;
+                    if (c > NQ || (c >= r * Q && c < r * Q + Q)) val = 0.0f;
                     else if (c == NQ) val = av[u] + two_lh * tv[u];
                     else val = av[u] + two_lj * tv[u];
                     o[u] = val;
                 }
-                *(float4 *)(G + (size_t)row * d.KP + cb) = make_float4(o[0], o[1], o[2], o[3]);
+                *(float4 *)(G + (size_t)rowk[k] * d.KP + cb) = make_float4(o[0], o[1], o[2], o[3]);
             }
+        }
+        // the padding rows (states Q..QP-1) of this half's sites
+        constexpr int PR = GR_SITES * (QP - Q);
+        for (int e = t; e < PR * (GRN / 4); e += GR_PROD) {
+            const int pr = e / (GRN / 4), c4 = e % (GRN / 4);
+            const int r = sh0 + pr / (QP - Q), cb = c0 + 4 * c4;
+            if (ok && r < d.N && cb < d.KP)
+                *(float4 *)(G + (size_t)(r * QP + Q + pr % (QP - Q)) * d.KP + cb) =
+                    make_float4(0.f, 0.f, 0.f, 0.f);
         }
         if (h + 1 < MH) epi_bar256();  // the staging buffer is reused by the next half
         }
@@ -1649,9 +1684,10 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
     return fn;
 }
 
-// 3-D bf16 map over the split Theta [N][QP][KP] that skips the padding
-// rows: dims (KP, Q states, N sites), box (64, Q, sh) lands as sh x Q rows
-// of 128 bytes, 128-byte swizzled
+// 3-D bf16 map over a site-major [N][QP][KP] array (the split Theta, or the
+// residual D^T with KP = BP) that skips the padding rows: dims (KP, Q
+// states, N sites), box (64, Q, sh) lands as sh x Q rows of 128 bytes,
+// 128-byte swizzled
 bool make_map_sites(CUtensorMap *m, const void *base, uint64_t KP, uint64_t N, uint32_t sh)
 {
     auto fn = encode_fn();
@@ -1772,7 +1808,8 @@ bool tc_config_valid(const TcConfig &c)
     const bool lg = c.lg_pair ? ((c.lg_pair == 1 || c.lg_pair == 2) &&
                                  (c.lg_sites == 4 || c.lg_sites == 8 || c.lg_sites == 12))
                               : (c.lg_sites >= 2 && c.lg_sites <= MAX_LG_SITES && c.lg_sites % 2 == 0);
-    return lg && c.gr_ncols >= 32 && c.gr_ncols <= 256 && c.gr_ncols % 32 == 0 &&
+    // one CTA: widths in steps of 16 (the MMA's N); a pair splits the width in two halves
+    return lg && c.gr_ncols >= 32 && c.gr_ncols <= 256 && c.gr_ncols % (c.gr_pair ? 32 : 16) == 0 &&
            (c.gr_rows == TC_M || c.gr_rows == 2 * TC_M) &&
            (c.gr_pair == 0 || (c.gr_pair == 1 && c.gr_rows == 2 * TC_M));
 }
@@ -1885,7 +1922,11 @@ cudaError_t launch_tc_eval(void *prof, const TcBatch &b_in, const TcConfig &cfg,
         F.tile0_grad = tg;
         const int nbt = cfg.lg_pair ? (F.BP / TC_M + 1) / 2 : F.BP / TC_M;
         tl += nbt * ((F.N + cfg.lg_sites - 1) / cfg.lg_sites);
-        tg += ((F.KP + cfg.gr_ncols - 1) / cfg.gr_ncols) * ((F.R + cfg.gr_rows - 1) / cfg.gr_rows);
+        // row tiles: padded rows on CTA pairs, GR_SITES sites per 128 rows on one CTA
+        const int nrt = cfg.gr_pair ? (F.R + cfg.gr_rows - 1) / cfg.gr_rows
+                                    : (F.N + GR_SITES * cfg.gr_rows / TC_M - 1) /
+                                          (GR_SITES * cfg.gr_rows / TC_M);
+        tg += ((F.KP + cfg.gr_ncols - 1) / cfg.gr_ncols) * nrt;
     }
     lp.b.ntiles_logits = tl;
     lp.b.ntiles_grad = tg;
@@ -1909,10 +1950,13 @@ cudaError_t launch_tc_eval(void *prof, const TcBatch &b_in, const TcConfig &cfg,
                            make_map_sites(&pp.lo[i], F.th_lo, F.KP, F.N, sh))
                         : (make_map(&lp.hi[i], F.th_hi, F.KP, F.R, TC_BK, lg_ncols) &&
                            make_map(&lp.lo[i], F.th_lo, F.KP, F.R, TC_BK, lg_ncols));
-        const int gbox = cfg.gr_pair ? TC_M : cfg.gr_rows;  // a pair's CTA loads 128 rows
-        if (!lg_ok || !make_map(&gp.dhi[i], F.dt_hi, F.BP, F.R, TC_BK, gbox) ||
-            !make_map(&gp.dlo[i], F.dt_lo, F.BP, F.R, TC_BK, gbox))
-            return cudaErrorInvalidValue;
+        // a pair's CTA loads 128 padded rows; one CTA loads GR_SITES sites per box
+        const bool gr_ok =
+            cfg.gr_pair ? (make_map(&gp.dhi[i], F.dt_hi, F.BP, F.R, TC_BK, TC_M) &&
+                           make_map(&gp.dlo[i], F.dt_lo, F.BP, F.R, TC_BK, TC_M))
+                        : (make_map_sites(&gp.dhi[i], F.dt_hi, F.BP, F.N, GR_SITES) &&
+                           make_map_sites(&gp.dlo[i], F.dt_lo, F.BP, F.N, GR_SITES));
+        if (!lg_ok || !gr_ok) return cudaErrorInvalidValue;
     }
     if (which & 1) {
         void *t0 = prof ? prof_start(prof) : nullptr;

@@ -445,8 +445,9 @@ std::string problem_signature(const Problem &P)
 // straddles two lanes
 std::vector<int> lane_bounds(int N, const TcConfig &c, int K)
 {
-    // 16 sites = 384 rows = three 128-row tiles; 32 sites = three 256-row tiles
-    const int step = c.gr_rows > 128 ? 32 : 16;
+    // gradient row tiles: 6 or 12 sites on one CTA; on CTA pairs 32 sites =
+    // 768 padded rows = three 256-row tiles
+    const int step = c.gr_pair ? 32 : (c.gr_rows > 128 ? 12 : 6);
     int unit = step;
     while (unit % c.lg_sites) unit += step;
     std::vector<int> b{0};
@@ -493,6 +494,22 @@ plm_status autotune_tc(plm_ctx *ctx, Problem &P, int *tc_err)
                 *best = 1e30f;
                 return PLM_OK;
             }
+            if (which == 2 && !c.gr_pair) {
+                // a lane's gradient grid leaves a fifth of the SMs to the other
+                // lanes' L-BFGS passes (about 150 registers a thread, so they
+                // cannot share an SM that a gradient CTA holds).  Measured on
+                // the family (N = 120, 60-site lanes, 128-row tiles): 120 CTAs
+                // a lane 0.029 s per solve, 130 0.029, 140 0.030, 150 0.031-0.032,
+                // while timed alone the 150-CTA grid is the fastest.
+                const FamDesc &F = P.tcb[0].f[0];
+                const int spt = GR_SITES * c.gr_rows / 128;
+                const int nct = (F.KP + c.gr_ncols - 1) / c.gr_ncols;
+                for (int k = 0; k < nl; ++k)
+                    if ((b[k + 1] - b[k] + spt - 1) / spt * nct > num_sms() * 4 / 5) {
+                        *best = 1e30f;
+                        return PLM_OK;
+                    }
+            }
             std::vector<uint8_t> h((size_t)nl * N, 0);
             for (int k = 0; k < nl; ++k)
                 for (int r = b[k]; r < b[k + 1]; ++r) h[(size_t)k * N + r] = 1;
@@ -536,8 +553,10 @@ plm_status autotune_tc(plm_ctx *ctx, Problem &P, int *tc_err)
     }
     tbest = 1e30f;
     // gradient: 128- or 256-row single-CTA tiles, or 256-row tiles on CTA pairs
+    // (whose width splits in two halves of a multiple of 16)
     for (int shape : {0, 1, 2})
-        for (int cols : {128, 160, 192, 224, 256}) {
+        for (int cols : {128, 144, 160, 176, 192, 208, 224, 256}) {
+            if (shape == 2 && cols % 32) continue;
             TcConfig c = best;
             c.gr_rows = shape == 0 ? 128 : 256;
             c.gr_pair = shape == 2 ? 1 : 0;
@@ -554,6 +573,9 @@ plm_status autotune_tc(plm_ctx *ctx, Problem &P, int *tc_err)
         }
     ctx->event_pool.push_back(e0);
     ctx->event_pool.push_back(e1);
+    if (getenv("PLMDCA_TC_VERBOSE"))  // the chosen shape, in PLMDCA_TC_TILES form
+        fprintf(stderr, "plmdca tiles %s: %d,%d,%d,%d,%d\n", sig.c_str(), best.lg_sites,
+                best.gr_ncols, best.gr_rows, best.lg_pair, best.gr_pair);
     P.tc_cfg = best;
     P.tc_tuned = true;
     std::lock_guard<std::mutex> lock(g_tune_mutex);

@@ -48,6 +48,9 @@ void count_launches(int n);
 
 constexpr int Q = 21;     // states: 20 amino acids + gap (Sec. 2)
 constexpr int QP = 24;    // rows per site in the padded layout
+// sites per 128-row accumulator of the single-CTA gradient kernel: its D^T
+// box skips the QP - Q padding rows of every site, so 6 sites fill 126 rows
+constexpr int GR_SITES = 6;
 constexpr int KALIGN = 64;
 
 struct Dims {

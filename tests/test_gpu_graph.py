@@ -22,17 +22,18 @@ def test_graph_replay_equals_eager(prec):
     assert r1["n_converged"] == S.shape[1]
 
 
-@pytest.mark.parametrize("tiles", ["8,224", "8,224,256", "12,224,128,1", "12,224,256,1,1"])
+@pytest.mark.parametrize("tiles", ["8,224", "8,224,256", "12,224,128,1", "12,176,256,1",
+                                   "12,224,256,1,1"])
 @pytest.mark.parametrize("which", ["family", "ragged"])
 def test_two_lane_pipeline_equals_one_lane(which, tiles, monkeypatch):
     # With graphs on, a one-family tensor-core solve runs in two lanes (two
     # streams, device-side loops, one lane rotated by half a round) when the
     # sites split at a boundary shared by the site groups and the gradient
-    # row tiles; with 8-site groups that boundary is a multiple of 16 sites
-    # for 128-row tiles and of 32 sites for 256-row tiles (N = 120: 64 + 56
-    # both ways; N = 70: 32 + 38 both ways).  Each site's iterates depend
-    # only on its own row block, so the result must equal the one-lane
-    # eager solve bit for bit.
+    # row tiles (6 or 12 sites on one CTA, 32 sites on CTA pairs); with
+    # 8-site groups that boundary is a multiple of 24 sites (N = 120: 72 +
+    # 48; N = 70: 24 + 46), with 12-site groups one of 12 (N = 120: 60 + 60).
+    # Each site's iterates depend only on its own row block, so the result
+    # must equal the one-lane eager solve bit for bit.
     from paper_1401_4832_gb300 import api
     monkeypatch.setenv("PLMDCA_TC_TILES", tiles)
     if which == "family":

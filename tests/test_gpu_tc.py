@@ -141,8 +141,8 @@ def test_tc_solve_tiny_identical_contacts(ctx):
 
 
 TILE_SHAPES = ([(s, 256, 128, 0, 0) for s in (2, 4, 6, 10)]
-               + [(8, c, 128, 0, 0) for c in (32, 128, 160, 192, 224)]
-               + [(8, c, 256, 0, 0) for c in (32, 128, 224, 256)]
+               + [(8, c, 128, 0, 0) for c in (32, 128, 144, 160, 176, 192, 224)]
+               + [(8, c, 256, 0, 0) for c in (32, 48, 128, 176, 208, 224, 256)]
                + [(s, 256, 128, 1, 0) for s in (4, 8, 12)]
                + [(12, c, 256, 1, 1) for c in (128, 160, 192, 224, 256)])
 
@@ -150,10 +150,13 @@ TILE_SHAPES = ([(s, 256, 128, 0, 0) for s in (2, 4, 6, 10)]
 @pytest.mark.parametrize("sites,cols,rows,pair,gpair", TILE_SHAPES)
 def test_tc_every_tile_shape(sites, cols, rows, pair, gpair, monkeypatch):
     # every shape the autotuner may pick gives the same numbers (ragged in
-    # both GEMM dimensions: N=37 -> 37 % sites != 0, K = 800 -> K % cols != 0,
-    # R = 37 * 24 = 888 rows -> the last 256-row tile holds 120 real rows, so
-    # its second 128-row half is all padding); pair = 1: the logits on 2-CTA
-    # clusters, gpair = 1: the gradient on 2-CTA clusters
+    # both GEMM dimensions: N=37 -> 37 % sites != 0, K = 800 -> K % cols != 0;
+    # one CTA packs 6 sites per 128 gradient rows, so the last 256-row tile
+    # holds one site and its second half lies wholly beyond N; on CTA pairs
+    # R = 37 * 24 = 888 padded rows -> the last 256-row tile holds 120 real
+    # rows); widths that are odd multiples of 16 split the epilogue's column
+    # groups unevenly; pair = 1: the logits on 2-CTA clusters, gpair = 1:
+    # the gradient on 2-CTA clusters
     from paper_1401_4832_gb300 import api
     monkeypatch.setenv("PLMDCA_TC_TILES", f"{sites},{cols},{rows},{pair},{gpair}")
     S = synth.add_clusters(synth.small_random(37, 203, 4), 0.3, 4, max_redraw=0.1)
