@@ -495,20 +495,24 @@ plm_status autotune_tc(plm_ctx *ctx, Problem &P, int *tc_err)
                 return PLM_OK;
             }
             if (which == 2 && !c.gr_pair) {
-                // a lane's gradient grid leaves a fifth of the SMs to the other
-                // lanes' L-BFGS passes (about 150 registers a thread, so they
-                // cannot share an SM that a gradient CTA holds).  Measured on
-                // the family (N = 120, 60-site lanes, 128-row tiles): 120 CTAs
-                // a lane 0.029 s per solve, 130 0.029, 140 0.030, 150 0.031-0.032,
-                // while timed alone the 150-CTA grid is the fastest.
+                // a lane's one-wave gradient grid leaves a fifth of the SMs to
+                // the other lanes' L-BFGS passes (about 150 registers a
+                // thread, so they cannot share an SM that a gradient CTA
+                // holds).  Measured on the family (N = 120, 60-site lanes,
+                // 128-row tiles): 120 CTAs a lane 0.029 s per solve, 130
+                // 0.029, 140 0.030, 150 0.031-0.032, while timed alone the
+                // 150-CTA grid is the fastest.  Grids of several waves hold
+                // every SM whatever their width and stay candidates.
                 const FamDesc &F = P.tcb[0].f[0];
                 const int spt = GR_SITES * c.gr_rows / 128;
                 const int nct = (F.KP + c.gr_ncols - 1) / c.gr_ncols;
-                for (int k = 0; k < nl; ++k)
-                    if ((b[k + 1] - b[k] + spt - 1) / spt * nct > num_sms() * 4 / 5) {
+                for (int k = 0; k < nl; ++k) {
+                    const int ctas = (b[k + 1] - b[k] + spt - 1) / spt * nct;
+                    if (ctas > num_sms() * 4 / 5 && ctas <= num_sms()) {
                         *best = 1e30f;
                         return PLM_OK;
                     }
+                }
             }
             std::vector<uint8_t> h((size_t)nl * N, 0);
             for (int k = 0; k < nl; ++k)
