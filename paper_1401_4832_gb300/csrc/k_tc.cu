@@ -1806,7 +1806,8 @@ int num_sms()
 bool tc_config_valid(const TcConfig &c)
 {
     const bool lg = c.lg_pair ? ((c.lg_pair == 1 || c.lg_pair == 2) &&
-                                 (c.lg_sites == 4 || c.lg_sites == 8 || c.lg_sites == 12))
+                                 (c.lg_sites == 4 || c.lg_sites == 8 || c.lg_sites == 10 ||
+                                  c.lg_sites == 12))
                               : (c.lg_sites >= 2 && c.lg_sites <= MAX_LG_SITES && c.lg_sites % 2 == 0);
     // one CTA: widths in steps of 16 (the MMA's N); a pair splits the width in two halves
     return lg && c.gr_ncols >= 32 && c.gr_ncols <= 256 && c.gr_ncols % (c.gr_pair ? 32 : 16) == 0 &&
@@ -1968,6 +1969,8 @@ cudaError_t launch_tc_eval(void *prof, const TcBatch &b_in, const TcConfig &cfg,
                                                : launch_logits_pair<2, 2>(pp, tl, err, st);
             else if (sh == 4) e2 = cfg.lg_pair == 2 ? launch_logits_pair<4, 1>(pp, tl, err, st)
                                                     : launch_logits_pair<4, 2>(pp, tl, err, st);
+            else if (sh == 5) e2 = cfg.lg_pair == 2 ? launch_logits_pair<5, 1>(pp, tl, err, st)
+                                                    : launch_logits_pair<5, 2>(pp, tl, err, st);
             else e2 = cfg.lg_pair == 2 ? launch_logits_pair<6, 1>(pp, tl, err, st)
                                        : launch_logits_pair<6, 2>(pp, tl, err, st);
             if (e2) return e2;

@@ -540,8 +540,8 @@ plm_status autotune_tc(plm_ctx *ctx, Problem &P, int *tc_err)
     float tbest = 1e30f;
     if (laned && lane_bounds(N, best, P.tune_lanes).size() - 1 < (size_t)P.tune_lanes)
         best.lg_sites = 4;  // a default that splits
-    // logits: single-CTA tiles of 4..10 sites, pair tiles of 8 or 12 sites
-    const int lg_cand[6][2] = {{4, 0}, {6, 0}, {8, 0}, {10, 0}, {8, 1}, {12, 1}};
+    // logits: single-CTA tiles of 4..10 sites, pair tiles of 8, 10 or 12 sites
+    const int lg_cand[7][2] = {{4, 0}, {6, 0}, {8, 0}, {10, 0}, {8, 1}, {10, 1}, {12, 1}};
     for (const auto &lc : lg_cand) {
         TcConfig c = best;
         c.lg_sites = lc[0];

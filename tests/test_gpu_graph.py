@@ -23,7 +23,7 @@ def test_graph_replay_equals_eager(prec):
 
 
 @pytest.mark.parametrize("tiles", ["8,224", "8,224,256", "12,224,128,1", "12,176,256,1",
-                                   "12,224,256,1,1"])
+                                   "10,224,128,1", "12,224,256,1,1"])
 @pytest.mark.parametrize("which", ["family", "ragged"])
 def test_two_lane_pipeline_equals_one_lane(which, tiles, monkeypatch):
     # With graphs on, a one-family tensor-core solve runs in two lanes (two
@@ -31,7 +31,9 @@ def test_two_lane_pipeline_equals_one_lane(which, tiles, monkeypatch):
     # sites split at a boundary shared by the site groups and the gradient
     # row tiles (6 or 12 sites on one CTA, 32 sites on CTA pairs); with
     # 8-site groups that boundary is a multiple of 24 sites (N = 120: 72 +
-    # 48; N = 70: 24 + 46), with 12-site groups one of 12 (N = 120: 60 + 60).
+    # 48; N = 70: 24 + 46), with 12-site groups one of 12 (N = 120: 60 + 60),
+    # with 10-site groups and 128-row tiles one of 30 (N = 120: 60 + 60;
+    # N = 70: 30 + 40).
     # Each site's iterates depend only on its own row block, so the result
     # must equal the one-lane eager solve bit for bit.
     from paper_1401_4832_gb300 import api

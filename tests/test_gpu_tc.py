@@ -143,7 +143,7 @@ def test_tc_solve_tiny_identical_contacts(ctx):
 TILE_SHAPES = ([(s, 256, 128, 0, 0) for s in (2, 4, 6, 10)]
                + [(8, c, 128, 0, 0) for c in (32, 128, 144, 160, 176, 192, 224)]
                + [(8, c, 256, 0, 0) for c in (32, 48, 128, 176, 208, 224, 256)]
-               + [(s, 256, 128, 1, 0) for s in (4, 8, 12)]
+               + [(s, 256, 128, 1, 0) for s in (4, 8, 10, 12)]
                + [(12, c, 256, 1, 1) for c in (128, 160, 192, 224, 256)])
 
 
@@ -165,7 +165,7 @@ def test_tc_every_tile_shape(sites, cols, rows, pair, gpair, monkeypatch):
         _compare(c, S, h, J)
 
 
-@pytest.mark.parametrize("sites,gpair", [(4, 0), (8, 0), (12, 0), (12, 1)])
+@pytest.mark.parametrize("sites,gpair", [(4, 0), (8, 0), (10, 0), (12, 0), (12, 1)])
 @pytest.mark.parametrize("N,B", [(50, 300), (23, 129), (120, 5000)])
 def test_tc_pair_logits_ragged(sites, gpair, N, B, monkeypatch):
     # 2-CTA logits tiles: an odd number of 128-sequence tiles (the last pair
@@ -216,7 +216,8 @@ def test_tc_autotuner_tries_every_shape_in_one_process():
 
 
 @pytest.mark.parametrize("N,B", [(2, 1), (5, 127), (13, 129), (7, 257)])
-@pytest.mark.parametrize("tiles", ["12,224,256,1,0", "4,128,256,1,1", "12,256,256,2,1"])
+@pytest.mark.parametrize("tiles", ["12,224,256,1,0", "4,128,256,1,1", "12,256,256,2,1",
+                                   "10,176,128,1,0"])
 def test_tc_pair_shapes_at_the_edges(N, B, tiles, monkeypatch):
     # smallest problems on the 2-CTA kernels: fewer sites than half a tile
     # (the peer CTA's Theta box lies wholly beyond N and reads zeros), one
